@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Throughput of the randomized block-CG solver on one GB300 (or N replicas).
+
+Workload: the sparse SPD system of a variable-coefficient 3D 7-point diffusion
+operator on a 128^3 grid (d = 2,097,152, nnz = 14,581,760, face coefficients
+exp(N(0,1)), FP64 values, int32 indices), shift mu = 1e-4, b ~ N(0, I), sketch
+Omega of 32 Gaussian columns (block width 33). All inputs are seeded synthetic data.
+
+One step = one complete solve to relative residual 1e-8 (FP64 residual recomputed
+from the FP64 matrix): FP32 block operator / updates, FP64 Grams, small solves and
+refinement. The plain FP64 path (every block quantity in FP64, stopped at the same
+1e-8) is timed beside it. value = solves/s over all ranks (weak scaling: every rank
+solves its own copy of the system).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2501_18717_gb300 import workloads as W  # noqa: E402
+
+GRID = 128
+SKETCH = 32
+MU = 1e-4
+TOL = 1e-8
+SEED = W.BASE_SEED + 2
+OMEGA_SEED = W.BASE_SEED + 3
+METRIC = "solves/s at rel. residual 1e-8 and HBM GB/s per iteration, mixed vs FP64 plain"
+WORKLOAD = "csr_diffusion_128^3_d2097152_nnz14581760_mu1e-4_l32"
+KERNEL_SOURCES = ["paper_2501_18717_gb300/csrc/k_ops.cu", "paper_2501_18717_gb300/csrc/k_block.cu",
+                  "paper_2501_18717_gb300/csrc/bk_tile.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    # smaller cases for profiling runs (ncu); the default is the 128^3 workload
+    ap.add_argument("--grid", type=int, default=GRID)
+    ap.add_argument("--max-loads", type=int, default=20000)
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def algorithmic_bytes(d, nnz, m):
+    """Bytes each kernel must move per launch at FP32 block precision."""
+    blk = d * m * 4
+    return {
+        "operator": nnz * (4 + 4) + (d + 1) * 4 + 2 * blk,  # A values+indices, read P, write Y
+        "update_r": 3 * blk,                               # read Y, R; write R
+        "update_p": 3 * blk + 2 * d * 8,                   # read R, P; write P; x read+write (FP64)
+    }
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            j = json.load(fh)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(name):
+    """ncu DRAM bytes per launch for `name`, if the committed capture matches the sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        j = json.load(fh)
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if j.get("sources_sha256") != h.hexdigest():
+        return None
+    return j.get("kernels", {}).get(name)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------------- oracle
+def oracle_sample(rp, ci, va, b, seconds, max_loads=60):
+    """Time the FP64 oracle's block-CG recurrence on the full workload for a bounded
+    number of loads; returns (seconds per load, loads run, threads)."""
+    from oracle import bcg, operators
+    op = operators.CSR(rp, ci, va)
+    d = b.shape[0]
+    om = W.omega(OMEGA_SEED, d, SKETCH)
+    B = W.inner_start_block(b, om)
+    # one load to learn the per-load time, then as many as fit in the budget
+    t0 = time.perf_counter()
+    bcg.block_cg(op, MU, B[:, 0], B[:, 1:], tol=0.0, max_loads=1)
+    t1 = time.perf_counter() - t0
+    n = int(max(2, min(max_loads, seconds / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    bcg.block_cg(op, MU, B[:, 0], B[:, 1:], tol=0.0, max_loads=n)
+    dt = time.perf_counter() - t0
+    threads = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max(i.get("num_threads", 1) for i in threadpool_info()) or threads
+    except Exception:  # noqa: BLE001
+        pass
+    return dt / n, n, threads
+
+
+def oracle_loads_per_solve():
+    p = os.path.join(ROOT, "oracle", "loads_diffusion128.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)["loads_fp64_refined_1e-8"], "oracle run to 1e-8 (oracle/loads_diffusion128.json)"
+    return None, None
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    rp, ci, va, d = W.diffusion_csr(SEED, GRID)
+    b = W.normals(SEED, W.STREAM_RHS, d)
+    lps, src = oracle_loads_per_solve()
+    per_load = []
+    for i in range(args.warmup + args.steps):
+        s, n, thr = oracle_sample(rp, ci, va, b, min(args.cpu_seconds, 15.0), max_loads=8)
+        if i >= args.warmup:
+            per_load.append(s)
+    spl = statistics.median(per_load)
+    value = (1.0 / (spl * lps)) if lps else None
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": spl * 1e3 * (lps or 0),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "working set larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": thr, "kind": "oracle",
+                         "sample": f"each step: {n} loads of the FP64 oracle block-CG recurrence on the full "
+                                   f"workload; solves/s = 1/(s per load x {lps} loads per solve, {src})"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    from paper_2501_18717_gb300 import bk
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    rp, ci, va, d = W.diffusion_csr(SEED, args.grid)
+    b = W.normals(SEED, W.STREAM_RHS, d)
+    nnz = va.shape[0]
+    m = SKETCH + 1
+    A = bk.csr_operator(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), torch.from_numpy(va).to(dev))
+    bd = torch.from_numpy(b).to(dev)
+    x = torch.zeros(d, dtype=torch.float64, device=dev)
+    ctx = bk.Context(local)
+    stream = torch.cuda.Stream(dev)
+    ctx.set_stream(stream.cuda_stream)
+
+    mixed = bk.default_opts(tol=TOL, sketch=SKETCH, seed=OMEGA_SEED, inner="fp32", inner_tol=1e-5,
+                            check_every=16, max_loads=args.max_loads, profile=1)
+    plain = bk.default_opts(tol=TOL, sketch=SKETCH, seed=OMEGA_SEED, inner="fp64", inner_tol=1e-6,
+                            check_every=16, max_loads=args.max_loads, profile=1)
+
+    def solve(opts, A_, b_, x_):
+        with torch.cuda.stream(stream):
+            return bk.solve(ctx, A_, MU, b_, x_, opts, check=args.max_loads >= 20000)
+
+    for _ in range(args.warmup):
+        solve(mixed, A, bd, x)
+    barrier()
+    torch.cuda.synchronize(dev)
+    infos = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            infos.append(solve(mixed, A, bd, x))
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1e3)
+    rel_res = max(i.rel_residual for i in infos)
+    loads = [i.loads for i in infos]
+
+    # per-kernel timings from the events recorded between launches in the timed solves
+    kms = np.sum([list(i.ms_kernel) for i in infos], axis=0)
+    kn = np.sum([list(i.launches) for i in infos], axis=0)
+    names = bk.KERNEL_CLASSES
+    algo = algorithmic_bytes(d, nnz, m)
+    peak, peak_src = measured_peaks()
+    kernels = {}
+    for k in ("operator", "update_r", "update_p"):
+        j = names.index(k)
+        avg_ms = kms[j] / max(kn[j], 1)
+        gbs = algo[k] / (avg_ms / 1e3) / 1e9
+        kernels[k] = {"avg_ms": avg_ms, "launches": int(kn[j]), "algo_bytes": algo[k], "gbs": gbs,
+                      "frac": gbs / peak, "share": float(kms[j] / max(np.sum(kms), 1e-9))}
+    for k in ("reduce", "alpha", "beta"):
+        j = names.index(k)
+        kernels[k] = {"avg_ms": kms[j] / max(kn[j], 1), "launches": int(kn[j]),
+                      "share": float(kms[j] / max(np.sum(kms), 1e-9))}
+    dom = max(("operator", "update_r", "update_p"), key=lambda k: kernels[k]["share"])
+    kd = kernels[dom]
+    iter_ms = float(np.sum(kms)) / max(int(kn[names.index("operator")]), 1)
+    iter_bytes = algo["operator"] + algo["update_r"] + algo["update_p"]
+
+    # plain FP64 path on the same GPU
+    fp64 = None
+    if args.fp64_steps > 0:
+        solve(plain, A, bd, x)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pinfo = [solve(plain, A, bd, x) for _ in range(args.fp64_steps)]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        pms = e0.elapsed_time(e1)
+        pk = np.sum([list(i.ms_kernel) for i in pinfo], axis=0)
+        pn = np.sum([list(i.launches) for i in pinfo], axis=0)
+        fp64 = {"value": args.fp64_steps / (pms / 1e3), "unit": "solves/s", "ms_per_solve": pms / args.fp64_steps,
+                "loads": [i.loads for i in pinfo], "rel_residual": max(i.rel_residual for i in pinfo),
+                "iter_ms": float(np.sum(pk)) / max(int(pn[names.index("operator")]), 1)}
+
+    # end to end through the C ABI with pinned host buffers: H2D of A and b, D2H of x
+    if args.no_e2e:
+        args.steps_e2e = 0
+    hrp = torch.from_numpy(rp).pin_memory()
+    hci = torch.from_numpy(ci).pin_memory()
+    hva = torch.from_numpy(va).pin_memory()
+    hb = torch.from_numpy(b).pin_memory()
+    hx = torch.zeros(d, dtype=torch.float64).pin_memory()
+    Ah = bk.csr_operator(hrp, hci, hva)
+    e2e_opts = bk.default_opts(tol=TOL, sketch=SKETCH, seed=OMEGA_SEED, inner="fp32", inner_tol=1e-5,
+                               check_every=16, max_loads=20000)
+    n_e2e = 0 if args.no_e2e else args.steps
+    if n_e2e:
+        solve(e2e_opts, Ah, hb, hx)
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        solve(e2e_opts, Ah, hb, hx)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = rp.nbytes + ci.nbytes + va.nbytes + b.nbytes
+    d2h = d * 8
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        spl, n, thr = oracle_sample(rp, ci, va, b, args.cpu_seconds)
+        lps, src = oracle_loads_per_solve()
+        if lps is None:
+            lps, src = (fp64["loads"][0] if fp64 else loads[0]), "loads of this run's FP64 GPU solve"
+            # (used only until oracle/loads_diffusion128.json, written by the oracle itself, exists)
+        cpu = {"value": 1.0 / (spl * lps), "unit": "solves/s", "cores": thr, "kind": "oracle",
+               "sample": f"{n} loads of the FP64 oracle block-CG recurrence (NumPy/SciPy) on the full workload, "
+                         f"{spl:.3f} s/load; solves/s = 1/(s per load x {lps} loads per solve, {src})"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 block ops + f64 Gram/solve/refinement", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sketch_l": SKETCH, "block_width": m, "tol": TOL,
+                       "inner": "fp32, inner_tol 1e-5", "l2": "working set (blocks 3 x 277 MB + A 125 MB) "
+                                                             "larger than L2; no flush"},
+            "loads_per_solve": loads, "rel_residual_max": rel_res,
+            "iteration": {"ms": iter_ms, "algo_bytes": iter_bytes, "gbs": iter_bytes / (iter_ms / 1e3) / 1e9,
+                          "frac": iter_bytes / (iter_ms / 1e3) / 1e9 / peak},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": kd["gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": kd["frac"], "traffic": kernel_traffic(dom), "peak_source": peak_src},
+            "kernels": kernels,
+            "fp64_plain": fp64,
+            "e2e": {"value": world * n_e2e / e2e_s if n_e2e else None, "unit": "solves/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(sum(i.kernel_launches for i in infos)),
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * bk.h -- C ABI of the randomized ("augmented") block-CG library for GB300 (sm_103a).
+ *
+ * The method: to solve A_mu x = b with A_mu = A + mu I, A symmetric positive
+ * definite and mu >= 0 (paper Sec. 1, Eq. regularized_ls), run block-CG on the
+ * augmented start block B = [b Omega], Omega a d x l Gaussian sketch, and keep the
+ * iterate of the first column, bcg_t^(1)(mu) (Sec. 3, Def. BCG and Thm. main).
+ * The iterate is the minimiser of the A_mu-norm error over the block Krylov space
+ * K_t(A_mu, B); by Thm. main it is at least as accurate, after the same number of
+ * passes over A ("matrix-loads", Sec. 1.2), as CG preconditioned by any Nystrom
+ * preconditioner built from Omega.
+ *
+ * Conventions for every entry point
+ *   - Memory: every array argument may be a host pointer or a device pointer of the
+ *     context's device; the library detects which (cudaPointerGetAttributes) and
+ *     copies host arrays through its own workspace. Arrays are borrowed for the call
+ *     only; the caller keeps ownership. The library owns the context's workspace.
+ *   - Layout: dense matrices are row-major with leading dimension ld (>= cols).
+ *     Block vectors (d x m) are column-major with leading dimension ld (>= d).
+ *     CSR uses int32 rowptr (d+1 entries, rowptr[0] = 0) and int32 colidx.
+ *   - Streams: work is ordered on the context's stream. Each call returns after its
+ *     results are complete (it synchronises that stream).
+ *   - Errors: functions return a bk_status and never throw. On BK_ERR_* the outputs
+ *     are undefined. BK_NOT_CONVERGED and BK_BREAKDOWN leave the best iterate so far
+ *     in x. A CUDA error is reported as BK_ERR_CUDA and leaves the context usable
+ *     unless the CUDA context itself was lost.
+ *   - Threads: a context is not thread-safe; use one context per host thread.
+ */
+#ifndef BK_H
+#define BK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bk_ctx bk_ctx;
+
+typedef enum {
+  BK_OK = 0,
+  BK_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, bad enum) */
+  BK_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  BK_ERR_OOM = 3,          /* device workspace could not be allocated */
+  BK_NOT_CONVERGED = 4,    /* max_loads or max_refine reached before tol */
+  BK_BREAKDOWN = 5,        /* a block Gram matrix lost positive definiteness */
+  BK_STAGNATED = 6,        /* refinement stopped reducing the FP64 residual */
+  BK_TIMEOUT = 7,          /* reserved: a device wait ran past its limit */
+  BK_ERR_UNSUPPORTED = 8   /* operator kind / dtype / width not built */
+} bk_status;
+
+typedef enum { BK_DENSE = 0, BK_CSR = 1 } bk_op_kind;
+typedef enum { BK_F64 = 0, BK_F32 = 1 } bk_dtype;
+
+/* Precision of the inner block-CG iteration (block vectors, block products,
+ * updates). Gram matrices, the small Cholesky solves, the solution accumulator and
+ * the refinement residual are FP64 in both modes. */
+typedef enum { BK_PREC_FP64 = 0, BK_PREC_FP32 = 1 } bk_prec;
+
+/* The matrix A (without the shift mu).
+ *   BK_DENSE: vals is rows x cols row-major with leading dimension ld, rows = cols = d.
+ *   BK_CSR:   rowptr[rows+1], colidx[nnz], vals[nnz]; rows = cols = d; ld ignored.
+ *   dtype gives the element type of vals. A must be symmetric positive definite
+ *   (or positive semi-definite with mu > 0); the library does not check symmetry. */
+typedef struct {
+  int32_t kind;           /* bk_op_kind */
+  int32_t dtype;          /* bk_dtype of vals */
+  int64_t rows, cols, ld;
+  const void* vals;
+  const int32_t* rowptr;
+  const int32_t* colidx;
+  int64_t nnz;
+} bk_operator;
+
+typedef struct {
+  double tol;             /* stop when ||b - A_mu x||_2 <= tol ||b||_2, the residual
+                             recomputed in FP64 from the stored A (Sec. 4 remark on
+                             a-posteriori residual checks) */
+  int32_t max_loads;      /* cap on block products over all refinement steps */
+  int32_t sketch;         /* l, the columns of Omega; block width m = l + 1 (<= 64) */
+  uint64_t seed;          /* Philox4x32-10 key of Omega (stream 3, see bk_gaussian) */
+  int32_t inner;          /* bk_prec of the inner iteration */
+  double inner_tol;       /* inner solve stops when its column-0 residual has been
+                             reduced by this factor (or enough to meet tol) */
+  int32_t max_refine;     /* cap on FP64 refinement restarts */
+  int32_t check_every;    /* block products between host polls of the device flag */
+  int32_t profile;        /* nonzero: time every step kernel with CUDA events recorded
+                             between launches (kept inside the CUDA graph) and report
+                             the sums in bk_info.ms_kernel / launches */
+} bk_opts;
+
+/* Kernel classes reported by a profiled solve. */
+enum {
+  BK_K_OPERATOR = 0,  /* block product Y = A_mu P with the Gram P^T Y */
+  BK_K_REDUCE = 1,    /* Gram partial reductions (both per step) */
+  BK_K_ALPHA = 2,     /* small solve alpha = G^+ S */
+  BK_K_UPDATE_R = 3,  /* R -= Y alpha with the Gram R^T R */
+  BK_K_BETA = 4,      /* residual test and small solve beta = S^+ S' */
+  BK_K_UPDATE_P = 5,  /* x += P alpha e_1, P = R + P beta */
+  BK_K_CLASSES = 8
+};
+
+typedef struct {
+  int32_t status;         /* bk_status of the call */
+  int32_t loads;          /* block products applied (the paper's matrix-loads) */
+  int32_t refinements;    /* inner solves run (1 = no restart was needed) */
+  int32_t residual_loads; /* single-column FP64 residual products */
+  double rel_residual;    /* final ||b - A_mu x|| / ||b|| in FP64 */
+  double ms_total;        /* wall time of the call on the context stream */
+  double ms_kernel[8];    /* profiled solves: summed kernel time per class (BK_K_*) */
+  int32_t launches[8];    /* profiled solves: active launches per class */
+  int32_t kernel_launches;/* all kernels this call launched, including graph replays
+                             and steps that found the solve already finished */
+} bk_info;
+
+/* Fills *opts with defaults: tol 1e-10, max_loads 20000, sketch 20, seed 0,
+ * inner FP64, inner_tol 1e-6, max_refine 8, check_every 8, profile 0. */
+void bk_default_opts(bk_opts* opts);
+
+/* Creates a context on CUDA device `device`, ordering work on `cuda_stream` (a
+ * cudaStream_t). NULL makes the context create its own blocking stream, which is
+ * ordered with the legacy default stream (needed because the solve captures its
+ * step sequence into a CUDA graph, which the legacy stream does not allow). */
+bk_status bk_create(bk_ctx** ctx, int device, void* cuda_stream);
+bk_status bk_destroy(bk_ctx* ctx);
+bk_status bk_set_stream(bk_ctx* ctx, void* cuda_stream);
+const char* bk_status_string(bk_status s);
+/* Text of the last CUDA failure seen by a call on this context ("" if none). The
+ * string is owned by the context and valid until its next call. */
+const char* bk_last_error(const bk_ctx* ctx);
+
+/* Solves A_mu x = b by randomized block-CG on [b Omega] with FP64 residual
+ * refinement (Def. BCG, Thm. main; stopping rule of the Sec. 4 remark).
+ *   A    operator descriptor (see bk_operator)
+ *   mu   shift, >= 0
+ *   b    d doubles
+ *   x    d doubles; output. Its input value is ignored (the solve starts at 0).
+ *   opts NULL for defaults
+ *   info may be NULL
+ * With inner = BK_PREC_FP32 the block products use an FP32 copy of the values
+ * (made by the library from FP64 values, or the values themselves when dtype is
+ * FP32) and the refinement residual uses the values as given. */
+bk_status bk_solve(bk_ctx* ctx, const bk_operator* A, double mu, const double* b, double* x,
+                   const bk_opts* opts, bk_info* info);
+
+/* One block product with its Gram matrix (one "matrix-load", Sec. 1.2):
+ *   Y = A P + mu P  and  G = P^T Y  (m x m, FP64, row-major).
+ * P and Y are d x m column-major with leading dimension ld, element type `dtype`
+ * (BK_F64 or BK_F32; for BK_F32 the operator values are rounded to FP32 first if
+ * they are FP64). 1 <= m <= 64. G accumulates FP32 products in FP32 over row tiles
+ * and in FP64 across tiles when dtype is BK_F32. */
+bk_status bk_block_apply(bk_ctx* ctx, const bk_operator* A, double mu, int32_t dtype, int64_t m,
+                         const void* P, void* Y, int64_t ld, double* G);
+
+/* G = X^T Y for d x m column-major blocks X, Y (leading dimension ld, element type
+ * dtype); G is m x m FP64 row-major. */
+bk_status bk_gram(bk_ctx* ctx, int32_t dtype, int64_t d, int64_t m, const void* X, const void* Y,
+                  int64_t ld, double* G);
+
+/* X = G^{-1} S for a symmetric positive definite m x m G (the small factor/solve of
+ * each block-CG step): Cholesky of D^{-1/2} G D^{-1/2} (D = diag G) with diagonal
+ * pivoting, one warp per column of S. G, S, X are m x m FP64 row-major. Returns
+ * BK_BREAKDOWN if G is numerically rank deficient (a scaled pivot below 1e-14) or has
+ * a non-positive diagonal entry. 1 <= m <= 64. */
+bk_status bk_chol_solve(bk_ctx* ctx, int64_t m, const double* G, const double* S, double* X);
+
+/* Standard normals k = offset .. offset+n-1 of Philox4x32-10 stream `stream` with
+ * key `seed`, by Box-Muller, as defined for the sketch Omega:
+ *   block c = k / 2; counter (c mod 2^32, c / 2^32, stream, 0); key (seed mod 2^32,
+ *   seed / 2^32); u1 = ((x0>>5) 2^26 + (x1>>6) + 1/2) 2^-53, u2 likewise from x2, x3;
+ *   value = sqrt(-2 ln u1) cos(2 pi u2) for even k, sin for odd k.
+ * Omega (d x l) is entry k = j d + i of stream 3. out has n doubles. */
+bk_status bk_gaussian(bk_ctx* ctx, uint64_t seed, uint32_t stream, int64_t n, int64_t offset,
+                      double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BK_H */

@@ -1,0 +1,260 @@
+"""Python binding of the block-CG C ABI (include/bk.h): argument marshalling only.
+
+Every entry point passes raw pointers and sizes straight to libbk.so; all arithmetic
+runs in the library's CUDA kernels. Arrays may be torch tensors (CUDA or CPU) or
+NumPy arrays; CUDA tensors are passed as device pointers, everything else as host
+pointers (the library copies host arrays through its workspace). PyTorch is used
+only for device memory and the current CUDA stream.
+
+The library is required: importing this module without a built libbk.so raises
+ImportError (there is no CPU fallback). Build it with
+``python -m paper_2501_18717_gb300.build``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbk.so")
+
+BK_OK, BK_ERR_ARG, BK_ERR_CUDA, BK_ERR_OOM, BK_NOT_CONVERGED, BK_BREAKDOWN, BK_STAGNATED, BK_TIMEOUT, \
+    BK_ERR_UNSUPPORTED = range(9)
+BK_DENSE, BK_CSR = 0, 1
+BK_F64, BK_F32 = 0, 1
+BK_PREC_FP64, BK_PREC_FP32 = 0, 1
+
+EXPORTS = ("bk_default_opts", "bk_create", "bk_destroy", "bk_set_stream", "bk_status_string", "bk_last_error",
+           "bk_solve",
+           "bk_block_apply", "bk_gram", "bk_chol_solve", "bk_gaussian")
+
+
+class Operator(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dtype", ctypes.c_int32), ("rows", ctypes.c_int64),
+                ("cols", ctypes.c_int64), ("ld", ctypes.c_int64), ("vals", ctypes.c_void_p),
+                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("nnz", ctypes.c_int64)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_loads", ctypes.c_int32), ("sketch", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("inner", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("max_refine", ctypes.c_int32), ("check_every", ctypes.c_int32), ("profile", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("loads", ctypes.c_int32), ("refinements", ctypes.c_int32),
+                ("residual_loads", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("ms_kernel", ctypes.c_double * 8), ("launches", ctypes.c_int32 * 8),
+                ("kernel_launches", ctypes.c_int32)]
+
+    def as_dict(self):
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if not isinstance(v, (int, float)) else v
+        return out
+
+
+KERNEL_CLASSES = ("operator", "reduce", "alpha", "update_r", "beta", "update_p")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libbk.so is not built ({LIB_PATH}); run python -m paper_2501_18717_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    sig = {
+        "bk_default_opts": (None, [ctypes.POINTER(Opts)]),
+        "bk_create": (i32, [ctypes.POINTER(vp), ctypes.c_int, vp]),
+        "bk_destroy": (i32, [vp]),
+        "bk_set_stream": (i32, [vp, vp]),
+        "bk_status_string": (ctypes.c_char_p, [i32]),
+        "bk_last_error": (ctypes.c_char_p, [vp]),
+        "bk_solve": (i32, [vp, ctypes.POINTER(Operator), dbl, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
+        "bk_block_apply": (i32, [vp, ctypes.POINTER(Operator), dbl, i32, i64, vp, vp, i64, vp]),
+        "bk_gram": (i32, [vp, i32, i64, i64, vp, vp, i64, vp]),
+        "bk_chol_solve": (i32, [vp, i64, vp, vp, vp]),
+        "bk_gaussian": (i32, [vp, u64, ctypes.c_uint32, i64, i64, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+class BKError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status}) {detail}".rstrip())
+
+
+def status_string(s: int) -> str:
+    return _lib.bk_status_string(int(s)).decode()
+
+
+def _ptr(a):
+    """(pointer, keepalive) of a torch tensor or NumPy array (must be contiguous)."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if not (a.flags["C_CONTIGUOUS"] or a.flags["F_CONTIGUOUS"]):
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data, a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _dtype_code(a):
+    s = str(getattr(a, "dtype", ""))
+    if s.endswith("float64"):
+        return BK_F64
+    if s.endswith("float32"):
+        return BK_F32
+    raise TypeError(f"unsupported dtype {s}")
+
+
+def _current_stream(device):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream(device).cuda_stream
+    except Exception:  # noqa: BLE001 - torch is optional for host-only callers
+        pass
+    return None
+
+
+class Context:
+    """A bk_ctx bound to one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.device = device
+        h = ctypes.c_void_p()
+        st = _current_stream(device) if stream is None else stream
+        s = _lib.bk_create(ctypes.byref(h), int(device), st)
+        if s != BK_OK:
+            raise BKError(s, "bk_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def last_error(self) -> str:
+        return _lib.bk_last_error(self._h).decode()
+
+    def set_stream(self, stream):
+        s = _lib.bk_set_stream(self._h, stream)
+        if s != BK_OK:
+            raise BKError(s, "bk_set_stream")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.bk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class OperatorRef:
+    """A bk_operator plus references that keep its arrays alive."""
+
+    def __init__(self, op: Operator, keep):
+        self.op = op
+        self.keep = keep
+        self.d = op.rows
+
+
+def dense_operator(a) -> OperatorRef:
+    """A dense row-major d x d matrix (float64 or float32)."""
+    d = a.shape[0]
+    ld = a.stride(0) if hasattr(a, "stride") and callable(a.stride) else a.strides[0] // a.itemsize
+    p, k = _ptr(a)
+    op = Operator(BK_DENSE, _dtype_code(a), d, a.shape[1], ld, p, None, None, 0)
+    return OperatorRef(op, [k])
+
+
+def csr_operator(rowptr, colidx, vals) -> OperatorRef:
+    """A CSR matrix with int32 rowptr/colidx and float64/float32 values."""
+    d = rowptr.shape[0] - 1
+    pr, kr = _ptr(rowptr)
+    pc, kc = _ptr(colidx)
+    pv, kv = _ptr(vals)
+    op = Operator(BK_CSR, _dtype_code(vals), d, d, 0, pv, pr, pc, vals.shape[0])
+    return OperatorRef(op, [kr, kc, kv])
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    _lib.bk_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "inner" and isinstance(v, str):
+            v = {"fp64": BK_PREC_FP64, "fp32": BK_PREC_FP32}[v]
+        setattr(o, k, v)
+    return o
+
+
+def solve(ctx: Context, A: OperatorRef, mu: float, b, x, opts: Opts | None = None, check=True) -> Info:
+    """bk_solve: x <- (A + mu I)^{-1} b by randomized block-CG with FP64 refinement."""
+    info = Info()
+    pb, kb = _ptr(b)
+    px, kx = _ptr(x)
+    o = opts if opts is not None else default_opts()
+    s = _lib.bk_solve(ctx.handle, ctypes.byref(A.op), float(mu), pb, px, ctypes.byref(o), ctypes.byref(info))
+    if check and s not in (BK_OK,):
+        raise BKError(s, "bk_solve", ctx.last_error())
+    return info
+
+
+def block_apply(ctx: Context, A: OperatorRef, mu: float, P, Y, G, m: int, ld: int, dtype=None) -> None:
+    """bk_block_apply: Y = A P + mu P and G = P^T Y (column-major blocks, leading dim ld)."""
+    dt = _dtype_code(P) if dtype is None else dtype
+    pp, kp = _ptr(P)
+    py, ky = _ptr(Y)
+    pg, kg = _ptr(G)
+    s = _lib.bk_block_apply(ctx.handle, ctypes.byref(A.op), float(mu), dt, int(m), pp, py, int(ld), pg)
+    if s != BK_OK:
+        raise BKError(s, "bk_block_apply", ctx.last_error())
+
+
+def gram(ctx: Context, X, Y, G, d: int, m: int, ld: int) -> None:
+    """bk_gram: G = X^T Y for column-major d x m blocks."""
+    px, kx = _ptr(X)
+    py, ky = _ptr(Y)
+    pg, kg = _ptr(G)
+    s = _lib.bk_gram(ctx.handle, _dtype_code(X), int(d), int(m), px, py, int(ld), pg)
+    if s != BK_OK:
+        raise BKError(s, "bk_gram")
+
+
+def chol_solve(ctx: Context, G, S, X, m: int) -> int:
+    """bk_chol_solve: X = G^{-1} S (m x m, row-major FP64). Returns the status."""
+    pg, kg = _ptr(G)
+    ps, ks = _ptr(S)
+    px, kx = _ptr(X)
+    return _lib.bk_chol_solve(ctx.handle, int(m), pg, ps, px)
+
+
+def gaussian(ctx: Context, seed: int, stream: int, out, offset: int = 0) -> None:
+    """bk_gaussian: normals offset .. offset + len(out) - 1 of a Philox stream."""
+    po, ko = _ptr(out)
+    n = out.shape[0]
+    s = _lib.bk_gaussian(ctx.handle, int(seed), int(stream), int(n), int(offset), po)
+    if s != BK_OK:
+        raise BKError(s, "bk_gaussian")

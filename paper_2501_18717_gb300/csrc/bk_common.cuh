@@ -1,0 +1,131 @@
+// Shared declarations of the CUDA side of the block-CG library (device code and the
+// host launchers used by the C ABI). Nothing here is visible through include/bk.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bk {
+
+// Device-side control block of one inner block-CG solve. Written and read by the
+// step kernels so that the iteration needs no host round trip; the host reads it
+// every `check_every` block products.
+//
+// Race-free ownership: every field is written by exactly one kind of kernel, and no
+// kernel reads a field that its own launch writes (except where a stale read is
+// harmless, noted below).
+//   done_a, pending_x, loads  written by the alpha small-solve (CTA 0); loads is
+//                             read back only by the beta small-solve
+//   done_b, res               written by the beta small-solve (CTA 0)
+//   status                    written by whichever sets a done flag
+struct DevState {
+  int done_a;       // G invalid, or rank deficient (after applying its step)
+  int done_b;       // column-0 residual met its target, load cap, or S rank deficient
+  int pending_x;    // this step's alpha is valid: the x update must run
+  int loads;        // block products completed in this inner solve
+  int status;       // ST_* below
+  int max_loads;    // cap for this inner solve
+  double tol_abs;   // target on ||R[:,0]|| (column 0 starts with norm 1)
+  double res;       // latest ||R[:,0]|| from the recurrence
+};
+
+enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_LOADCAP = 3, ST_DEFLATED = 4 };
+
+// Padded block widths the kernels are compiled for (multiples of 4 for the 4x4
+// register blocks of the Gram kernels).
+constexpr int kMaxWidth = 36;
+inline int padded_width(int m) {
+  if (m <= 4) return 4;
+  if (m <= 8) return 8;
+  if (m <= 16) return 16;
+  if (m <= 24) return 24;
+  if (m <= 36) return 36;
+  return -1;
+}
+// Entries of one Gram partial: upper-triangular 4x4 blocks, 16 entries each.
+inline int gram_entries(int mp) {
+  int nb = mp / 4;
+  return nb * (nb + 1) / 2 * 16;
+}
+
+// ---------------------------------------------------------------- launchers
+// All launchers enqueue on `st` and return the launch status.
+
+// Y = A P + mu P and the per-CTA partials of G = P^T Y, CSR operator.
+cudaError_t launch_csr_spmm_gram(int is_f64, int mp, int64_t d, const int* rowptr, const int* colidx,
+                                 const void* vals, double mu, const void* P, void* Y, int64_t ld, int m,
+                                 double* parts, int nparts, const DevState* state, cudaStream_t st);
+int csr_spmm_gram_grid(int is_f64, int mp, int64_t d, int device);
+
+// Same for a dense row-major operator with leading dimension lda.
+cudaError_t launch_dense_gram(int is_f64, int mp, int64_t d, const void* A, int64_t lda, double mu,
+                              const void* P, void* Y, int64_t ld, int m, double* parts, int nparts,
+                              const DevState* state, cudaStream_t st);
+int dense_gram_grid(int is_f64, int mp, int64_t d, int device);
+
+// Partials of G = X^T Y.
+cudaError_t launch_gram(int is_f64, int mp, int64_t d, const void* X, const void* Y, int64_t ld, int m,
+                        double* parts, int nparts, cudaStream_t st);
+int gram_grid(int is_f64, int mp, int64_t d, int device);
+
+// Sum of partials (fixed order) into a full symmetric m x m FP64 matrix.
+cudaError_t launch_reduce_gram(int mp, int m, const double* parts, int nparts, double* out,
+                               const DevState* state, cudaStream_t st);
+
+// Small solves. mode 0 (alpha): X = G^{-1} S; mode 1 (beta): convergence test on
+// Snew and X = S^{-1} Snew. Writes the FP64 result and a padded copy in the
+// block precision (mp x mp, row-major) for the update kernels.
+// rank_tol: pivots of the unit-diagonal scaled matrix below it count as dependent.
+cudaError_t launch_small_alpha(int is_f64, int mp, int m, const double* G, const double* S, double* X,
+                               void* Xt, double rank_tol, DevState* state, cudaStream_t st);
+cudaError_t launch_small_beta(int is_f64, int mp, int m, const double* Sold, const double* Snew, double* X,
+                              void* Xt, double rank_tol, DevState* state, cudaStream_t st);
+// Stand-alone X = G^{-1} S (no state); status word set to 1 on breakdown.
+cudaError_t launch_chol_solve(int m, const double* G, const double* S, double* X, int* flag, cudaStream_t st);
+
+// R -= Y alpha with per-CTA partials of R^T R.
+cudaError_t launch_update_r(int is_f64, int mp, int64_t d, int m, const void* Y, void* R, int64_t ld,
+                            const void* alpha_t, double* parts, int nparts, const DevState* state,
+                            cudaStream_t st);
+int update_r_grid(int is_f64, int mp, int64_t d, int device);
+
+// x += P alpha[:,0] (FP64 accumulator) and, unless converged, P = R + P beta.
+// Also copies Snew into Sold (CTA 0) for the next step.
+cudaError_t launch_update_p(int is_f64, int mp, int64_t d, int m, const void* R, void* P, int64_t ld,
+                            const void* alpha_t, const void* beta_t, double* x, const double* Snew,
+                            double* Sold, const DevState* state, cudaStream_t st);
+
+// Start block of an inner solve: R[:,0] = r * scale, R[:,1:] = Omega, P = R, x = 0.
+cudaError_t launch_start_block(int is_f64, int64_t d, int m, int64_t ld, const double* r, double scale,
+                               const void* omega, void* R, void* P, double* x, cudaStream_t st);
+// Omega (d x l, column-major, leading dimension ld) from Philox stream 3, times `scale`.
+cudaError_t launch_omega(int is_f64, int64_t d, int l, int64_t ld, uint64_t seed, double scale, void* out,
+                         cudaStream_t st);
+// Standard normals of a stream (FP64).
+cudaError_t launch_gaussian(uint64_t seed, uint32_t stream, int64_t n, int64_t offset, double* out,
+                            cudaStream_t st);
+
+// FP64 residual r = b - (A x + mu x) and per-CTA partials of ||r||^2.
+cudaError_t launch_csr_residual(int vals_f64, int64_t d, const int* rowptr, const int* colidx,
+                                const void* vals, double mu, const double* x, const double* b, double* r,
+                                double* norm_parts, int nparts, cudaStream_t st);
+cudaError_t launch_dense_residual(int vals_f64, int64_t d, const void* A, int64_t lda, double mu,
+                                  const double* x, const double* b, double* r, double* norm_parts,
+                                  int nparts, cudaStream_t st);
+// x += a * y (FP64)
+cudaError_t launch_axpy(int64_t d, double a, const double* y, double* x, cudaStream_t st);
+// FP64 -> FP32 copy
+cudaError_t launch_to_f32(int64_t n, const double* in, float* out, cudaStream_t st);
+// FP32 -> FP64 copy
+cudaError_t launch_to_f64(int64_t n, const float* in, double* out, cudaStream_t st);
+// ||v||^2 partials (nparts CTAs of 256 threads)
+cudaError_t launch_norm2_parts(int64_t d, const double* v, double* parts, int nparts, cudaStream_t st);
+// Dense: FP64 -> FP32 copy of a d x d row-major matrix with leading dimension lda into lda32.
+cudaError_t launch_dense_to_f32(int64_t d, const double* in, int64_t lda, float* out, int64_t lda32,
+                                cudaStream_t st);
+// Reset the control block for a new inner solve.
+cudaError_t launch_init_state(DevState* state, int max_loads, double tol_abs, cudaStream_t st);
+// Norm partial count used by the residual launchers.
+int residual_parts(int64_t d);
+
+}  // namespace bk

@@ -1,0 +1,175 @@
+// Fused tall-skinny Gram accumulation G += X_tile^T Y_tile for a tile of rows staged in
+// shared memory (row-major, stride MP). Used by every kernel that produces a block and
+// needs its Gram matrix in the same pass (P^T Y after a block product, R^T R after the
+// residual update), so the blocks are never re-read for the Grams.
+//
+// Work split: the MP x MP result is cut into 4x4 register blocks; only the blocks on or
+// above the diagonal are formed (NT of them). Thread s owns block s mod NT and the tile
+// rows congruent to s / NT modulo NPH = blockDim / NT.
+//
+// Precision: FP64 tiles accumulate in FP64. FP32 tiles multiply and add in FP32 within
+// one tile (at most TM / NPH rows per thread) and carry the running sum across tiles as
+// an unevaluated FP32 pair (hi, lo) with Knuth's TwoSum, so the sum over the whole block
+// is formed with about twice FP32 precision; the per-CTA result is converted to FP64 and
+// the CTA partials are added in FP64 in a fixed order (deterministic).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bk {
+
+template <int MP>
+struct GramShape {
+  static constexpr int NB = MP / 4;
+  static constexpr int NT = NB * (NB + 1) / 2;
+  static constexpr int NE = NT * 16;
+};
+
+template <typename T, int MP>
+struct GramAcc;
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+template <int MP>
+struct GramAcc<float, MP> {
+  using S = GramShape<MP>;
+  int t, ph, nph, bi, bj;
+  bool active;
+  float hi[16], lo[16];
+
+  __device__ void init() {
+    nph = blockDim.x / S::NT;
+    t = threadIdx.x % S::NT;
+    ph = threadIdx.x / S::NT;
+    active = ph < nph;
+    int tt = t, r = 0;
+    while (tt >= S::NB - r) {
+      tt -= S::NB - r;
+      ++r;
+    }
+    bi = r;
+    bj = r + tt;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) hi[e] = lo[e] = 0.f;
+  }
+
+  __device__ void tile(const float* sX, const float* sY, int rows) {
+    if (!active) return;
+    float acc[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[e] = 0.f;
+    for (int r = ph; r < rows; r += nph) {
+      float4 x = *reinterpret_cast<const float4*>(sX + r * MP + 4 * bi);
+      float4 y = *reinterpret_cast<const float4*>(sY + r * MP + 4 * bj);
+      float xa[4] = {x.x, x.y, x.z, x.w};
+      float yb[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a * 4 + b] = fmaf(xa[a], yb[b], acc[a * 4 + b]);
+    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      float s, err;
+      two_sum(hi[e], acc[e], s, err);
+      hi[e] = s;
+      lo[e] = __fadd_rn(lo[e], err);
+    }
+  }
+
+  __device__ double value(int e) const { return (double)hi[e] + (double)lo[e]; }
+};
+
+template <int MP>
+struct GramAcc<double, MP> {
+  using S = GramShape<MP>;
+  int t, ph, nph, bi, bj;
+  bool active;
+  double hi[16];
+
+  __device__ void init() {
+    nph = blockDim.x / S::NT;
+    t = threadIdx.x % S::NT;
+    ph = threadIdx.x / S::NT;
+    active = ph < nph;
+    int tt = t, r = 0;
+    while (tt >= S::NB - r) {
+      tt -= S::NB - r;
+      ++r;
+    }
+    bi = r;
+    bj = r + tt;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) hi[e] = 0.0;
+  }
+
+  __device__ void tile(const double* sX, const double* sY, int rows) {
+    if (!active) return;
+    for (int r = ph; r < rows; r += nph) {
+      const double2* px = reinterpret_cast<const double2*>(sX + r * MP + 4 * bi);
+      const double2* py = reinterpret_cast<const double2*>(sY + r * MP + 4 * bj);
+      double2 x01 = px[0], x23 = px[1], y01 = py[0], y23 = py[1];
+      double xa[4] = {x01.x, x01.y, x23.x, x23.y};
+      double yb[4] = {y01.x, y01.y, y23.x, y23.y};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) hi[a * 4 + b] = fma(xa[a], yb[b], hi[a * 4 + b]);
+    }
+  }
+
+  __device__ double value(int e) const { return hi[e]; }
+};
+
+// Combine the phases of one CTA (fixed order) and write the CTA partial:
+// parts[e * nparts + cta] for e in [0, NE). sred needs nph * NT * 16 doubles and may
+// alias the tile buffers (the caller synchronises before calling).
+template <typename T, int MP>
+__device__ void gram_finish(const GramAcc<T, MP>& g, double* sred, double* parts, int nparts, int cta) {
+  using S = GramShape<MP>;
+  if (g.active) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) sred[(g.ph * S::NT + g.t) * 16 + e] = g.value(e);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < S::NE; idx += blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < g.nph; ++p) s += sred[p * S::NE + idx];
+    parts[(size_t)idx * nparts + cta] = s;
+  }
+}
+
+// Row `row` of a shared tile (stride MP) from MP register values.
+template <int MP>
+__device__ __forceinline__ void store_row(float* s, int row, const float (&v)[MP]) {
+  float4* p = reinterpret_cast<float4*>(s + row * MP);
+#pragma unroll
+  for (int q = 0; q < MP / 4; ++q) p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+template <int MP>
+__device__ __forceinline__ void store_row(double* s, int row, const double (&v)[MP]) {
+  double2* p = reinterpret_cast<double2*>(s + row * MP);
+#pragma unroll
+  for (int q = 0; q < MP / 2; ++q) p[q] = make_double2(v[2 * q], v[2 * q + 1]);
+}
+template <typename T, int MP>
+__device__ __forceinline__ void zero_row(T* s, int row) {
+#pragma unroll
+  for (int c = 0; c < MP; ++c) s[row * MP + c] = (T)0;
+}
+
+// Shared bytes a Gram-fused kernel needs: two tiles of TM rows, or the phase buffer.
+template <typename T, int MP>
+inline size_t gram_smem_bytes(int tm, int threads) {
+  size_t tiles = 2 * (size_t)tm * MP * sizeof(T);
+  int nph = threads / GramShape<MP>::NT;
+  size_t red = (size_t)nph * GramShape<MP>::NE * sizeof(double);
+  return tiles > red ? tiles : red;
+}
+
+}  // namespace bk

@@ -1,0 +1,336 @@
+// Block products with A_mu = A + mu I ("matrix-loads", Sec. 1.2) and the FP64 residual.
+//
+// k_csr_spmm_gram: Y = A P + mu P for CSR A, reading each matrix row once for all m
+//   columns (thread per row, m accumulators in registers), with G = P^T Y formed in
+//   the same pass from the row tile staged in shared memory (bk_tile.cuh).
+//   Blocks are column-major: for stencil-like sparsity neighbouring rows touch
+//   neighbouring columns, so every gather P[c][j] is coalesced across a warp.
+// k_dense_gram: the same for a dense row-major A (tiled over K in shared memory).
+// k_*_residual: r = b - A_mu x in FP64 from the stored values, with ||r||^2 partials.
+#include "bk_common.cuh"
+#include "bk_tile.cuh"
+
+namespace bk {
+namespace {
+
+__device__ __forceinline__ bool is_done(const DevState* s) { return s && (s->done_a | s->done_b); }
+
+int sm_count_ops(int device) {
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) n = 152;
+  return n;
+}
+
+// ------------------------------------------------------------------ CSR
+template <typename T, int MP, int TM>
+__global__ void __launch_bounds__(TM) k_csr_spmm_gram(int64_t d, const int* __restrict__ rowptr,
+                                                     const int* __restrict__ colidx, const T* __restrict__ vals,
+                                                     T mu, const T* __restrict__ P, T* __restrict__ Y, int64_t ld,
+                                                     int m, double* parts, int nparts, const DevState* state) {
+  if (is_done(state)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sX = reinterpret_cast<T*>(smem_raw);
+  T* sY = sX + TM * MP;
+  GramAcc<T, MP> g;
+  g.init();
+  int64_t ntiles = (d + TM - 1) / TM;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int64_t i = tile * TM + threadIdx.x;
+    if (i < d) {
+      T acc[MP];
+#pragma unroll
+      for (int c = 0; c < MP; ++c) acc[c] = (c < m) ? P[c * ld + i] : (T)0;
+      store_row<MP>(sX, threadIdx.x, acc);
+#pragma unroll
+      for (int c = 0; c < MP; ++c) acc[c] *= mu;
+      int k0 = rowptr[i], k1 = rowptr[i + 1];
+      for (int k = k0; k < k1; ++k) {
+        T v = vals[k];
+        const T* pj = P + colidx[k];
+#pragma unroll
+        for (int c = 0; c < MP; ++c)
+          if (c < m) acc[c] = fma(v, pj[c * ld], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < MP; ++c)
+        if (c < m) Y[c * ld + i] = acc[c];
+      store_row<MP>(sY, threadIdx.x, acc);
+    } else {
+      zero_row<T, MP>(sX, threadIdx.x);
+      zero_row<T, MP>(sY, threadIdx.x);
+    }
+    __syncthreads();
+    g.tile(sX, sY, TM);
+    __syncthreads();
+  }
+  gram_finish<T, MP>(g, reinterpret_cast<double*>(smem_raw), parts, nparts, blockIdx.x);
+}
+
+// ------------------------------------------------------------------ dense
+// CTA computes TMD rows x MP columns of Y. K is walked in chunks of KC: the A chunk
+// (TMD x KC, coalesced along K) and the P chunk (KC x MP, coalesced along K per
+// column) are staged in shared memory. Thread (r, cg) owns row r and the columns
+// cg, cg + CG, ... (CG = threads / TMD).
+template <typename T, int MP, int TMD, int KC, int NTH>
+__global__ void __launch_bounds__(NTH) k_dense_gram(int64_t d, const T* __restrict__ A, int64_t lda, T mu,
+                                                   const T* __restrict__ P, T* __restrict__ Y, int64_t ld, int m,
+                                                   double* parts, int nparts, const DevState* state) {
+  if (is_done(state)) return;
+  constexpr int CG = NTH / TMD;
+  constexpr int NC = (MP + CG - 1) / CG;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sA = reinterpret_cast<T*>(smem_raw);  // TMD x (KC + 1)
+  T* sP = sA + TMD * (KC + 1);             // KC x MP
+  T* sX = sP + KC * MP;                    // TMD x MP tiles for the Gram
+  T* sY = sX + TMD * MP;
+  GramAcc<T, MP> g;
+  g.init();
+  int r = threadIdx.x / CG, cg = threadIdx.x % CG;
+  int64_t ntiles = (d + TMD - 1) / TMD;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int64_t row0 = tile * TMD;
+    T acc[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) acc[q] = (T)0;
+    for (int64_t k0 = 0; k0 < d; k0 += KC) {
+      for (int idx = threadIdx.x; idx < TMD * KC; idx += NTH) {
+        int rr = idx / KC, kk = idx - rr * KC;
+        int64_t gr = row0 + rr, gk = k0 + kk;
+        sA[rr * (KC + 1) + kk] = (gr < d && gk < d) ? A[gr * lda + gk] : (T)0;
+      }
+      for (int idx = threadIdx.x; idx < KC * MP; idx += NTH) {
+        int c = idx / KC, kk = idx - c * KC;
+        int64_t gk = k0 + kk;
+        sP[kk * MP + c] = (c < m && gk < d) ? P[c * ld + gk] : (T)0;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < KC; ++kk) {
+        T a = sA[r * (KC + 1) + kk];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          int c = cg + q * CG;
+          if (c < MP) acc[q] = fma(a, sP[kk * MP + c], acc[q]);
+        }
+      }
+      __syncthreads();
+    }
+    int64_t gi = row0 + r;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      int c = cg + q * CG;
+      if (c < MP) {
+        T pv = (gi < d && c < m) ? P[c * ld + gi] : (T)0;
+        T yv = (gi < d && c < m) ? fma(mu, pv, acc[q]) : (T)0;
+        if (gi < d && c < m) Y[c * ld + gi] = yv;
+        sX[r * MP + c] = pv;
+        sY[r * MP + c] = yv;
+      }
+    }
+    __syncthreads();
+    g.tile(sX, sY, TMD);
+    __syncthreads();
+  }
+  gram_finish<T, MP>(g, reinterpret_cast<double*>(smem_raw), parts, nparts, blockIdx.x);
+}
+
+// ------------------------------------------------------------------ FP64 residuals
+constexpr int kResThreads = 256;
+
+__device__ __forceinline__ void block_sum_to(double v, double* parts, double* red) {
+  // deterministic CTA reduction: warp shuffle tree, then warp 0 over the warp sums
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    double s = (l < nw) ? red[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) parts[blockIdx.x] = s;
+  }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kResThreads) k_csr_residual(int64_t d, const int* __restrict__ rowptr,
+                                                             const int* __restrict__ colidx,
+                                                             const V* __restrict__ vals, double mu,
+                                                             const double* __restrict__ x,
+                                                             const double* __restrict__ b, double* r,
+                                                             double* norm_parts) {
+  __shared__ double red[32];
+  double ss = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = mu * x[i];
+    int k0 = rowptr[i], k1 = rowptr[i + 1];
+    for (int k = k0; k < k1; ++k) s = fma((double)vals[k], x[colidx[k]], s);
+    double ri = b[i] - s;
+    if (r) r[i] = ri;
+    ss = fma(ri, ri, ss);
+  }
+  block_sum_to(ss, norm_parts, red);
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kResThreads) k_dense_residual(int64_t d, const V* __restrict__ A, int64_t lda,
+                                                               double mu, const double* __restrict__ x,
+                                                               const double* __restrict__ b, double* r,
+                                                               double* norm_parts) {
+  __shared__ double red[32];
+  int lane = threadIdx.x & 31;
+  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double ss = 0.0;
+  for (int64_t i = warp; i < d; i += nwarps) {
+    double s = 0.0;
+    const V* row = A + i * lda;
+    for (int64_t k = lane; k < d; k += 32) s = fma((double)row[k], x[k], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    double ri = b[i] - (s + mu * x[i]);
+    if (lane == 0) {
+      if (r) r[i] = ri;
+      ss = fma(ri, ri, ss);
+    }
+  }
+  block_sum_to(ss, norm_parts, red);
+}
+
+// ------------------------------------------------------------------ dispatch helpers
+template <typename T, int MP>
+constexpr int csr_tm() {
+  return sizeof(T) == 4 ? 256 : 128;
+}
+
+template <typename T, int MP>
+cudaError_t csr_impl(int64_t d, const int* rowptr, const int* colidx, const void* vals, double mu, const void* P,
+                     void* Y, int64_t ld, int m, double* parts, int nparts, const DevState* state, cudaStream_t st) {
+  constexpr int TM = csr_tm<T, MP>();
+  size_t smem = gram_smem_bytes<T, MP>(TM, TM);
+  auto kern = k_csr_spmm_gram<T, MP, TM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<nparts, TM, smem, st>>>(d, rowptr, colidx, (const T*)vals, (T)mu, (const T*)P, (T*)Y, ld, m, parts, nparts,
+                                 state);
+  return cudaGetLastError();
+}
+
+template <typename T, int MP>
+struct DenseCfg {
+  static constexpr int TMD = 16, KC = 64, NTH = 128;
+  static size_t smem() {
+    size_t main = (size_t)(TMD * (KC + 1) + KC * MP + 2 * TMD * MP) * sizeof(T);
+    int nph = NTH / GramShape<MP>::NT;
+    size_t red = (size_t)nph * GramShape<MP>::NE * sizeof(double);
+    return main > red ? main : red;
+  }
+};
+
+template <typename T, int MP>
+cudaError_t dense_impl(int64_t d, const void* A, int64_t lda, double mu, const void* P, void* Y, int64_t ld, int m,
+                       double* parts, int nparts, const DevState* state, cudaStream_t st) {
+  using C = DenseCfg<T, MP>;
+  size_t smem = C::smem();
+  auto kern = k_dense_gram<T, MP, C::TMD, C::KC, C::NTH>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<nparts, C::NTH, smem, st>>>(d, (const T*)A, lda, (T)mu, (const T*)P, (T*)Y, ld, m, parts, nparts, state);
+  return cudaGetLastError();
+}
+
+#define BK_DISPATCH_MP2(mp, F, ...)        \
+  switch (mp) {                            \
+    case 4: return F<4>(__VA_ARGS__);      \
+    case 8: return F<8>(__VA_ARGS__);      \
+    case 16: return F<16>(__VA_ARGS__);    \
+    case 24: return F<24>(__VA_ARGS__);    \
+    case 36: return F<36>(__VA_ARGS__);    \
+    default: return cudaErrorInvalidValue; \
+  }
+
+template <int MP>
+cudaError_t csr_d(int64_t d, const int* rp, const int* ci, const void* v, double mu, const void* P, void* Y,
+                  int64_t ld, int m, double* parts, int np, const DevState* s, cudaStream_t st) {
+  return csr_impl<double, MP>(d, rp, ci, v, mu, P, Y, ld, m, parts, np, s, st);
+}
+template <int MP>
+cudaError_t csr_f(int64_t d, const int* rp, const int* ci, const void* v, double mu, const void* P, void* Y,
+                  int64_t ld, int m, double* parts, int np, const DevState* s, cudaStream_t st) {
+  return csr_impl<float, MP>(d, rp, ci, v, mu, P, Y, ld, m, parts, np, s, st);
+}
+template <int MP>
+cudaError_t dense_d(int64_t d, const void* A, int64_t lda, double mu, const void* P, void* Y, int64_t ld, int m,
+                    double* parts, int np, const DevState* s, cudaStream_t st) {
+  return dense_impl<double, MP>(d, A, lda, mu, P, Y, ld, m, parts, np, s, st);
+}
+template <int MP>
+cudaError_t dense_f(int64_t d, const void* A, int64_t lda, double mu, const void* P, void* Y, int64_t ld, int m,
+                    double* parts, int np, const DevState* s, cudaStream_t st) {
+  return dense_impl<float, MP>(d, A, lda, mu, P, Y, ld, m, parts, np, s, st);
+}
+
+}  // namespace
+
+int csr_spmm_gram_grid(int is_f64, int mp, int64_t d, int device) {
+  int tm = is_f64 ? 128 : 256;
+  int64_t ntiles = (d + tm - 1) / tm;
+  int cap = sm_count_ops(device) * (is_f64 ? 2 : 3);
+  if (ntiles < 1) ntiles = 1;
+  return (int)(ntiles < cap ? ntiles : cap);
+}
+
+int dense_gram_grid(int is_f64, int mp, int64_t d, int device) {
+  int64_t ntiles = (d + 15) / 16;
+  int cap = sm_count_ops(device) * 4;
+  if (ntiles < 1) ntiles = 1;
+  return (int)(ntiles < cap ? ntiles : cap);
+}
+
+cudaError_t launch_csr_spmm_gram(int is_f64, int mp, int64_t d, const int* rowptr, const int* colidx,
+                                 const void* vals, double mu, const void* P, void* Y, int64_t ld, int m,
+                                 double* parts, int nparts, const DevState* state, cudaStream_t st) {
+  if (is_f64) {
+    BK_DISPATCH_MP2(mp, csr_d, d, rowptr, colidx, vals, mu, P, Y, ld, m, parts, nparts, state, st);
+  } else {
+    BK_DISPATCH_MP2(mp, csr_f, d, rowptr, colidx, vals, mu, P, Y, ld, m, parts, nparts, state, st);
+  }
+}
+
+cudaError_t launch_dense_gram(int is_f64, int mp, int64_t d, const void* A, int64_t lda, double mu, const void* P,
+                              void* Y, int64_t ld, int m, double* parts, int nparts, const DevState* state,
+                              cudaStream_t st) {
+  if (is_f64) {
+    BK_DISPATCH_MP2(mp, dense_d, d, A, lda, mu, P, Y, ld, m, parts, nparts, state, st);
+  } else {
+    BK_DISPATCH_MP2(mp, dense_f, d, A, lda, mu, P, Y, ld, m, parts, nparts, state, st);
+  }
+}
+
+int residual_parts(int64_t d) {
+  int64_t g = (d + kResThreads - 1) / kResThreads;
+  if (g < 1) g = 1;
+  if (g > 1024) g = 1024;
+  return (int)g;
+}
+
+cudaError_t launch_csr_residual(int vals_f64, int64_t d, const int* rowptr, const int* colidx, const void* vals,
+                                double mu, const double* x, const double* b, double* r, double* norm_parts,
+                                int nparts, cudaStream_t st) {
+  if (vals_f64)
+    k_csr_residual<double><<<nparts, kResThreads, 0, st>>>(d, rowptr, colidx, (const double*)vals, mu, x, b, r,
+                                                           norm_parts);
+  else
+    k_csr_residual<float><<<nparts, kResThreads, 0, st>>>(d, rowptr, colidx, (const float*)vals, mu, x, b, r,
+                                                          norm_parts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_residual(int vals_f64, int64_t d, const void* A, int64_t lda, double mu, const double* x,
+                                  const double* b, double* r, double* norm_parts, int nparts, cudaStream_t st) {
+  if (vals_f64)
+    k_dense_residual<double><<<nparts, kResThreads, 0, st>>>(d, (const double*)A, lda, mu, x, b, r, norm_parts);
+  else
+    k_dense_residual<float><<<nparts, kResThreads, 0, st>>>(d, (const float*)A, lda, mu, x, b, r, norm_parts);
+  return cudaGetLastError();
+}
+
+}  // namespace bk

@@ -1,0 +1,103 @@
+// Gaussian sketch Omega on the device: Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
+// "Parallel random numbers: as easy as 1, 2, 3", SC'11) and the Box-Muller
+// transform. The paper draws Omega with independent standard normal entries
+// (Sec. 2.2.2, Eq. nystromBKI_def; Thm. main); the stream layout is given in bk.h.
+#include "bk_common.cuh"
+
+namespace bk {
+namespace {
+
+struct U4 {
+  uint32_t x0, x1, x2, x3;
+};
+
+__device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                       uint32_t k1) {
+  // Ten rounds; round constants and Weyl key increments from the SC'11 definition.
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// Both normals of Philox block c of `stream`.
+__device__ __forceinline__ void normal_pair(uint64_t seed, uint32_t stream, uint64_t c, double& z0,
+                                            double& z1) {
+  U4 w = philox10((uint32_t)c, (uint32_t)(c >> 32), stream, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const double two53 = 1.1102230246251565e-16;  // 2^-53
+  double u1 = ((double)(w.x0 >> 5) * 67108864.0 + (double)(w.x1 >> 6) + 0.5) * two53;
+  double u2 = ((double)(w.x2 >> 5) * 67108864.0 + (double)(w.x3 >> 6) + 0.5) * two53;
+  double r = sqrt(-2.0 * log(u1));
+  double ang = 6.283185307179586 * u2;  // 2 pi u2, the same product the host generator forms
+  z0 = r * cos(ang);
+  z1 = r * sin(ang);
+}
+
+__global__ void k_gaussian(uint64_t seed, uint32_t stream, int64_t n, int64_t offset, double* out) {
+  // thread per Philox block covering normals [offset, offset + n)
+  int64_t first_blk = offset >> 1;
+  int64_t last_blk = (offset + n - 1) >> 1;
+  for (int64_t blk = first_blk + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; blk <= last_blk;
+       blk += (int64_t)gridDim.x * blockDim.x) {
+    double z0, z1;
+    normal_pair(seed, stream, (uint64_t)blk, z0, z1);
+    int64_t k0 = 2 * blk, k1 = 2 * blk + 1;
+    if (k0 >= offset && k0 < offset + n) out[k0 - offset] = z0;
+    if (k1 >= offset && k1 < offset + n) out[k1 - offset] = z1;
+  }
+}
+
+template <typename T>
+__global__ void k_omega(int64_t d, int l, int64_t ld, uint64_t seed, double scale, T* out) {
+  int64_t n = d * (int64_t)l;
+  int64_t nblk = (n + 1) >> 1;
+  for (int64_t blk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; blk < nblk;
+       blk += (int64_t)gridDim.x * blockDim.x) {
+    double z0, z1;
+    normal_pair(seed, 3u, (uint64_t)blk, z0, z1);
+    int64_t k0 = 2 * blk, k1 = k0 + 1;
+    // entry k is (row k mod d, column k / d) of Omega
+    int64_t j0 = k0 / d, i0 = k0 - j0 * d;
+    out[j0 * ld + i0] = (T)(z0 * scale);
+    if (k1 < n) {
+      int64_t j1 = k1 / d, i1 = k1 - j1 * d;
+      out[j1 * ld + i1] = (T)(z1 * scale);
+    }
+  }
+}
+
+inline int grid_for(int64_t work, int threads) {
+  int64_t g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_gaussian(uint64_t seed, uint32_t stream, int64_t n, int64_t offset, double* out,
+                            cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t nblk = ((offset + n - 1) >> 1) - (offset >> 1) + 1;
+  k_gaussian<<<grid_for(nblk, 256), 256, 0, st>>>(seed, stream, n, offset, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_omega(int is_f64, int64_t d, int l, int64_t ld, uint64_t seed, double scale, void* out,
+                         cudaStream_t st) {
+  if (l <= 0 || d <= 0) return cudaSuccess;
+  int64_t nblk = (d * (int64_t)l + 1) >> 1;
+  if (is_f64)
+    k_omega<double><<<grid_for(nblk, 256), 256, 0, st>>>(d, l, ld, seed, scale, (double*)out);
+  else
+    k_omega<float><<<grid_for(nblk, 256), 256, 0, st>>>(d, l, ld, seed, scale, (float*)out);
+  return cudaGetLastError();
+}
+
+}  // namespace bk
