@@ -147,6 +147,8 @@ def test_edge_cases(bk, ctx):
     with pytest.raises(bk.BKError) as e:
         bk.solve(ctx, A, -1.0, b, x)
     assert e.value.status == bk.BK_ERR_ARG
+    # blocks wider than the compiled widths (m <= 36) on a system large enough to use them
+    big = np.diag(np.arange(1.0, 101.0))
     with pytest.raises(bk.BKError) as e:
-        bk.solve(ctx, A, 0.0, b, x, bk.default_opts(sketch=40))
+        bk.solve(ctx, bk.dense_operator(big), 0.0, np.ones(100), np.zeros(100), bk.default_opts(sketch=40))
     assert e.value.status == bk.BK_ERR_UNSUPPORTED
