@@ -46,7 +46,8 @@ typedef enum {
   BK_BREAKDOWN = 5,        /* a block Gram matrix lost positive definiteness */
   BK_STAGNATED = 6,        /* refinement stopped reducing the FP64 residual */
   BK_TIMEOUT = 7,          /* reserved: a device wait ran past its limit */
-  BK_ERR_UNSUPPORTED = 8   /* operator kind / dtype / width not built */
+  BK_ERR_UNSUPPORTED = 8,  /* operator kind / dtype / width not built */
+  BK_ERR_TOO_LARGE = 9     /* the call needs more than the fixed static scratch holds */
 } bk_status;
 
 typedef enum { BK_DENSE = 0, BK_CSR = 1 } bk_op_kind;
@@ -172,6 +173,33 @@ bk_status bk_chol_solve(bk_ctx* ctx, int64_t m, const double* G, const double* S
  * Omega (d x l) is entry k = j d + i of stream 3. out has n doubles. */
 bk_status bk_gaussian(bk_ctx* ctx, uint64_t seed, uint32_t stream, int64_t n, int64_t offset,
                       double* out);
+
+/* bk_block_apply without any device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot let a library allocate device memory,
+ * such as a host framework that owns every device allocation through its own pool and
+ * budget (a library cudaMalloc would be invisible to it), or a latency-sensitive caller
+ * that cannot afford the device-wide synchronisation a cudaMalloc or cudaFree implies.
+ *
+ * It computes the same Y = A P + mu P and G = P^T Y as bk_block_apply, with the same
+ * kernels and launch shape, but takes no context and allocates nothing:
+ *   - every array (A's arrays, P, Y, G) must be device memory of the current device
+ *     (BK_ERR_ARG otherwise): there is no staging copy;
+ *   - A->dtype must equal dtype (BK_ERR_UNSUPPORTED otherwise): there is no converted
+ *     copy of the values;
+ *   - the Gram partials use a fixed scratch array of 4 MiB (2^19 doubles) compiled into
+ *     the library as a __device__ variable. Each device that loads the library holds it
+ *     until the process exits. A call whose partials would not fit (more CTAs times
+ *     Gram entries than 2^19) returns BK_ERR_TOO_LARGE; on GB300 every supported size
+ *     fits.
+ * The first call on a device looks up the scratch address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. All calls share
+ * the scratch, so calls whose kernels overlap on the GPU (different streams or host
+ * threads, same device) race on it and must be serialised by the caller. Each call
+ * rewrites every partial it reads, so no clearing is needed. Work is enqueued on
+ * `cuda_stream` (a cudaStream_t, NULL for the legacy default stream) and the call
+ * returns after synchronising that stream. 1 <= m <= 36. */
+bk_status bk_block_apply_static(const bk_operator* A, double mu, int32_t dtype, int64_t m, const void* P,
+                                void* Y, int64_t ld, double* G, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -21,14 +21,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbk.so")
 
 BK_OK, BK_ERR_ARG, BK_ERR_CUDA, BK_ERR_OOM, BK_NOT_CONVERGED, BK_BREAKDOWN, BK_STAGNATED, BK_TIMEOUT, \
-    BK_ERR_UNSUPPORTED = range(9)
+    BK_ERR_UNSUPPORTED, BK_ERR_TOO_LARGE = range(10)
 BK_DENSE, BK_CSR = 0, 1
 BK_F64, BK_F32 = 0, 1
 BK_PREC_FP64, BK_PREC_FP32 = 0, 1
 
 EXPORTS = ("bk_default_opts", "bk_create", "bk_destroy", "bk_set_stream", "bk_status_string", "bk_last_error",
            "bk_solve",
-           "bk_block_apply", "bk_gram", "bk_chol_solve", "bk_gaussian")
+           "bk_block_apply", "bk_gram", "bk_chol_solve", "bk_gaussian", "bk_block_apply_static")
 
 
 class Operator(ctypes.Structure):
@@ -77,6 +77,7 @@ def _load():
         "bk_gram": (i32, [vp, i32, i64, i64, vp, vp, i64, vp]),
         "bk_chol_solve": (i32, [vp, i64, vp, vp, vp]),
         "bk_gaussian": (i32, [vp, u64, ctypes.c_uint32, i64, i64, vp]),
+        "bk_block_apply_static": (i32, [ctypes.POINTER(Operator), dbl, i32, i64, vp, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -258,3 +259,14 @@ def gaussian(ctx: Context, seed: int, stream: int, out, offset: int = 0) -> None
     s = _lib.bk_gaussian(ctx.handle, int(seed), int(stream), int(n), int(offset), po)
     if s != BK_OK:
         raise BKError(s, "bk_gaussian")
+
+
+def block_apply_static(A: OperatorRef, mu: float, P, Y, G, m: int, ld: int, stream=None, dtype=None) -> int:
+    """bk_block_apply_static: bk_block_apply without device allocation (device arrays
+    only; scratch in a fixed static array shared by all calls on a device). Returns the
+    status; callers that cannot allocate device memory use this entry point."""
+    dt = _dtype_code(P) if dtype is None else dtype
+    pp, kp = _ptr(P)
+    py, ky = _ptr(Y)
+    pg, kg = _ptr(G)
+    return _lib.bk_block_apply_static(ctypes.byref(A.op), float(mu), dt, int(m), pp, py, int(ld), pg, stream)

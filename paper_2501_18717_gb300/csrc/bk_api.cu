@@ -249,6 +249,7 @@ const char* bk_status_string(bk_status s) {
     case BK_STAGNATED: return "refinement stagnated";
     case BK_TIMEOUT: return "device wait timed out";
     case BK_ERR_UNSUPPORTED: return "unsupported operator, dtype or block width";
+    case BK_ERR_TOO_LARGE: return "problem exceeds the fixed static scratch";
   }
   return "unknown status";
 }
