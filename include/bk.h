@@ -16,8 +16,12 @@
  *     copies host arrays through its own workspace. Arrays are borrowed for the call
  *     only; the caller keeps ownership. The library owns the context's workspace.
  *   - Layout: dense matrices are row-major with leading dimension ld (>= cols).
- *     Block vectors (d x m) are column-major with leading dimension ld (>= d).
- *     CSR uses int32 rowptr (d+1 entries, rowptr[0] = 0) and int32 colidx.
+ *     Block vectors (d x m) are stored in panels of four columns: element (i, c) is at
+ *     offset ((c / 4) * ld + i) * 4 + c % 4 (ld >= d rows per panel), so each row of a
+ *     panel is one 16-byte (FP32) or 32-byte (FP64) vector. Columns m .. 4*ceil(m/4)-1
+ *     of the last panel are padding: they are read, must hold finite values, and are
+ *     written as zeros. CSR uses int32 rowptr (d+1 entries, rowptr[0] = 0) and int32
+ *     colidx.
  *   - Streams: work is ordered on the context's stream. Each call returns after its
  *     results are complete (it synchronises that stream).
  *   - Errors: functions return a bk_status and never throw. On BK_ERR_* the outputs
@@ -146,15 +150,15 @@ bk_status bk_solve(bk_ctx* ctx, const bk_operator* A, double mu, const double* b
 
 /* One block product with its Gram matrix (one "matrix-load", Sec. 1.2):
  *   Y = A P + mu P  and  G = P^T Y  (m x m, FP64, row-major).
- * P and Y are d x m column-major with leading dimension ld, element type `dtype`
+ * P and Y are d x m blocks in the panel layout above (leading dimension ld), element type `dtype`
  * (BK_F64 or BK_F32; for BK_F32 the operator values are rounded to FP32 first if
  * they are FP64). 1 <= m <= 64. G accumulates FP32 products in FP32 over row tiles
  * and in FP64 across tiles when dtype is BK_F32. */
 bk_status bk_block_apply(bk_ctx* ctx, const bk_operator* A, double mu, int32_t dtype, int64_t m,
                          const void* P, void* Y, int64_t ld, double* G);
 
-/* G = X^T Y for d x m column-major blocks X, Y (leading dimension ld, element type
- * dtype); G is m x m FP64 row-major. */
+/* G = X^T Y for d x m blocks X, Y in the panel layout (leading dimension ld, element
+ * type dtype); G is m x m FP64 row-major. */
 bk_status bk_gram(bk_ctx* ctx, int32_t dtype, int64_t d, int64_t m, const void* X, const void* Y,
                   int64_t ld, double* G);
 

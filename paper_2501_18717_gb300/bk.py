@@ -223,8 +223,26 @@ def solve(ctx: Context, A: OperatorRef, mu: float, b, x, opts: Opts | None = Non
     return info
 
 
+def to_panels(B, ld=None):
+    """A d x m NumPy block as the library's panel layout: array (ceil(m/4), ld, 4) with
+    element (i, c) at [c // 4, i, c % 4] and zero padding rows/columns."""
+    d, m = B.shape
+    ld = d if ld is None else ld
+    nq = (m + 3) // 4
+    out = np.zeros((nq, ld, 4), dtype=B.dtype)
+    for c in range(m):
+        out[c // 4, :d, c % 4] = B[:, c]
+    return out
+
+
+def from_panels(Pn, d, m):
+    """The d x m block held in a panel-layout array (inverse of to_panels)."""
+    Pn = np.asarray(Pn)
+    return np.stack([Pn[c // 4, :d, c % 4] for c in range(m)], axis=1)
+
+
 def block_apply(ctx: Context, A: OperatorRef, mu: float, P, Y, G, m: int, ld: int, dtype=None) -> None:
-    """bk_block_apply: Y = A P + mu P and G = P^T Y (column-major blocks, leading dim ld)."""
+    """bk_block_apply: Y = A P + mu P and G = P^T Y (panel-layout blocks, leading dim ld)."""
     dt = _dtype_code(P) if dtype is None else dtype
     pp, kp = _ptr(P)
     py, ky = _ptr(Y)
@@ -235,7 +253,7 @@ def block_apply(ctx: Context, A: OperatorRef, mu: float, P, Y, G, m: int, ld: in
 
 
 def gram(ctx: Context, X, Y, G, d: int, m: int, ld: int) -> None:
-    """bk_gram: G = X^T Y for column-major d x m blocks."""
+    """bk_gram: G = X^T Y for d x m blocks in the panel layout."""
     px, kx = _ptr(X)
     py, ky = _ptr(Y)
     pg, kg = _ptr(G)

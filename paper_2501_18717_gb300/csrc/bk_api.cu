@@ -366,7 +366,7 @@ bk_status bk_gram(bk_ctx* c, int32_t dtype, int64_t d, int64_t m, const void* X,
   if (mp < 0 || m > bk::kMaxWidth) return BK_ERR_UNSUPPORTED;
   BK_CK(cudaSetDevice(c->device));
   size_t es = dtype_size(dtype);
-  size_t bytes = ((size_t)(m - 1) * ld + d) * es;
+  size_t bytes = ((size_t)((m + 3) / 4 - 1) * ld + d) * 4 * es;  // panel layout
   const void *x = nullptr, *y = nullptr;
   BK_CK(stage_in(c, WS_TMP_IN, X, bytes, &x));
   BK_CK(stage_in(c, WS_TMP_G, Y, bytes, &y));
@@ -404,7 +404,7 @@ bk_status bk_block_apply(bk_ctx* c, const bk_operator* A, double mu, int32_t dty
   BK_CK(inner_values(c, o, is64, &vin, &lda_in));
   int64_t d = o.d;
   size_t es = dtype_size(dtype);
-  size_t bytes = ((size_t)(m - 1) * ld + d) * es;
+  size_t bytes = ((size_t)((m + 3) / 4 - 1) * ld + d) * 4 * es;  // panel layout
   const void* p = nullptr;
   BK_CK(stage_in(c, WS_TMP_IN, P, bytes, &p));
   bool ydev = is_device_ptr(Y);
@@ -470,12 +470,13 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
   // workspace
   const int64_t ld = (d + 31) & ~int64_t(31);
   const size_t es = is64 ? 8 : 4;
-  const size_t blk = (size_t)ld * m * es;
+  const int nq = (m + 3) / 4;  // panels of four columns
+  const size_t blk = (size_t)ld * 4 * nq * es;
   SolveBufs w;
   BK_CK(ws_get(c, WS_P, blk, &w.P));
   BK_CK(ws_get(c, WS_R, blk, &w.R));
   BK_CK(ws_get(c, WS_Y, blk, &w.Y));
-  BK_CK(ws_get(c, WS_OMEGA, (size_t)ld * (m > 1 ? m - 1 : 1) * es, &w.omega));
+  BK_CK(ws_get(c, WS_OMEGA, blk, &w.omega));
   BK_CK(ws_get(c, WS_XIN, (size_t)d * 8, (void**)&w.xin));
   BK_CK(ws_get(c, WS_X64, (size_t)d * 8, (void**)&w.x64));
   BK_CK(ws_get(c, WS_R64, (size_t)d * 8, (void**)&w.r64));
@@ -502,6 +503,7 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
 
   // Omega once per solve; its columns are scaled to unit expected norm (the Krylov
   // space, and so the column-0 iterate, does not depend on column scaling).
+  BK_CK(cudaMemsetAsync(w.omega, 0, blk, st));  // column 0 and padding columns stay zero
   BK_CK(bk::launch_omega(is64, d, m - 1, ld, opts.seed, 1.0 / std::sqrt((double)d), w.omega, st));
   BK_CK(cudaMemsetAsync(w.x64, 0, (size_t)d * 8, st));
   BK_CK(cudaMemcpyAsync(w.r64, bd, (size_t)d * 8, cudaMemcpyDeviceToDevice, st));

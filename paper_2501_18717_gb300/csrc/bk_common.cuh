@@ -98,7 +98,8 @@ cudaError_t launch_update_p(int is_f64, int mp, int64_t d, int m, const void* R,
 // Start block of an inner solve: R[:,0] = r * scale, R[:,1:] = Omega, P = R, x = 0.
 cudaError_t launch_start_block(int is_f64, int64_t d, int m, int64_t ld, const double* r, double scale,
                                const void* omega, void* R, void* P, double* x, cudaStream_t st);
-// Omega (d x l, column-major, leading dimension ld) from Philox stream 3, times `scale`.
+// Omega (d x l) from Philox stream 3, times `scale`, written as columns 1..l of a panel
+// block with leading dimension ld (the caller zeroes column 0 and the padding).
 cudaError_t launch_omega(int is_f64, int64_t d, int l, int64_t ld, uint64_t seed, double scale, void* out,
                          cudaStream_t st);
 // Standard normals of a stream (FP64).

@@ -157,10 +157,62 @@ __device__ __forceinline__ void store_row(double* s, int row, const double (&v)[
 #pragma unroll
   for (int q = 0; q < MP / 2; ++q) p[q] = make_double2(v[2 * q], v[2 * q + 1]);
 }
+// Four consecutive columns (chunk q) of row `row` as one 16-byte store (FP32) or two
+// (FP64); conflict-free when consecutive threads store consecutive rows.
+template <int MP>
+__device__ __forceinline__ void store4(float* s, int row, int q, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(s + row * MP + 4 * q) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <int MP>
+__device__ __forceinline__ void store4(double* s, int row, int q, const double (&v)[4]) {
+  double2* p = reinterpret_cast<double2*>(s + row * MP + 4 * q);
+  p[0] = make_double2(v[0], v[1]);
+  p[1] = make_double2(v[2], v[3]);
+}
 template <typename T, int MP>
 __device__ __forceinline__ void zero_row(T* s, int row) {
 #pragma unroll
   for (int c = 0; c < MP; ++c) s[row * MP + c] = (T)0;
+}
+
+// ---------------------------------------------------------------- block layout
+// A d x m block is stored as panels of four columns: element (i, c) lives at
+// ((c / 4) * ld + i) * 4 + c % 4, so one row of a panel is one 16-byte (FP32) or
+// 32-byte (FP64) vector and consecutive rows are contiguous. Columns m..4*ceil(m/4)-1
+// of the last panel are padding and hold zeros in every block the library writes.
+template <typename T>
+__device__ __forceinline__ const T* panel_row(const T* base, int64_t ld, int q, int64_t i) {
+  return base + ((int64_t)q * ld + i) * 4;
+}
+template <typename T>
+__device__ __forceinline__ T* panel_row(T* base, int64_t ld, int q, int64_t i) {
+  return base + ((int64_t)q * ld + i) * 4;
+}
+__device__ __forceinline__ void ldg4(const float* p, float* v) {
+  float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ldg4(const double* p, double* v) {
+  double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+// plain (coherent) load for blocks the same kernel also writes
+__device__ __forceinline__ void ld4(const float* p, float* v) {
+  float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* v) {
+  double2 a = reinterpret_cast<const double2*>(p)[0];
+  double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
 
 // Shared bytes a Gram-fused kernel needs: two tiles of TM rows, or the phase buffer.

@@ -14,7 +14,7 @@
 namespace bk {
 namespace {
 
-constexpr int kUpdThreads = 256;
+constexpr int kUpdThreads = 128;
 
 __device__ __forceinline__ bool is_done(const DevState* s) { return s && (s->done_a | s->done_b); }
 
@@ -32,10 +32,15 @@ __global__ void __launch_bounds__(TM) k_gram(int64_t d, const T* __restrict__ X,
     int64_t i = tile * TM + threadIdx.x;
     T vx[MP], vy[MP];
 #pragma unroll
-    for (int c = 0; c < MP; ++c) {
-      bool ok = (i < d) && (c < m);
-      vx[c] = ok ? X[c * ld + i] : (T)0;
-      vy[c] = ok ? Y[c * ld + i] : (T)0;
+    for (int q = 0; q < MP / 4; ++q) {
+      bool ok = (i < d) && (4 * q < m);
+      if (ok) {
+        ldg4(panel_row(X, ld, q, i), vx + 4 * q);
+        ldg4(panel_row(Y, ld, q, i), vy + 4 * q);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) vx[4 * q + u] = vy[4 * q + u] = (T)0;
+      }
     }
     store_row<MP>(sX, threadIdx.x, vx);
     store_row<MP>(sY, threadIdx.x, vy);
@@ -79,14 +84,13 @@ __global__ void k_reduce_gram(int m, const double* __restrict__ parts, int npart
 
 // ------------------------------------------------------------------ small solves
 // The m x m systems G alpha = S and S beta = S' of each step are solved by a Cholesky
-// factorisation of the unit-diagonal scaled matrix D^{-1/2} M D^{-1/2} with diagonal
-// pivoting, by one warp per right-hand-side column (every CTA factors the same matrix
-// in the same order, so all agree on the pivots). The factorisation stops at the first
-// pivot below rank_tol: the remaining columns are numerically in the span of the
-// chosen ones, and the solution is taken on the chosen columns only (zero rows
-// elsewhere). For G = P^T A_mu P this keeps X += P alpha the Galerkin update over
-// span(P) when the block has become rank deficient (Sec. 3.2: blocks can lose rank
-// even in exact arithmetic).
+// factorisation of the unit-diagonal scaled matrix D^{-1/2} M D^{-1/2}, one CTA per
+// right-hand-side column (every CTA factors the same matrix in the same order, so all
+// agree on which columns are kept). A column whose pivot falls below rank_tol is
+// numerically in the span of the columns before it; it is dropped and the solution
+// is taken on the kept columns only (zero rows elsewhere). For G = P^T A_mu P this
+// keeps X += P alpha the Galerkin update over span(P) when the block has become rank
+// deficient (Sec. 3.2: blocks can lose rank even in exact arithmetic).
 constexpr int kSmallMax = 64;
 constexpr int kLds = kSmallMax + 1;
 
@@ -94,135 +98,144 @@ struct SmallShared {
   double W[kSmallMax * kLds];
   double z[kSmallMax];
   double dscale[kSmallMax];
+  double invd[kSmallMax];  // 1 / L[k][k]
   int perm[kSmallMax];
 };
 
-// Returns the numerical rank (0..m), or -1 if M has a non-positive or non-finite
-// diagonal entry. On return the lower triangle of W[0:r, 0:r] holds L of the scaled,
-// permuted matrix.
-__device__ int warp_pivoted_cholesky(SmallShared& sh, int m, double rank_tol) {
-  int lane = threadIdx.x & 31;
+constexpr int kSmallThreads = 128;
+
+// 1/sqrt(x) for a positive normal FP64 x: an FP32 estimate of the argument brought
+// into [1, 4) by an exact power-of-two scaling, then two Newton steps in FP64
+// (r <- r (3 - x r^2) / 2 converges quadratically: about 1e-7 -> 1e-14 -> rounding).
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  const int e = ((__double2hiint(x) >> 20) & 0x7ff) - 1023;
+  const int h = e >> 1;  // floor(e / 2)
+  const double xs = x * __hiloint2double((1023 - 2 * h) << 20, 0);
+  double r = (double)rsqrtf((float)xs) * __hiloint2double((1023 - h) << 20, 0);
+  r = r * fma(-0.5 * x, r * r, 1.5);
+  r = r * fma(-0.5 * x, r * r, 1.5);
+  return r;
+}
+
+// On this part an FP64 instruction has a 64-cycle latency, a single warp issues at
+// most one FP64 instruction per 64 cycles, and a square root or division is a
+// dependent chain of several hundred cycles, so the factorisation is organised around
+// its dependency chain: no pivot search (comparisons are FP64 instructions too), one
+// thread forms 1/sqrt(pivot) by Newton steps, and the trailing update is spread over
+// four warps (four SM sub-partitions).
+//
+// Cholesky of the unit-diagonal scaled matrix in the given column order; a pivot at
+// or below rank_tol marks column k as numerically in the span of the kept columns
+// before it: its row and column are dropped (flag keep[k] = 0) and the factorisation
+// continues. Returns the number of kept columns, or -1 for a non-positive or
+// non-finite diagonal entry. On return the lower triangle of W holds L on the kept
+// rows/columns (zeros elsewhere) and invd[k] = 1 / L[k][k] (0 for dropped columns).
+__device__ int block_cholesky_skip(SmallShared& sh, int m, double rank_tol) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kSmallThreads / 32;
   double* W = sh.W;
-  bool bad = false;
-  for (int i = lane; i < m; i += 32) {
-    double g = W[i * kLds + i];
-    bad |= !(g > 0.0) || !isfinite(g);
-    sh.dscale[i] = bad ? 1.0 : sqrt(g);
-    sh.perm[i] = i;
+  __shared__ int s_bad, s_rank;
+  if (tid == 0) {
+    s_bad = 0;
+    s_rank = 0;
   }
-  if (__any_sync(0xffffffffu, bad)) return -1;
-  __syncwarp();
-  for (int idx = lane; idx < m * m; idx += 32) {
-    int r = idx / m, c = idx - r * m;
-    W[r * kLds + c] /= sh.dscale[r] * sh.dscale[c];
+  __syncthreads();
+  for (int i = tid; i < m; i += kSmallThreads) {
+    const double g = W[i * kLds + i];
+    const bool bad = !(g > 0.0) || !isfinite(g);
+    if (bad) s_bad = 1;
+    const double r = bad ? 1.0 : rsqrt_newton(g);  // D^{-1/2}
+    sh.z[i] = r;
+    sh.dscale[i] = bad ? 1.0 : g * r;  // sqrt(g)
   }
+  __syncthreads();
+  if (s_bad) return -1;
+  for (int idx = tid; idx < m * m; idx += kSmallThreads) {
+    const int r = idx / m, c = idx - r * m;
+    W[r * kLds + c] *= sh.z[r] * sh.z[c];
+  }
+  __syncthreads();
   for (int k = 0; k < m; ++k) {
-    __syncwarp();
-    // pivot: largest remaining diagonal, ties to the smallest index
-    double best = -1.0;
-    int bi = k;
-    for (int i = k + lane; i < m; i += 32) {
-      double v = W[i * kLds + i];
-      if (v > best) {
-        best = v;
-        bi = i;
+    if (tid == 0) {
+      const double x = W[k * kLds + k];
+      const bool keep = x > rank_tol;
+      double r = 0.0;
+      if (keep) {
+        r = rsqrt_newton(x);
+        s_rank += 1;
+      }
+      W[k * kLds + k] = keep ? x * r : 0.0;
+      sh.invd[k] = r;
+      sh.perm[k] = keep;
+    }
+    __syncthreads();
+    const double inv = sh.invd[k];  // 0 drops the column: L[:,k] = 0, no trailing update
+    for (int i = k + 1 + tid; i < m; i += kSmallThreads) W[i * kLds + k] *= inv;
+    __syncthreads();
+    if (inv != 0.0) {
+      for (int i = k + 1 + warp; i < m; i += NW) {
+        const double lik = W[i * kLds + k];
+        for (int j = k + 1 + lane; j <= i; j += 32) W[i * kLds + j] = fma(-lik, W[j * kLds + k], W[i * kLds + j]);
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-      }
-    }
-    if (!(best > rank_tol)) return k;
-    if (bi != k) {
-      for (int j = lane; j < m; j += 32) {
-        double t = W[k * kLds + j];
-        W[k * kLds + j] = W[bi * kLds + j];
-        W[bi * kLds + j] = t;
-      }
-      __syncwarp();
-      for (int i = lane; i < m; i += 32) {
-        double t = W[i * kLds + k];
-        W[i * kLds + k] = W[i * kLds + bi];
-        W[i * kLds + bi] = t;
-      }
-      if (lane == 0) {
-        int t = sh.perm[k];
-        sh.perm[k] = sh.perm[bi];
-        sh.perm[bi] = t;
-      }
-      __syncwarp();
-    }
-    double lkk = sqrt(W[k * kLds + k]);
-    double inv = 1.0 / lkk;
-    __syncwarp();
-    for (int i = k + 1 + lane; i < m; i += 32) W[i * kLds + k] *= inv;
-    __syncwarp();
-    if (lane == 0) W[k * kLds + k] = lkk;
-    // trailing update, kept symmetric so later pivot swaps see both triangles
-    for (int i = k + 1 + lane; i < m; i += 32) {
-      double lik = W[i * kLds + k];
-      for (int j = k + 1; j <= i; ++j) {
-        double v = fma(-lik, W[j * kLds + k], W[i * kLds + j]);
-        W[i * kLds + j] = v;
-        W[j * kLds + i] = v;
-      }
-    }
+    __syncthreads();
   }
-  __syncwarp();
-  return m;
+  return s_rank;
 }
 
-// z <- L^{-T} L^{-1} z on the leading r x r factor, one warp.
-__device__ void warp_chol_apply(const double* L, double* z, int r) {
-  int lane = threadIdx.x & 31;
-  for (int k = 0; k < r; ++k) {
+// z <- L^+ applied twice (L^{-T} L^{-1} on the kept columns, zero on dropped ones),
+// warp 0; invd holds 1 / L[k][k] (0 for dropped columns).
+__device__ void chol_apply_warp0(const double* L, const double* invd, double* z, int m) {
+  if ((threadIdx.x >> 5) == 0) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < m; ++k) {
+      __syncwarp();
+      const double zk = z[k] * invd[k];
+      __syncwarp();
+      if (lane == 0) z[k] = zk;
+      for (int i = k + 1 + lane; i < m; i += 32) z[i] = fma(-L[i * kLds + k], zk, z[i]);
+    }
+    for (int k = m - 1; k >= 0; --k) {
+      __syncwarp();
+      const double zk = z[k] * invd[k];
+      __syncwarp();
+      if (lane == 0) z[k] = zk;
+      for (int i = lane; i < k; i += 32) z[i] = fma(-L[k * kLds + i], zk, z[i]);
+    }
     __syncwarp();
-    double zk = z[k] / L[k * kLds + k];
-    __syncwarp();
-    if (lane == 0) z[k] = zk;
-    for (int i = k + 1 + lane; i < r; i += 32) z[i] = fma(-L[i * kLds + k], zk, z[i]);
   }
-  for (int k = r - 1; k >= 0; --k) {
-    __syncwarp();
-    double zk = z[k] / L[k * kLds + k];
-    __syncwarp();
-    if (lane == 0) z[k] = zk;
-    for (int i = lane; i < k; i += 32) z[i] = fma(-L[k * kLds + i], zk, z[i]);
-  }
-  __syncwarp();
+  __syncthreads();
 }
 
-// CTA j (one warp): column j of X = M^+ RHS on the kept columns; the result (original
-// order) is left in sh.z[0:m]. Returns the rank (-1: invalid diagonal).
+// CTA j: column j of X = M^+ RHS on the kept columns (zero rows on dropped ones); the
+// result is left in sh.z[0:m]. Returns the number of kept columns (-1: invalid diagonal).
 __device__ int small_solve_column(const double* M, const double* RHS, int m, int j, double rank_tol,
                                   SmallShared& sh) {
-  int lane = threadIdx.x & 31;
-  for (int idx = lane; idx < m * m; idx += 32) {
-    int r = idx / m, c = idx - r * m;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < m * m; idx += kSmallThreads) {
+    const int r = idx / m, c = idx - r * m;
     sh.W[r * kLds + c] = M[idx];
   }
-  __syncwarp();
-  int rank = warp_pivoted_cholesky(sh, m, rank_tol);
+  __syncthreads();
+  const int rank = block_cholesky_skip(sh, m, rank_tol);
   if (rank <= 0) return rank;
+  // the scaled system: (D^{-1/2} M D^{-1/2}) (D^{1/2} x) = D^{-1/2} rhs, D^{-1/2} = 1/dscale
   __shared__ double y[kSmallMax];
-  for (int i = lane; i < rank; i += 32) y[i] = RHS[sh.perm[i] * m + j] / sh.dscale[sh.perm[i]];
-  warp_chol_apply(sh.W, y, rank);
-  for (int i = lane; i < m; i += 32) sh.z[i] = 0.0;
-  __syncwarp();
-  for (int i = lane; i < rank; i += 32) sh.z[sh.perm[i]] = y[i] / sh.dscale[sh.perm[i]];
-  __syncwarp();
+  __shared__ double rs[kSmallMax];
+  for (int i = tid; i < m; i += kSmallThreads) {
+    rs[i] = sh.z[i];  // D^{-1/2} from the scaling step
+    y[i] = RHS[i * m + j] * rs[i];
+  }
+  __syncthreads();
+  chol_apply_warp0(sh.W, sh.invd, y, m);
+  for (int i = tid; i < m; i += kSmallThreads) sh.z[i] = y[i] * rs[i];
+  __syncthreads();
   return rank;
 }
 
 template <typename T>
 __device__ void write_column(const double* z, int m, int mp, int j, double* X, T* Xt) {
-  int lane = threadIdx.x & 31;
-  for (int i = lane; i < mp; i += 32) {
+  for (int i = threadIdx.x; i < mp; i += kSmallThreads) {
     double v = (i < m) ? z[i] : 0.0;
     if (i < m) X[i * m + j] = v;
     Xt[i * mp + j] = (T)v;
@@ -232,8 +245,7 @@ __device__ void write_column(const double* z, int m, int mp, int j, double* X, T
 template <typename T>
 __device__ void zero_pad_columns(int m, int mp, T* Xt) {
   // columns m..mp-1 of the padded copy (CTA 0 only)
-  int lane = threadIdx.x & 31;
-  for (int idx = lane; idx < mp * mp; idx += 32) {
+  for (int idx = threadIdx.x; idx < mp * mp; idx += kSmallThreads) {
     int c = idx % mp;
     if (c >= m) Xt[idx] = (T)0;
   }
@@ -309,19 +321,20 @@ __global__ void k_chol_solve(int m, const double* G, const double* S, double* X,
   int j = blockIdx.x;
   int rank = small_solve_column(G, S, m, j, rank_tol, sh);
   if (rank != m) {
-    if ((threadIdx.x & 31) == 0) atomicExch(flag, 1);
+    if (threadIdx.x == 0) atomicExch(flag, 1);
     return;
   }
-  int lane = threadIdx.x & 31;
-  for (int i = lane; i < m; i += 32) X[i * m + j] = sh.z[i];
+  for (int i = threadIdx.x; i < m; i += kSmallThreads) X[i * m + j] = sh.z[i];
 }
 
 // ------------------------------------------------------------------ updates
-// R -= Y alpha, then the Gram partial of the new R.
+// R -= Y alpha, then the Gram partial of the new R. Thread per row; the whole R and Y
+// rows are loaded up front (2 MP independent loads per thread in flight), alpha is
+// read from shared memory as 16-byte broadcasts.
 template <typename T, int MP, int TM>
-__global__ void __launch_bounds__(TM) k_update_r(int64_t d, int m, const T* __restrict__ Y, T* __restrict__ R,
-                                                int64_t ld, const T* __restrict__ alpha_t, double* parts,
-                                                int nparts, const DevState* state) {
+__global__ void __launch_bounds__(TM, sizeof(T) == 4 ? 4 : 2)
+    k_update_r(int64_t d, int m, const T* __restrict__ Y, T* __restrict__ R, int64_t ld,
+               const T* __restrict__ alpha_t, double* parts, int nparts, const DevState* state) {
   if (is_done(state)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sA = reinterpret_cast<T*>(smem_raw);  // MP x MP
@@ -332,25 +345,32 @@ __global__ void __launch_bounds__(TM) k_update_r(int64_t d, int m, const T* __re
   g.init();
   int64_t ntiles = (d + TM - 1) / TM;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    int64_t i = tile * TM + threadIdx.x;
-    T acc[MP];
-    if (i < d) {
+    const int64_t i = tile * TM + threadIdx.x;
+    const bool ok = i < d;
+    asm volatile("" ::: "memory");  // no hoisting of the alpha reads across tiles
+    T acc[MP], y[MP];
 #pragma unroll
-      for (int c = 0; c < MP; ++c) acc[c] = (c < m) ? R[c * ld + i] : (T)0;
-#pragma unroll 4
-      for (int k = 0; k < m; ++k) {
-        T y = Y[k * ld + i];
-        const T* a = sA + k * MP;
+    for (int q = 0; q < MP / 4; ++q) {
+      if (ok && 4 * q < m) {
+        ld4(panel_row(R, ld, q, i), acc + 4 * q);
+        ldg4(panel_row(Y, ld, q, i), y + 4 * q);
+      } else {
 #pragma unroll
-        for (int c = 0; c < MP; ++c) acc[c] = fma(-y, a[c], acc[c]);
+        for (int u = 0; u < 4; ++u) acc[4 * q + u] = y[4 * q + u] = (T)0;
       }
-#pragma unroll
-      for (int c = 0; c < MP; ++c)
-        if (c < m) R[c * ld + i] = acc[c];
-      store_row<MP>(sX, threadIdx.x, acc);
-    } else {
-      zero_row<T, MP>(sX, threadIdx.x);
     }
+#pragma unroll
+    for (int k = 0; k < MP; ++k) {
+      const T* a = sA + k * MP;
+#pragma unroll
+      for (int c = 0; c < MP; ++c) acc[c] = fma(-y[k], a[c], acc[c]);
+    }
+    if (ok) {
+#pragma unroll
+      for (int q = 0; q < MP / 4; ++q)
+        if (4 * q < m) st4(panel_row(R, ld, q, i), acc + 4 * q);
+    }
+    store_row<MP>(sX, threadIdx.x, acc);
     __syncthreads();
     g.tile(sX, sX, TM);
     __syncthreads();
@@ -360,63 +380,70 @@ __global__ void __launch_bounds__(TM) k_update_r(int64_t d, int m, const T* __re
                      nparts, blockIdx.x);
 }
 
-// x += P alpha[:,0]; unless done_b, P = R + P beta; CTA 0 copies Snew into Sold.
+// x += P alpha[:,0]; unless the solve just ended, P = R + P beta; CTA 0 copies Snew
+// into Sold. Thread per row, both rows loaded up front.
 template <typename T, int MP>
-__global__ void __launch_bounds__(kUpdThreads) k_update_p(int64_t d, int m, const T* __restrict__ R, T* P,
-                                                         int64_t ld, const T* __restrict__ alpha_t,
-                                                         const T* __restrict__ beta_t, double* x,
-                                                         const double* Snew, double* Sold,
-                                                         const DevState* state) {
+__global__ void __launch_bounds__(kUpdThreads, sizeof(T) == 4 ? 3 : 2)
+    k_update_p(int64_t d, int m, const T* __restrict__ R, T* P, int64_t ld, const T* __restrict__ alpha_t,
+               const T* __restrict__ beta_t, double* x, const double* Snew, double* Sold, const DevState* state) {
   if (state && !state->pending_x) return;
-  bool upd = !(state && (state->done_a | state->done_b));
+  const bool upd = !(state && (state->done_a | state->done_b));
   __shared__ __align__(16) T sB[MP * MP];
-  __shared__ T sa0[MP];
+  __shared__ __align__(16) T sa0[MP];
   for (int idx = threadIdx.x; idx < MP * MP; idx += blockDim.x) sB[idx] = beta_t[idx];
   for (int idx = threadIdx.x; idx < MP; idx += blockDim.x) sa0[idx] = alpha_t[idx * MP];
   if (upd && blockIdx.x == 0 && Sold)
     for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Sold[idx] = Snew[idx];
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
-    T p[MP];
+    asm volatile("" ::: "memory");  // no hoisting of the beta reads across rows
+    T p[MP], acc[MP];
 #pragma unroll
-    for (int c = 0; c < MP; ++c) p[c] = (c < m) ? P[c * ld + i] : (T)0;
+    for (int q = 0; q < MP / 4; ++q) {
+      if (4 * q < m) {
+        ld4(panel_row(P, ld, q, i), p + 4 * q);
+        if (upd) ldg4(panel_row(R, ld, q, i), acc + 4 * q);
+        else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[4 * q + u] = (T)0;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[4 * q + u] = acc[4 * q + u] = (T)0;
+      }
+    }
     T xs = 0;
 #pragma unroll
     for (int k = 0; k < MP; ++k) xs = fma(p[k], sa0[k], xs);
     x[i] += (double)xs;
     if (upd) {
-      // columns in chunks of 4 keep the live registers at MP + 4
-#pragma unroll 1
-      for (int c0 = 0; c0 < MP; c0 += 4) {
-        T acc[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = (c0 + q < m) ? R[(c0 + q) * ld + i] : (T)0;
+      for (int k = 0; k < MP; ++k) {
+        const T* b = sB + k * MP;
 #pragma unroll
-        for (int k = 0; k < MP; ++k) {
-          const T* b = sB + k * MP + c0;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[q] = fma(p[k], b[q], acc[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (c0 + q < m) P[(c0 + q) * ld + i] = acc[q];
+        for (int c = 0; c < MP; ++c) acc[c] = fma(p[k], b[c], acc[c]);
       }
+#pragma unroll
+      for (int q = 0; q < MP / 4; ++q)
+        if (4 * q < m) st4(panel_row(P, ld, q, i), acc + 4 * q);
     }
   }
 }
 
 // ------------------------------------------------------------------ start block, helpers
+// R = P = [r * scale, Omega] on panels: the Omega buffer is a full panel block whose
+// column 0 and padding columns are zero.
 template <typename T>
 __global__ void k_start_block(int64_t d, int m, int64_t ld, const double* r, double scale, const T* omega,
                               T* R, T* P, double* x) {
+  const int nq = (m + 3) >> 2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
-    T v0 = (T)(r[i] * scale);
-    R[i] = v0;
-    P[i] = v0;
-    for (int j = 1; j < m; ++j) {
-      T v = omega[(int64_t)(j - 1) * ld + i];
-      R[j * ld + i] = v;
-      P[j * ld + i] = v;
+    for (int q = 0; q < nq; ++q) {
+      T v[4];
+      ldg4(panel_row(omega, ld, q, i), v);
+      if (q == 0) v[0] = (T)(r[i] * scale);
+      st4(panel_row(R, ld, q, i), v);
+      st4(panel_row(P, ld, q, i), v);
     }
     x[i] = 0.0;
   }
@@ -502,7 +529,7 @@ cudaError_t gram_impl(int64_t d, const void* X, const void* Y, int64_t ld, int m
 template <typename T, int MP>
 cudaError_t update_r_impl(int64_t d, int m, const void* Y, void* R, int64_t ld, const void* alpha_t, double* parts,
                           int nparts, const DevState* state, cudaStream_t st) {
-  constexpr int TM = sizeof(T) == 4 ? 256 : 128;
+  constexpr int TM = 128;
   size_t head = ((MP * MP * sizeof(T) + 15) / 16) * 16;
   size_t smem = head + gram_smem_bytes<T, MP>(TM, TM);
   auto kern = k_update_r<T, MP, TM>;
@@ -516,7 +543,7 @@ template <typename T, int MP>
 cudaError_t update_p_impl(int64_t d, int m, const void* R, void* P, int64_t ld, const void* alpha_t,
                           const void* beta_t, double* x, const double* Snew, double* Sold, const DevState* state,
                           cudaStream_t st, int device) {
-  int grid = capped_grid(d, kUpdThreads, sm_count(device) * 8);
+  int grid = capped_grid(d, kUpdThreads, sm_count(device) * (sizeof(T) == 4 ? 4 : 2) * 4);
   k_update_p<T, MP><<<grid, kUpdThreads, 0, st>>>(d, m, (const T*)R, (T*)P, ld, (const T*)alpha_t,
                                                   (const T*)beta_t, x, Snew, Sold, state);
   return cudaGetLastError();
@@ -580,7 +607,11 @@ int gram_grid(int is_f64, int mp, int64_t d, int device) {
   int cap = sm_count(device) * 2;
   return (int)(ntiles < cap ? (ntiles < 1 ? 1 : ntiles) : cap);
 }
-int update_r_grid(int is_f64, int mp, int64_t d, int device) { return gram_grid(is_f64, mp, d, device); }
+int update_r_grid(int is_f64, int mp, int64_t d, int device) {
+  int64_t ntiles = (d + 127) / 128;
+  int cap = sm_count(device) * (is_f64 ? 2 : 4);
+  return (int)(ntiles < cap ? (ntiles < 1 ? 1 : ntiles) : cap);
+}
 
 cudaError_t launch_gram(int is_f64, int mp, int64_t d, const void* X, const void* Y, int64_t ld, int m,
                         double* parts, int nparts, cudaStream_t st) {
@@ -600,9 +631,9 @@ cudaError_t launch_small_alpha(int is_f64, int mp, int m, const double* G, const
                                double rank_tol, DevState* state, cudaStream_t st) {
   if (m < 1 || m > kSmallMax || mp < m) return cudaErrorInvalidValue;
   if (is_f64)
-    k_small_alpha<double><<<m, 32, 0, st>>>(m, mp, G, S, X, (double*)Xt, rank_tol, state);
+    k_small_alpha<double><<<m, kSmallThreads, 0, st>>>(m, mp, G, S, X, (double*)Xt, rank_tol, state);
   else
-    k_small_alpha<float><<<m, 32, 0, st>>>(m, mp, G, S, X, (float*)Xt, rank_tol, state);
+    k_small_alpha<float><<<m, kSmallThreads, 0, st>>>(m, mp, G, S, X, (float*)Xt, rank_tol, state);
   return cudaGetLastError();
 }
 
@@ -610,15 +641,15 @@ cudaError_t launch_small_beta(int is_f64, int mp, int m, const double* Sold, con
                               double rank_tol, DevState* state, cudaStream_t st) {
   if (m < 1 || m > kSmallMax || mp < m) return cudaErrorInvalidValue;
   if (is_f64)
-    k_small_beta<double><<<m, 32, 0, st>>>(m, mp, Sold, Snew, X, (double*)Xt, rank_tol, state);
+    k_small_beta<double><<<m, kSmallThreads, 0, st>>>(m, mp, Sold, Snew, X, (double*)Xt, rank_tol, state);
   else
-    k_small_beta<float><<<m, 32, 0, st>>>(m, mp, Sold, Snew, X, (float*)Xt, rank_tol, state);
+    k_small_beta<float><<<m, kSmallThreads, 0, st>>>(m, mp, Sold, Snew, X, (float*)Xt, rank_tol, state);
   return cudaGetLastError();
 }
 
 cudaError_t launch_chol_solve(int m, const double* G, const double* S, double* X, int* flag, cudaStream_t st) {
   if (m < 1 || m > kSmallMax) return cudaErrorInvalidValue;
-  k_chol_solve<<<m, 32, 0, st>>>(m, G, S, X, 1e-14, flag);
+  k_chol_solve<<<m, kSmallThreads, 0, st>>>(m, G, S, X, 1e-14, flag);
   return cudaGetLastError();
 }
 

@@ -1,10 +1,11 @@
 // Block products with A_mu = A + mu I ("matrix-loads", Sec. 1.2) and the FP64 residual.
 //
 // k_csr_spmm_gram: Y = A P + mu P for CSR A, reading each matrix row once for all m
-//   columns (thread per row, m accumulators in registers), with G = P^T Y formed in
-//   the same pass from the row tile staged in shared memory (bk_tile.cuh).
-//   Blocks are column-major: for stencil-like sparsity neighbouring rows touch
-//   neighbouring columns, so every gather P[c][j] is coalesced across a warp.
+//   columns (thread per row, the row's nonzeros held in registers), with G = P^T Y
+//   formed in the same pass from the row tile staged in shared memory (bk_tile.cuh).
+//   Blocks are stored in panels of four columns (bk_tile.cuh): one gather of row j of
+//   a panel is a single 16-byte load, and for stencil-like sparsity neighbouring rows
+//   touch neighbouring rows of P, so a warp's gathers are contiguous.
 // k_dense_gram: the same for a dense row-major A (tiled over K in shared memory).
 // k_*_residual: r = b - A_mu x in FP64 from the stored values, with ||r||^2 partials.
 #include "bk_common.cuh"
@@ -22,42 +23,68 @@ int sm_count_ops(int device) {
 }
 
 // ------------------------------------------------------------------ CSR
-template <typename T, int MP, int TM>
-__global__ void __launch_bounds__(TM) k_csr_spmm_gram(int64_t d, const int* __restrict__ rowptr,
-                                                     const int* __restrict__ colidx, const T* __restrict__ vals,
-                                                     T mu, const T* __restrict__ P, T* __restrict__ Y, int64_t ld,
-                                                     int m, double* parts, int nparts, const DevState* state) {
+// Thread per row. The row's nonzeros (up to KMAX, more are read in a tail loop) are
+// held in registers; the panels are walked one at a time, each step keeping nnz
+// independent 16-byte gathers in flight. Each panel row of the result goes to Y and,
+// as one 16-byte store, to the row-major shared tile used by the fused Gram.
+template <typename T, int MP, int TM, int KMAX>
+__global__ void __launch_bounds__(TM, sizeof(T) == 4 ? 5 : 3)
+    k_csr_spmm_gram(int64_t d, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                    const T* __restrict__ vals, T mu, const T* __restrict__ P, T* __restrict__ Y, int64_t ld, int m,
+                    double* parts, int nparts, const DevState* state) {
   if (is_done(state)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sX = reinterpret_cast<T*>(smem_raw);
   T* sY = sX + TM * MP;
   GramAcc<T, MP> g;
   g.init();
+  const int t = threadIdx.x;
+  const int nq = (m + 3) >> 2;
   int64_t ntiles = (d + TM - 1) / TM;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    int64_t i = tile * TM + threadIdx.x;
-    if (i < d) {
-      T acc[MP];
+    const int64_t i = tile * TM + t;
+    const bool ok = i < d;
+    int k0 = 0, nz = 0;
+    if (ok) {
+      k0 = rowptr[i];
+      nz = rowptr[i + 1] - k0;
+    }
+    T v[KMAX];
+    int off[KMAX];
 #pragma unroll
-      for (int c = 0; c < MP; ++c) acc[c] = (c < m) ? P[c * ld + i] : (T)0;
-      store_row<MP>(sX, threadIdx.x, acc);
+    for (int k = 0; k < KMAX; ++k) {
+      bool on = k < nz;
+      v[k] = on ? vals[k0 + k] : (T)0;
+      off[k] = on ? colidx[k0 + k] : 0;
+    }
+#pragma unroll 1
+    for (int q = 0; q < MP / 4; ++q) {
+      T a[4] = {0, 0, 0, 0}, pv[4] = {0, 0, 0, 0};
+      if (ok && q < nq) {
+        const T* pq = P + (int64_t)q * ld * 4;
+        ldg4(pq + i * 4, pv);
 #pragma unroll
-      for (int c = 0; c < MP; ++c) acc[c] *= mu;
-      int k0 = rowptr[i], k1 = rowptr[i + 1];
-      for (int k = k0; k < k1; ++k) {
-        T v = vals[k];
-        const T* pj = P + colidx[k];
+        for (int u = 0; u < 4; ++u) a[u] = mu * pv[u];
 #pragma unroll
-        for (int c = 0; c < MP; ++c)
-          if (c < m) acc[c] = fma(v, pj[c * ld], acc[c]);
+        for (int k = 0; k < KMAX; ++k) {
+          if (k < nz) {
+            T gv[4];
+            ldg4(pq + (int64_t)off[k] * 4, gv);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = fma(v[k], gv[u], a[u]);
+          }
+        }
+        for (int k = KMAX; k < nz; ++k) {
+          T gv[4];
+          ldg4(pq + (int64_t)colidx[k0 + k] * 4, gv);
+          const T vk = vals[k0 + k];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a[u] = fma(vk, gv[u], a[u]);
+        }
+        st4(Y + ((int64_t)q * ld + i) * 4, a);
       }
-#pragma unroll
-      for (int c = 0; c < MP; ++c)
-        if (c < m) Y[c * ld + i] = acc[c];
-      store_row<MP>(sY, threadIdx.x, acc);
-    } else {
-      zero_row<T, MP>(sX, threadIdx.x);
-      zero_row<T, MP>(sY, threadIdx.x);
+      store4<MP>(sX, t, q, pv);
+      store4<MP>(sY, t, q, a);
     }
     __syncthreads();
     g.tile(sX, sY, TM);
@@ -98,10 +125,13 @@ __global__ void __launch_bounds__(NTH) k_dense_gram(int64_t d, const T* __restri
         int64_t gr = row0 + rr, gk = k0 + kk;
         sA[rr * (KC + 1) + kk] = (gr < d && gk < d) ? A[gr * lda + gk] : (T)0;
       }
-      for (int idx = threadIdx.x; idx < KC * MP; idx += NTH) {
-        int c = idx / KC, kk = idx - c * KC;
+      for (int idx = threadIdx.x; idx < KC * (MP / 4); idx += NTH) {
+        int q = idx / KC, kk = idx - q * KC;
         int64_t gk = k0 + kk;
-        sP[kk * MP + c] = (c < m && gk < d) ? P[c * ld + gk] : (T)0;
+        T pv[4] = {0, 0, 0, 0};
+        if (gk < d) ldg4(P + ((int64_t)q * ld + gk) * 4, pv);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sP[kk * MP + 4 * q + u] = pv[u];
       }
       __syncthreads();
 #pragma unroll 8
@@ -120,9 +150,10 @@ __global__ void __launch_bounds__(NTH) k_dense_gram(int64_t d, const T* __restri
     for (int q = 0; q < NC; ++q) {
       int c = cg + q * CG;
       if (c < MP) {
-        T pv = (gi < d && c < m) ? P[c * ld + gi] : (T)0;
-        T yv = (gi < d && c < m) ? fma(mu, pv, acc[q]) : (T)0;
-        if (gi < d && c < m) Y[c * ld + gi] = yv;
+        const int64_t off = (((int64_t)(c >> 2) * ld + gi) << 2) + (c & 3);
+        T pv = (gi < d) ? P[off] : (T)0;
+        T yv = (gi < d) ? fma(mu, pv, acc[q]) : (T)0;
+        if (gi < d) Y[off] = yv;
         sX[r * MP + c] = pv;
         sY[r * MP + c] = yv;
       }
@@ -198,7 +229,7 @@ __global__ void __launch_bounds__(kResThreads) k_dense_residual(int64_t d, const
 // ------------------------------------------------------------------ dispatch helpers
 template <typename T, int MP>
 constexpr int csr_tm() {
-  return sizeof(T) == 4 ? 256 : 128;
+  return 128;
 }
 
 template <typename T, int MP>
@@ -206,7 +237,7 @@ cudaError_t csr_impl(int64_t d, const int* rowptr, const int* colidx, const void
                      void* Y, int64_t ld, int m, double* parts, int nparts, const DevState* state, cudaStream_t st) {
   constexpr int TM = csr_tm<T, MP>();
   size_t smem = gram_smem_bytes<T, MP>(TM, TM);
-  auto kern = k_csr_spmm_gram<T, MP, TM>;
+  auto kern = k_csr_spmm_gram<T, MP, TM, 8>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<nparts, TM, smem, st>>>(d, rowptr, colidx, (const T*)vals, (T)mu, (const T*)P, (T*)Y, ld, m, parts, nparts,
@@ -271,9 +302,9 @@ cudaError_t dense_f(int64_t d, const void* A, int64_t lda, double mu, const void
 }  // namespace
 
 int csr_spmm_gram_grid(int is_f64, int mp, int64_t d, int device) {
-  int tm = is_f64 ? 128 : 256;
+  int tm = 128;
   int64_t ntiles = (d + tm - 1) / tm;
-  int cap = sm_count_ops(device) * (is_f64 ? 2 : 3);
+  int cap = sm_count_ops(device) * (is_f64 ? 3 : 5);
   if (ntiles < 1) ntiles = 1;
   return (int)(ntiles < cap ? ntiles : cap);
 }

@@ -62,12 +62,13 @@ __global__ void k_omega(int64_t d, int l, int64_t ld, uint64_t seed, double scal
     double z0, z1;
     normal_pair(seed, 3u, (uint64_t)blk, z0, z1);
     int64_t k0 = 2 * blk, k1 = k0 + 1;
-    // entry k is (row k mod d, column k / d) of Omega
+    // entry k is (row k mod d, column k / d) of Omega, stored as column c = j + 1 of a
+    // panel block (element (i, c) at ((c / 4) ld + i) 4 + c % 4)
     int64_t j0 = k0 / d, i0 = k0 - j0 * d;
-    out[j0 * ld + i0] = (T)(z0 * scale);
+    out[(((j0 + 1) >> 2) * ld + i0) * 4 + ((j0 + 1) & 3)] = (T)(z0 * scale);
     if (k1 < n) {
       int64_t j1 = k1 / d, i1 = k1 - j1 * d;
-      out[j1 * ld + i1] = (T)(z1 * scale);
+      out[(((j1 + 1) >> 2) * ld + i1) * 4 + ((j1 + 1) & 3)] = (T)(z1 * scale);
     }
   }
 }

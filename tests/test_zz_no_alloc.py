@@ -25,9 +25,9 @@ def _case(kind, dtype, m, seed):
         ops = (W.dense_spd(W.BASE_SEED + 90 + seed, W.decay_spectrum(d, 1e2, 1e-1)).astype(npdt),)
     ld = d + 7
     rng = np.random.default_rng(seed)
-    P = np.zeros((m, ld))
-    P[:, :d] = rng.standard_normal((m, d))
-    return ops, P.astype(npdt), d, ld
+    P = rng.standard_normal((d, m)).astype(npdt)
+    from paper_2501_18717_gb300 import bk
+    return ops, bk.to_panels(P, ld), d, ld
 
 
 @pytest.mark.parametrize("kind,dtype,m", [("csr", "f32", 33), ("dense", "f64", 21)])
@@ -49,7 +49,7 @@ def test_static_matches_regular(kind, dtype, m):
         G = torch.zeros(m, m, dtype=torch.float64, device=dev)
         st = bk.block_apply_static(A, mu, Pt, Y, G, m, ld)
         assert st == bk.BK_OK, bk.status_string(st)
-        Yn, Yr = Y.cpu().numpy()[:, :d].astype(np.float64), Yref.cpu().numpy()[:, :d].astype(np.float64)
+        Yn, Yr = Y.cpu().numpy().astype(np.float64), Yref.cpu().numpy().astype(np.float64)
         assert np.max(np.abs(Yn - Yr)) <= tol * np.max(np.abs(Yr)), call
         Gn, Gr = G.cpu().numpy(), Gref.cpu().numpy()
         assert np.max(np.abs(Gn - Gr)) <= tol * np.max(np.abs(Gr)), call
