@@ -54,7 +54,7 @@ typedef enum {
   BK_ERR_TOO_LARGE = 9     /* the call needs more than the fixed static scratch holds */
 } bk_status;
 
-typedef enum { BK_DENSE = 0, BK_CSR = 1 } bk_op_kind;
+typedef enum { BK_DENSE = 0, BK_CSR = 1, BK_GRAM = 2 } bk_op_kind;
 typedef enum { BK_F64 = 0, BK_F32 = 1 } bk_dtype;
 
 /* Precision of the inner block-CG iteration (block vectors, block products,
@@ -65,6 +65,9 @@ typedef enum { BK_PREC_FP64 = 0, BK_PREC_FP32 = 1 } bk_prec;
 /* The matrix A (without the shift mu).
  *   BK_DENSE: vals is rows x cols row-major with leading dimension ld, rows = cols = d.
  *   BK_CSR:   rowptr[rows+1], colidx[nnz], vals[nnz]; rows = cols = d; ld ignored.
+ *   BK_GRAM:  A = Z^T Z applied matrix-free as Z^T (Z P) (ridge regression, Sec. 1);
+ *             vals is Z, rows x cols row-major with leading dimension ld; d = cols.
+ *             Accepted by bk_ridge_path and bk_sample.
  *   dtype gives the element type of vals. A must be symmetric positive definite
  *   (or positive semi-definite with mu > 0); the library does not check symmetry. */
 typedef struct {
@@ -147,6 +150,28 @@ const char* bk_last_error(const bk_ctx* ctx);
  * FP32) and the refinement residual uses the values as given. */
 bk_status bk_solve(bk_ctx* ctx, const bk_operator* A, double mu, const double* b, double* x,
                    const bk_opts* opts, bk_info* info);
+
+/* The whole ridge-regression path (Sec. 1, Sec. 3.2 Eq. bcg_alg, Thm. cost): for every
+ * shift mu_j, X[:, j] ~= (A + mu_j I)^{-1} b, all from one block-Lanczos basis of
+ * K_t(A, [b Omega]) with full reorthogonalisation (shift invariance, Eq.
+ * shift_invariance). T_t is block tridiagonal with half-bandwidth m; the L shifted
+ * banded systems (T_t + mu_j I) z_j = ||b|| e_1 are solved in one launch (one thread
+ * block per shift, FP64) and combined as X = Q_t [z_1 .. z_L]. The run stops when the
+ * Lanczos residual estimate ||B_t z_j,last|| of every shift meets the inner target.
+ * FP64 refinement: the residuals r_j = b - (A + mu_j) x_j are formed in FP64 from the
+ * stored values; while max_j ||r_j|| > tol ||b||, a block-Lanczos basis of the residual
+ * block [r_1 .. r_L] (block width L) gives every correction at once and x_j is updated.
+ *   A      BK_DENSE or BK_GRAM, FP32 or FP64 values (FP32 runs use FP32 values; FP64
+ *          values are rounded by the library for them)
+ *   L      number of shifts, 1 <= L <= 1024; mus: L shifts >= 0 (host or device)
+ *   b      d doubles; X: d x L doubles, column-major (leading dimension d), output
+ *   opts   sketch (l, block width l + 1 <= 256), seed, tol (relative residual of every
+ *          shift), inner (FP64 or FP32 basis and products), inner_tol, max_loads (cap on
+ *          operator applications per basis), max_refine (bases built), check_every
+ *   info   loads (all bases), refinements (bases built), rel_residual (worst shift)
+ * Returns BK_NOT_CONVERGED if the worst shift misses tol after max_refine bases. */
+bk_status bk_ridge_path(bk_ctx* ctx, const bk_operator* A, int32_t L, const double* mus, const double* b,
+                        double* X, const bk_opts* opts, bk_info* info);
 
 /* One block product with its Gram matrix (one "matrix-load", Sec. 1.2):
  *   Y = A P + mu P  and  G = P^T Y  (m x m, FP64, row-major).

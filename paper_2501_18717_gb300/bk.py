@@ -22,13 +22,13 @@ LIB_PATH = os.path.join(_HERE, "libbk.so")
 
 BK_OK, BK_ERR_ARG, BK_ERR_CUDA, BK_ERR_OOM, BK_NOT_CONVERGED, BK_BREAKDOWN, BK_STAGNATED, BK_TIMEOUT, \
     BK_ERR_UNSUPPORTED, BK_ERR_TOO_LARGE = range(10)
-BK_DENSE, BK_CSR = 0, 1
+BK_DENSE, BK_CSR, BK_GRAM = 0, 1, 2
 BK_F64, BK_F32 = 0, 1
 BK_PREC_FP64, BK_PREC_FP32 = 0, 1
 
 EXPORTS = ("bk_default_opts", "bk_create", "bk_destroy", "bk_set_stream", "bk_status_string", "bk_last_error",
            "bk_solve",
-           "bk_block_apply", "bk_gram", "bk_chol_solve", "bk_gaussian", "bk_block_apply_static")
+           "bk_block_apply", "bk_gram", "bk_chol_solve", "bk_gaussian", "bk_block_apply_static", "bk_ridge_path")
 
 
 class Operator(ctypes.Structure):
@@ -78,6 +78,8 @@ def _load():
         "bk_chol_solve": (i32, [vp, i64, vp, vp, vp]),
         "bk_gaussian": (i32, [vp, u64, ctypes.c_uint32, i64, i64, vp]),
         "bk_block_apply_static": (i32, [ctypes.POINTER(Operator), dbl, i32, i64, vp, vp, i64, vp, vp]),
+        "bk_ridge_path": (i32, [vp, ctypes.POINTER(Operator), i32, vp, vp, vp, ctypes.POINTER(Opts),
+                                ctypes.POINTER(Info)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -201,6 +203,17 @@ def csr_operator(rowptr, colidx, vals) -> OperatorRef:
     return OperatorRef(op, [kr, kc, kv])
 
 
+def gram_operator(Z) -> OperatorRef:
+    """A = Z^T Z applied matrix-free; Z is n x d row-major (float64 or float32)."""
+    n, d = Z.shape
+    ld = Z.stride(0) if hasattr(Z, "stride") and callable(Z.stride) else Z.strides[0] // Z.itemsize
+    p, k = _ptr(Z)
+    op = Operator(BK_GRAM, _dtype_code(Z), n, d, ld, p, None, None, 0)
+    ref = OperatorRef(op, [k])
+    ref.d = d
+    return ref
+
+
 def default_opts(**kw) -> Opts:
     o = Opts()
     _lib.bk_default_opts(ctypes.byref(o))
@@ -239,6 +252,22 @@ def from_panels(Pn, d, m):
     """The d x m block held in a panel-layout array (inverse of to_panels)."""
     Pn = np.asarray(Pn)
     return np.stack([Pn[c // 4, :d, c % 4] for c in range(m)], axis=1)
+
+
+def ridge_path(ctx: Context, A: OperatorRef, mus, b, X, opts: Opts | None = None, check=True) -> Info:
+    """bk_ridge_path: X[:, j] = (A + mus[j] I)^{-1} b for every shift from one
+    block-Lanczos basis (X is d x L column-major: a Fortran-ordered array or the
+    transpose view of an L x d row-major array)."""
+    info = Info()
+    pm, km = _ptr(mus)
+    pb, kb = _ptr(b)
+    px, kx = _ptr(X)
+    o = opts if opts is not None else default_opts()
+    s = _lib.bk_ridge_path(ctx.handle, ctypes.byref(A.op), int(len(mus)), pm, pb, px, ctypes.byref(o),
+                           ctypes.byref(info))
+    if check and s != BK_OK:
+        raise BKError(s, "bk_ridge_path", ctx.last_error())
+    return info
 
 
 def block_apply(ctx: Context, A: OperatorRef, mu: float, P, Y, G, m: int, ld: int, dtype=None) -> None:

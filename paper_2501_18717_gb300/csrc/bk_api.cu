@@ -12,104 +12,13 @@
 
 #include "../../include/bk.h"
 #include "bk_common.cuh"
+#include "bk_ctx.h"
 
 using bk::DevState;
 
-namespace {
-
-enum Slot {
-  WS_P, WS_R, WS_Y, WS_OMEGA, WS_XIN, WS_X64, WS_R64, WS_B64, WS_PARTS_G, WS_PARTS_S, WS_MATS, WS_STATE,
-  WS_OP_VALS, WS_OP_ROW, WS_OP_COL, WS_VALS_INNER, WS_NORMP, WS_TMP_IN, WS_TMP_OUT, WS_TMP_G, WS_TMP_S,
-  WS_COUNT
-};
-
-struct Buf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
-
-}  // namespace
-
-struct bk_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  cudaStream_t own_stream = nullptr;  // created when the caller passes the legacy default stream
-  char last_error[256] = {0};
-  Buf ws[WS_COUNT];
-  DevState* hstate = nullptr;  // pinned mirror of the device control block
-  double* hparts = nullptr;    // pinned buffer for norm partials
-  int sms = 152;
-};
+using namespace bkx;
 
 namespace {
-
-constexpr int kHostParts = 1024;
-
-thread_local bk_ctx* g_err_ctx = nullptr;
-
-bk_status from_cuda(cudaError_t e, const char* what = nullptr, int line = 0) {
-  if (e == cudaSuccess) return BK_OK;
-  cudaGetLastError();  // clear a sticky launch error so the context stays usable
-  if (g_err_ctx)
-    std::snprintf(g_err_ctx->last_error, sizeof(g_err_ctx->last_error), "bk_api.cu:%d %s: %s", line,
-                  what ? what : "", cudaGetErrorString(e));
-  if (e == cudaErrorMemoryAllocation) return BK_ERR_OOM;
-  return BK_ERR_CUDA;
-}
-
-#define BK_CK(expr)                                              \
-  do {                                                           \
-    cudaError_t e_ = (expr);                                     \
-    if (e_ != cudaSuccess) return from_cuda(e_, #expr, __LINE__); \
-  } while (0)
-
-cudaError_t ws_get(bk_ctx* c, Slot s, size_t bytes, void** out) {
-  Buf& b = c->ws[s];
-  if (bytes == 0) bytes = 16;
-  if (b.bytes < bytes) {
-    if (b.p) {
-      cudaError_t e = cudaStreamSynchronize(c->stream);
-      if (e != cudaSuccess) return e;
-      cudaFree(b.p);
-      b.p = nullptr;
-      b.bytes = 0;
-    }
-    size_t want = (bytes + (1u << 20) - 1) & ~((size_t)(1u << 20) - 1);
-    cudaError_t e = cudaMalloc(&b.p, want);
-    if (e != cudaSuccess) {
-      b.p = nullptr;
-      return e;
-    }
-    b.bytes = want;
-  }
-  *out = b.p;
-  return cudaSuccess;
-}
-
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes a;
-  cudaError_t e = cudaPointerGetAttributes(&a, p);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-// Device view of a borrowed input array: the pointer itself, or a staged copy.
-cudaError_t stage_in(bk_ctx* c, Slot s, const void* p, size_t bytes, const void** out) {
-  if (is_device_ptr(p)) {
-    *out = p;
-    return cudaSuccess;
-  }
-  void* d = nullptr;
-  cudaError_t e = ws_get(c, s, bytes, &d);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, c->stream);
-  *out = d;
-  return e;
-}
 
 size_t dtype_size(int dt) { return dt == BK_F64 ? 8 : 4; }
 
@@ -184,18 +93,6 @@ cudaError_t inner_values(bk_ctx* c, const OpDev& o, int want_f64, const void** o
   }
   *out = buf;
   return e;
-}
-
-// Host sum of per-CTA partials in fixed order.
-cudaError_t host_sum(bk_ctx* c, const double* dparts, int n, double* out) {
-  cudaError_t e = cudaMemcpyAsync(c->hparts, dparts, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return e;
-  double s = 0.0;
-  for (int i = 0; i < n; ++i) s += c->hparts[i];
-  *out = s;
-  return cudaSuccess;
 }
 
 cudaError_t residual(bk_ctx* c, const OpDev& o, double mu, const double* x, const double* b, double* r,
@@ -318,7 +215,7 @@ bk_status bk_set_stream(bk_ctx* c, void* s) {
 const char* bk_last_error(const bk_ctx* c) { return c ? c->last_error : ""; }
 
 bk_status bk_gaussian(bk_ctx* c, uint64_t seed, uint32_t stream, int64_t n, int64_t offset, double* out) {
-  g_err_ctx = c;
+  err_ctx() = c;
   if (c) c->last_error[0] = 0;
   if (!c || !out || n < 0 || offset < 0) return BK_ERR_ARG;
   if (n == 0) return BK_OK;
@@ -333,7 +230,7 @@ bk_status bk_gaussian(bk_ctx* c, uint64_t seed, uint32_t stream, int64_t n, int6
 }
 
 bk_status bk_chol_solve(bk_ctx* c, int64_t m, const double* G, const double* S, double* X) {
-  g_err_ctx = c;
+  err_ctx() = c;
   if (c) c->last_error[0] = 0;
   if (!c || !G || !S || !X || m < 1 || m > 64) return BK_ERR_ARG;
   BK_CK(cudaSetDevice(c->device));
@@ -358,7 +255,7 @@ bk_status bk_chol_solve(bk_ctx* c, int64_t m, const double* G, const double* S, 
 
 bk_status bk_gram(bk_ctx* c, int32_t dtype, int64_t d, int64_t m, const void* X, const void* Y, int64_t ld,
                   double* G) {
-  g_err_ctx = c;
+  err_ctx() = c;
   if (c) c->last_error[0] = 0;
   if (!c || !X || !Y || !G || d < 1 || m < 1 || ld < d) return BK_ERR_ARG;
   if (dtype != BK_F64 && dtype != BK_F32) return BK_ERR_UNSUPPORTED;
@@ -386,7 +283,7 @@ bk_status bk_gram(bk_ctx* c, int32_t dtype, int64_t d, int64_t m, const void* X,
 
 bk_status bk_block_apply(bk_ctx* c, const bk_operator* A, double mu, int32_t dtype, int64_t m, const void* P,
                          void* Y, int64_t ld, double* G) {
-  g_err_ctx = c;
+  err_ctx() = c;
   if (c) c->last_error[0] = 0;
   if (!c || !P || !Y || !G) return BK_ERR_ARG;
   bk_status s = check_operator(A);
@@ -431,7 +328,7 @@ bk_status bk_block_apply(bk_ctx* c, const bk_operator* A, double mu, int32_t dty
 
 bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, double* x, const bk_opts* opts_in,
                    bk_info* info) {
-  g_err_ctx = c;
+  err_ctx() = c;
   if (c) c->last_error[0] = 0;
   if (info) std::memset(info, 0, sizeof(*info));
   if (!c || !b || !x) return BK_ERR_ARG;

@@ -124,6 +124,33 @@ cudaError_t launch_norm2_parts(int64_t d, const double* v, double* parts, int np
 // Dense: FP64 -> FP32 copy of a d x d row-major matrix with leading dimension lda into lda32.
 cudaError_t launch_dense_to_f32(int64_t d, const double* in, int64_t lda, float* out, int64_t lda32,
                                 cudaStream_t st);
+// C = alpha A B + beta C (column-major C, general strides for A and B; see k_gemm.cu).
+// is_f64: element type of B and C (and the accumulation). a_f64: 1 A is FP64, 0 A is
+// FP32; with is_f64 = 1, a_f64 = 2 means A and B are FP32 (FP64 accumulation/output).
+cudaError_t launch_gemm(int is_f64, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int a_f64,
+                        int64_t sai, int64_t sak, const void* B, int64_t sbk, int64_t sbj, double beta, void* C,
+                        int64_t ldc, cudaStream_t st);
+// ---- block-Lanczos drivers (k_krylov.cu)
+cudaError_t launch_e1r0(int n, int mb, const double* R0, double* rhs, cudaStream_t st);
+cudaError_t launch_chol_inv(int m, const double* G, double rank_tol, double* work, double* R, double* Rinv,
+                            int* keep, int* rank, cudaStream_t st);
+cudaError_t launch_band_put(int ldb, int bw, int m, int k, const double* A, const double* B, double* band,
+                            cudaStream_t st);
+cudaError_t launch_band_solve(int n, int bw, const double* band, int ldb, int L, const double* mus,
+                              const double* rhs, const int* rhs_col, int nrhs, double* work, double* Z, int* flags,
+                              cudaStream_t st);
+cudaError_t launch_band_mult(int n, int bw, const double* band, int ldb, const double* Y, int nc, double* out,
+                             cudaStream_t st);
+cudaError_t launch_combine_shifts(int n, int nc, int L, const double* Z, const double* c, double* Y,
+                                  cudaStream_t st);
+cudaError_t launch_lanczos_res(int n, int m, int L, int nrhs, const double* Blast, const double* Z, double* out,
+                               cudaStream_t st);
+cudaError_t launch_scale_cols(int is_f64, int64_t d, int m, int64_t ld, const double* scale, void* X,
+                              cudaStream_t st);
+cudaError_t launch_copy_cols(int in_f64, int out_f64, int64_t d, int m, const void* in, int64_t ldi, void* out,
+                             int64_t ldo, cudaStream_t st);
+cudaError_t launch_shift_residual(int64_t d, int L, const double* b, const double* AX, const double* X, int64_t ld,
+                                  const double* mus, double* R, double* norms2, cudaStream_t st);
 // Reset the control block for a new inner solve.
 cudaError_t launch_init_state(DevState* state, int max_loads, double tol_abs, cudaStream_t st);
 // Norm partial count used by the residual launchers.

@@ -1,0 +1,124 @@
+// Dense products for the block-Lanczos drivers (ridge path, sampling): the Gram-form
+// operator Z^T (Z P), the dense operator for wide blocks, the reorthogonalisation
+// products Q^T W and W - Q C, and the basis combination Q Z (Sec. 3.2, Thm. cost:
+// O(d m^2 t^2) work for full reorthogonalisation, O(d m t) per shift for the combine).
+//
+// C = alpha * A * B + beta * C with general element strides, so one kernel serves
+// row-major, column-major and transposed operands:
+//   A(i, k) = A[i * sai + k * sak]   (M x K)
+//   B(k, j) = B[k * sbk + j * sbj]   (K x N)
+//   C(i, j) = C[i + j * ldc]         (M x N, column-major)
+// Tiles of 64 x 64 outputs, K in steps of 16 staged in shared memory, 256 threads with
+// 4 x 4 outputs each, accumulation in the element type (FP32 or FP64). Operands may be
+// FP32 or FP64 (A also BF16-free here); the tile loader reads along whichever stride is
+// unit so the global loads coalesce.
+#include "bk_common.cuh"
+
+namespace bk {
+namespace {
+
+constexpr int GBM = 64, GBN = 64, GBK = 16, GTH = 256;
+
+template <typename TA, typename TB, typename TC>
+__global__ void __launch_bounds__(GTH) k_gemm(int64_t M, int64_t N, int64_t K, TC alpha, const TA* __restrict__ A,
+                                             int64_t sai, int64_t sak, const TB* __restrict__ B, int64_t sbk,
+                                             int64_t sbj, TC beta, TC* __restrict__ C, int64_t ldc) {
+  __shared__ TC sA[GBK][GBM + 4];
+  __shared__ TC sB[GBK][GBN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;  // 16 x 16 threads, 4 x 4 outputs each
+  const int64_t i0 = (int64_t)blockIdx.x * GBM, j0 = (int64_t)blockIdx.y * GBN;
+  TC acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = (TC)0;
+  const bool a_rows_fast = (sai == 1);  // consecutive i contiguous
+  const bool b_rows_fast = (sbk == 1);  // consecutive k contiguous
+  for (int64_t k0 = 0; k0 < K; k0 += GBK) {
+    // A tile: GBM x GBK elements, 4 per thread
+#pragma unroll
+    for (int e = 0; e < (GBM * GBK) / GTH; ++e) {
+      int idx = tid + e * GTH;
+      int ii, kk;
+      if (a_rows_fast) {
+        ii = idx % GBM;
+        kk = idx / GBM;
+      } else {
+        kk = idx % GBK;
+        ii = idx / GBK;
+      }
+      int64_t gi = i0 + ii, gk = k0 + kk;
+      sA[kk][ii] = (gi < M && gk < K) ? (TC)A[gi * sai + gk * sak] : (TC)0;
+    }
+#pragma unroll
+    for (int e = 0; e < (GBN * GBK) / GTH; ++e) {
+      int idx = tid + e * GTH;
+      int jj, kk;
+      if (b_rows_fast) {
+        kk = idx % GBK;
+        jj = idx / GBK;
+      } else {
+        jj = idx % GBN;
+        kk = idx / GBN;
+      }
+      int64_t gj = j0 + jj, gk = k0 + kk;
+      sB[kk][jj] = (gj < N && gk < K) ? (TC)B[gk * sbk + gj * sbj] : (TC)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      TC a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = sA[kk][ty + 16 * u];
+        b[u] = sB[kk][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int64_t gi = i0 + ty + 16 * u;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int64_t gj = j0 + tx + 16 * v;
+      if (gj >= N) continue;
+      TC* c = C + gi + gj * ldc;
+      *c = (beta == (TC)0) ? alpha * acc[u][v] : fma(alpha, acc[u][v], beta * *c);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gemm(int is_f64, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int a_f64,
+                        int64_t sai, int64_t sak, const void* B, int64_t sbk, int64_t sbj, double beta, void* C,
+                        int64_t ldc, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((M + GBM - 1) / GBM), (unsigned)((N + GBN - 1) / GBN));
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  if (is_f64) {
+    if (a_f64 == 1)
+      k_gemm<double, double, double><<<grid, GTH, 0, st>>>(M, N, K, alpha, (const double*)A, sai, sak,
+                                                           (const double*)B, sbk, sbj, beta, (double*)C, ldc);
+    else if (a_f64 == 0)
+      k_gemm<float, double, double><<<grid, GTH, 0, st>>>(M, N, K, alpha, (const float*)A, sai, sak,
+                                                          (const double*)B, sbk, sbj, beta, (double*)C, ldc);
+    else  // a_f64 == 2: FP32 A and B, FP64 accumulation and output (exact products)
+      k_gemm<float, float, double><<<grid, GTH, 0, st>>>(M, N, K, alpha, (const float*)A, sai, sak,
+                                                         (const float*)B, sbk, sbj, beta, (double*)C, ldc);
+  } else {
+    if (a_f64) return cudaErrorInvalidValue;
+    k_gemm<float, float, float><<<grid, GTH, 0, st>>>(M, N, K, (float)alpha, (const float*)A, sai, sak,
+                                                      (const float*)B, sbk, sbj, (float)beta, (float*)C, ldc);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace bk

@@ -1,0 +1,400 @@
+// Kernels of the block-Lanczos drivers (ridge path and Gaussian sampling):
+//   k_chol_inv      Cholesky with dropped dependent columns and the inverse factor of an
+//                   m x m FP64 Gram (m <= 256), for the CholQR orthogonalisation of a block
+//   k_band_*        the banded block-tridiagonal T_t (Sec. 3.2, Thm. cost): assembly
+//                   from the Lanczos blocks, shifted Cholesky solves for many shifts in
+//                   one launch (one CTA per shift), and the banded product T_t Y
+//   small helpers   FP32/FP64 block copies, scaled column sums, residual norms
+#include "bk_common.cuh"
+
+namespace bk {
+namespace {
+
+// 1/sqrt(x), x > 0 normal: FP32 estimate of an exactly rescaled argument, two Newton
+// steps in FP64 (quadratic convergence).
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const int e = ((__double2hiint(x) >> 20) & 0x7ff) - 1023;
+  const int h = e >> 1;
+  const double xs = x * __hiloint2double((1023 - 2 * h) << 20, 0);
+  double r = (double)rsqrtf((float)xs) * __hiloint2double((1023 - h) << 20, 0);
+  r = r * fma(-0.5 * x, r * r, 1.5);
+  r = r * fma(-0.5 * x, r * r, 1.5);
+  return r;
+}
+
+constexpr int kCholThreads = 1024;
+
+// One CTA. G (m x m, row-major, FP64) = W^T W of a block W. Writes
+//   R     (m x m, row-major, upper): W = Q R on the kept columns (R rows of dropped
+//         columns are zero; their entries above the diagonal record the dependence)
+//   Rinv  (m x m, row-major, upper): Q = W Rinv, zero rows/columns for dropped columns
+//   keep  (m ints): 1 for kept columns
+// with the factorisation done on D^{-1/2} G D^{-1/2} (D = diag G), dropping a column
+// whose scaled pivot is <= rank_tol. work: m * m doubles of scratch (global).
+// Returns the number of kept columns in *rank.
+__global__ void __launch_bounds__(kCholThreads) k_chol_inv(int m, const double* __restrict__ G, double rank_tol,
+                                                          double* work, double* R, double* Rinv, int* keep,
+                                                          int* rank) {
+  const int tid = threadIdx.x;
+  __shared__ double s_rs[256];     // D^{-1/2}
+  __shared__ double s_invd[256];   // 1 / L[k][k] (0 for dropped)
+  __shared__ int s_keep[256];
+  __shared__ int s_rank;
+  double* L = work;  // m x m row-major, lower triangle used
+  for (int i = tid; i < m; i += kCholThreads) {
+    const double g = G[i * m + i];
+    s_rs[i] = (g > 0.0 && isfinite(g)) ? rsqrt_nr(g) : 0.0;
+  }
+  if (tid == 0) s_rank = 0;
+  __syncthreads();
+  for (int idx = tid; idx < m * m; idx += kCholThreads) {
+    const int r = idx / m, c = idx - r * m;
+    L[idx] = G[idx] * s_rs[r] * s_rs[c];
+  }
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    if (tid == 0) {
+      const double x = L[k * m + k];
+      const bool kp = (s_rs[k] > 0.0) && (x > rank_tol);
+      const double r = kp ? rsqrt_nr(x) : 0.0;
+      L[k * m + k] = kp ? x * r : 0.0;
+      s_invd[k] = r;
+      s_keep[k] = kp;
+      s_rank += kp;
+    }
+    __syncthreads();
+    const double inv = s_invd[k];
+    for (int i = k + 1 + tid; i < m; i += kCholThreads) L[i * m + k] *= inv;
+    __syncthreads();
+    if (inv != 0.0) {
+      const int nt = m - k - 1;
+      for (int idx = tid; idx < nt * nt; idx += kCholThreads) {
+        const int i = k + 1 + idx / nt, j = k + 1 + idx % nt;
+        if (j <= i) L[i * m + j] = fma(-L[i * m + k], L[j * m + k], L[i * m + j]);
+      }
+    }
+    __syncthreads();
+  }
+  // R = L^T D^{1/2}: R[i][j] = L[j][i] / rs[j] for j >= i (upper)
+  for (int idx = tid; idx < m * m; idx += kCholThreads) {
+    const int i = idx / m, j = idx - i * m;
+    double v = 0.0;
+    if (j >= i && s_keep[i] && s_rs[j] > 0.0) v = L[j * m + i] / s_rs[j];
+    R[idx] = v;
+  }
+  // Rinv = D^{-1/2} L^{-T}: column c of L^{-T} is row c of L^{-1}; L^{-1} by forward
+  // substitution, one unit vector per thread group (columns c in parallel)
+  __syncthreads();
+  for (int c = tid; c < m; c += kCholThreads) {
+    // column c of L^{-1}: solve L y = e_c (kept indices only), write Rinv[j][c] later
+    for (int j = 0; j < m; ++j) Rinv[j * m + c] = 0.0;
+    if (!s_keep[c]) continue;
+    // y_j for j >= c
+    for (int j = c; j < m; ++j) {
+      if (!s_keep[j]) continue;
+      double s = (j == c) ? 1.0 : 0.0;
+      for (int l = c; l < j; ++l) s = fma(-L[j * m + l], Rinv[l * m + c], s);  // Rinv[l][c] holds y_l
+      Rinv[j * m + c] = s * s_invd[j];
+    }
+  }
+  __syncthreads();
+  // now Rinv[j][c] = (L^{-1})[j][c]; Rinv_final[i][j] = rs[i] * (L^{-1})[j][i] (upper)
+  for (int idx = tid; idx < m * m; idx += kCholThreads) {
+    const int i = idx / m, j = idx - i * m;
+    work[idx] = (j >= i) ? s_rs[i] * Rinv[j * m + i] : 0.0;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < m * m; idx += kCholThreads) Rinv[idx] = work[idx];
+  for (int i = tid; i < m; i += kCholThreads) keep[i] = s_keep[i];
+  if (tid == 0) *rank = s_rank;
+}
+
+// Band storage of the symmetric block-tridiagonal T (half-bandwidth bw, row stride ldb
+// >= the largest n used): band[r * ldb + c] = T(c + r, c) for 0 <= r <= bw.
+// Adds the m x m diagonal block A (row-major) at block k and the subdiagonal block B
+// (rows of block k+1, columns of block k) when B is non-null.
+__global__ void k_band_put(int ldb, int bw, int m, int k, const double* __restrict__ A, const double* __restrict__ B,
+                           double* band) {
+  const int c0 = k * m;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m * m; idx += gridDim.x * blockDim.x) {
+    const int i = idx / m, j = idx - i * m;
+    if (i >= j) band[(size_t)(i - j) * ldb + c0 + j] = 0.5 * (A[i * m + j] + A[j * m + i]);
+    if (B) {
+      // T(c0 + m + i, c0 + j) = B[i][j]; B is upper triangular, so r = m + i - j <= m
+      const int r = m + i - j;
+      if (r <= bw && c0 + j < ldb) band[(size_t)r * ldb + c0 + j] = B[i * m + j];
+    }
+  }
+}
+
+// Shifted banded Cholesky solves, one CTA per shift j:
+//   (T + mu_j I) Z_j = E_j, E_j = the nrhs columns of rhs starting at column rhs_col[j]
+//   (rhs: n x ncol column-major, ld n).
+// A diagonal entry that is exactly zero (a dropped Lanczos direction) is replaced by 1
+// so the dropped direction decouples. work: L x (bw + 2) x n doubles (the factor and
+// the reciprocal diagonal). Z_j is n x nrhs column-major at Z + j * n * nrhs.
+// flags[j] = 1 if a pivot was not positive. Cost O(n bw^2) per shift (Thm. cost).
+__global__ void __launch_bounds__(256) k_band_solve(int n, int bw, const double* __restrict__ band, int ldb,
+                                                    const double* __restrict__ mus, const double* __restrict__ rhs,
+                                                    const int* __restrict__ rhs_col, int nrhs, double* work,
+                                                    double* Z, int* flags) {
+  const int j = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+  double* Lb = work + (size_t)j * (bw + 2) * n;
+  double* invL = Lb + (size_t)(bw + 1) * n;
+  double* z = Z + (size_t)j * n * nrhs;
+  const double mu = mus[j];
+  const double* e = rhs + (size_t)rhs_col[j] * n;
+  __shared__ double s_inv;
+  __shared__ int s_bad;
+  for (size_t idx = tid; idx < (size_t)(bw + 1) * n; idx += nth) {
+    const int r = (int)(idx / n), c = (int)(idx % n);
+    // entries that reach past the end of T_t (rows >= n) are not part of it
+    double v = (c + r < n) ? band[(size_t)r * ldb + c] : 0.0;
+    if (r == 0) v = (v == 0.0) ? 1.0 : v + mu;
+    Lb[idx] = v;
+  }
+  for (size_t idx = tid; idx < (size_t)n * nrhs; idx += nth) z[idx] = e[idx];
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  // factorisation, column by column: L(c, c) = sqrt(pivot) formed by one thread
+  for (int c = 0; c < n; ++c) {
+    if (tid == 0) {
+      const double x = Lb[c];
+      if (!(x > 0.0)) {
+        s_bad = 1;
+        s_inv = 0.0;
+      } else {
+        const double r = rsqrt_nr(x);
+        Lb[c] = x * r;
+        s_inv = r;
+      }
+      invL[c] = s_inv;
+    }
+    __syncthreads();
+    const double inv = s_inv;
+    const int w = min(bw, n - 1 - c);
+    for (int r = 1 + tid; r <= w; r += nth) Lb[(size_t)r * n + c] *= inv;
+    __syncthreads();
+    // trailing window T(c+a, c+b) -= L(c+a, c) L(c+b, c), 1 <= b <= a <= w:
+    // warps over a, lanes over b
+    for (int a = 1 + warp; a <= w; a += nw) {
+      const double la = Lb[(size_t)a * n + c];
+      for (int b = 1 + lane; b <= a; b += 32) {
+        double* t = Lb + (size_t)(a - b) * n + (c + b);
+        *t = fma(-la, Lb[(size_t)b * n + c], *t);
+      }
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (tid == 0) flags[j] = 1;
+    return;
+  }
+  // forward L y = e, column-oriented: y_c *= 1/L_cc, then y_{c+r} -= L(c+r, c) y_c
+  for (int c = 0; c < n; ++c) {
+    const double inv = invL[c];
+    for (int q = tid; q < nrhs; q += nth) z[(size_t)q * n + c] *= inv;
+    __syncthreads();
+    const int w = min(bw, n - 1 - c);
+    for (int idx = tid; idx < w * nrhs; idx += nth) {
+      const int r = 1 + idx % w, q = idx / w;
+      z[(size_t)q * n + c + r] = fma(-Lb[(size_t)r * n + c], z[(size_t)q * n + c], z[(size_t)q * n + c + r]);
+    }
+    __syncthreads();
+  }
+  // backward L^T z = y, column-oriented: z_c *= 1/L_cc, then z_{c-r} -= L(c, c-r) z_c
+  for (int c = n - 1; c >= 0; --c) {
+    const double inv = invL[c];
+    for (int q = tid; q < nrhs; q += nth) z[(size_t)q * n + c] *= inv;
+    __syncthreads();
+    const int w = min(bw, c);
+    for (int idx = tid; idx < w * nrhs; idx += nth) {
+      const int r = 1 + idx % w, q = idx / w;
+      z[(size_t)q * n + c - r] = fma(-Lb[(size_t)r * n + c - r], z[(size_t)q * n + c], z[(size_t)q * n + c - r]);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) flags[j] = 0;
+}
+
+// out (n x nc, column-major) = T Y for the banded symmetric T (band storage).
+__global__ void k_band_mult(int n, int bw, const double* __restrict__ band, int ldb, const double* __restrict__ Y,
+                            int nc, double* out) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)n * nc;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n), q = (int)(idx / n);
+    double s = 0.0;
+    const int lo = max(0, i - bw), hi = min(n - 1, i + bw);
+    for (int k = lo; k <= hi; ++k) {
+      const double t = (k <= i) ? band[(size_t)(i - k) * ldb + k] : band[(size_t)(k - i) * ldb + i];
+      s = fma(t, Y[(size_t)q * n + k], s);
+    }
+    out[idx] = s;
+  }
+}
+
+// Y (n x nc) = sum_j c_j Z_j for L stacked n x nc blocks.
+__global__ void k_combine_shifts(int n, int nc, int L, const double* __restrict__ Z, const double* __restrict__ c,
+                                 double* Y) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)n * nc;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < L; ++j) s = fma(c[j], Z[(size_t)j * n * nc + idx], s);
+    Y[idx] = s;
+  }
+}
+
+// ||B z_last|| per shift: z_last = rows n-m..n-1 of Z_j (column q), B (m x m row-major).
+__global__ void k_lanczos_res(int n, int m, int L, int nrhs, const double* __restrict__ Blast,
+                              const double* __restrict__ Z, double* out) {
+  // one warp per (shift, rhs)
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= L * nrhs) return;
+  const int j = w / nrhs, q = w % nrhs;
+  const double* zl = Z + (size_t)j * n * nrhs + (size_t)q * n + (n - m);
+  double ss = 0.0;
+  for (int i = lane; i < m; i += 32) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) s = fma(Blast[i * m + k], zl[k], s);
+    ss = fma(s, s, ss);
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0) out[w] = sqrt(ss);
+}
+
+// Column c of a d x m block (column-major, ld) times scale[c]; FP32 or FP64.
+template <typename T>
+__global__ void k_scale_cols(int64_t d, int m, int64_t ld, const double* __restrict__ scale, T* X) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < d * m;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = idx / d, i = idx - c * d;
+    X[c * ld + i] = (T)((double)X[c * ld + i] * scale[c]);
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void k_copy_cols(int64_t d, int m, const TI* __restrict__ in, int64_t ldi, TO* out, int64_t ldo) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < d * m;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = idx / d, i = idx - c * d;
+    out[c * ldo + i] = (TO)in[c * ldi + i];
+  }
+}
+
+// R = B 1^T - (A X + X diag(mu)) given AX (d x L, FP64): column norms squared partials.
+__global__ void k_shift_residual(int64_t d, int L, const double* __restrict__ b, const double* __restrict__ AX,
+                                 const double* __restrict__ X, int64_t ld, const double* __restrict__ mus,
+                                 double* R, double* norms2) {
+  // one CTA per column
+  const int j = blockIdx.x;
+  __shared__ double red[32];
+  double ss = 0.0;
+  for (int64_t i = threadIdx.x; i < d; i += blockDim.x) {
+    const double r = b[i] - (AX[j * ld + i] + mus[j] * X[j * ld + i]);
+    R[j * ld + i] = r;
+    ss = fma(r, r, ss);
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) norms2[j] = s;
+  }
+}
+
+// rhs (n x mb, column-major, ld n) = E_1 R_0: rhs(i, q) = R0[i][q] for i < mb, else 0.
+__global__ void k_e1r0(int n, int mb, const double* __restrict__ R0, double* rhs) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)n * mb;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n), q = (int)(idx / n);
+    rhs[idx] = (i < mb) ? R0[i * mb + q] : 0.0;
+  }
+}
+
+inline int cgrid(int64_t work, int th) {
+  int64_t g = (work + th - 1) / th;
+  if (g < 1) g = 1;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_e1r0(int n, int mb, const double* R0, double* rhs, cudaStream_t st) {
+  k_e1r0<<<cgrid((int64_t)n * mb, 256), 256, 0, st>>>(n, mb, R0, rhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_inv(int m, const double* G, double rank_tol, double* work, double* R, double* Rinv,
+                            int* keep, int* rank, cudaStream_t st) {
+  if (m < 1 || m > 256) return cudaErrorInvalidValue;
+  k_chol_inv<<<1, kCholThreads, 0, st>>>(m, G, rank_tol, work, R, Rinv, keep, rank);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_put(int ldb, int bw, int m, int k, const double* A, const double* B, double* band,
+                            cudaStream_t st) {
+  k_band_put<<<cgrid((int64_t)m * m, 256), 256, 0, st>>>(ldb, bw, m, k, A, B, band);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_solve(int n, int bw, const double* band, int ldb, int L, const double* mus,
+                              const double* rhs, const int* rhs_col, int nrhs, double* work, double* Z, int* flags,
+                              cudaStream_t st) {
+  if (L <= 0) return cudaSuccess;
+  k_band_solve<<<L, 256, 0, st>>>(n, bw, band, ldb, mus, rhs, rhs_col, nrhs, work, Z, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_mult(int n, int bw, const double* band, int ldb, const double* Y, int nc, double* out,
+                             cudaStream_t st) {
+  k_band_mult<<<cgrid((int64_t)n * nc, 256), 256, 0, st>>>(n, bw, band, ldb, Y, nc, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_shifts(int n, int nc, int L, const double* Z, const double* c, double* Y,
+                                  cudaStream_t st) {
+  k_combine_shifts<<<cgrid((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, L, Z, c, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_res(int n, int m, int L, int nrhs, const double* Blast, const double* Z, double* out,
+                               cudaStream_t st) {
+  int warps = L * nrhs;
+  k_lanczos_res<<<(warps * 32 + 255) / 256, 256, 0, st>>>(n, m, L, nrhs, Blast, Z, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_cols(int is_f64, int64_t d, int m, int64_t ld, const double* scale, void* X,
+                              cudaStream_t st) {
+  if (is_f64)
+    k_scale_cols<double><<<cgrid(d * m, 256), 256, 0, st>>>(d, m, ld, scale, (double*)X);
+  else
+    k_scale_cols<float><<<cgrid(d * m, 256), 256, 0, st>>>(d, m, ld, scale, (float*)X);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_cols(int in_f64, int out_f64, int64_t d, int m, const void* in, int64_t ldi, void* out,
+                             int64_t ldo, cudaStream_t st) {
+  int g = cgrid(d * m, 256);
+  if (in_f64 && out_f64)
+    k_copy_cols<double, double><<<g, 256, 0, st>>>(d, m, (const double*)in, ldi, (double*)out, ldo);
+  else if (in_f64)
+    k_copy_cols<double, float><<<g, 256, 0, st>>>(d, m, (const double*)in, ldi, (float*)out, ldo);
+  else if (out_f64)
+    k_copy_cols<float, double><<<g, 256, 0, st>>>(d, m, (const float*)in, ldi, (double*)out, ldo);
+  else
+    k_copy_cols<float, float><<<g, 256, 0, st>>>(d, m, (const float*)in, ldi, (float*)out, ldo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift_residual(int64_t d, int L, const double* b, const double* AX, const double* X, int64_t ld,
+                                  const double* mus, double* R, double* norms2, cudaStream_t st) {
+  k_shift_residual<<<L, 256, 0, st>>>(d, L, b, AX, X, ld, mus, R, norms2);
+  return cudaGetLastError();
+}
+
+}  // namespace bk

@@ -199,3 +199,34 @@ def inner_start_block(r: np.ndarray, omega_unscaled: np.ndarray) -> np.ndarray:
     [r / ||r||, Omega / sqrt(d)] (column scaling leaves the column-0 iterate unchanged)."""
     d = r.shape[0]
     return np.column_stack([r / np.linalg.norm(r), omega_unscaled / np.sqrt(d)])
+
+
+# --------------------------------------------------------------------------------------
+# Ridge regression: Z = U diag(sigma) V^T + noise, f ~ N(0, I), b = Z^T f.
+# --------------------------------------------------------------------------------------
+def householder_orthonormal(seed: int, n: int, d: int, reflectors: int = 16, stream: int = STREAM_FACTORS,
+                            offset: int = 0) -> np.ndarray:
+    """First d columns of H_1 ... H_k (k Householder reflectors with Gaussian vectors),
+    an n x d matrix with orthonormal columns."""
+    Q = np.zeros((n, d))
+    Q[np.arange(d), np.arange(d)] = 1.0
+    for r in range(reflectors):
+        v = normals(seed, stream, n, offset=offset + r * n)
+        v /= np.linalg.norm(v)
+        Q -= 2.0 * np.outer(v, v @ Q)
+    return Q
+
+
+def ridge_workload(seed: int, n: int, d: int, noise_std: float, dtype=np.float32):
+    """Z (n x d, row-major, dtype) with singular values 1/i plus N(0, noise_std^2) noise,
+    f ~ N(0, I_n) and b = Z^T f computed from the stored Z in float64."""
+    U = householder_orthonormal(seed, n, d)
+    V = householder_orthonormal(seed, d, d, offset=16 * n)
+    sig = 1.0 / np.arange(1, d + 1)
+    Z = (U * sig[None, :]) @ V.T
+    if noise_std > 0:
+        Z += noise_std * normals(seed, STREAM_NOISE, n * d).reshape(n, d)
+    Z = np.ascontiguousarray(Z.astype(dtype))
+    f = normals(seed, STREAM_RHS, n)
+    b = Z.astype(np.float64).T @ f
+    return Z, f, b
