@@ -173,6 +173,35 @@ bk_status bk_solve(bk_ctx* ctx, const bk_operator* A, double mu, const double* b
 bk_status bk_ridge_path(bk_ctx* ctx, const bk_operator* A, int32_t L, const double* mus, const double* b,
                         double* X, const bk_opts* opts, bk_info* info);
 
+/* Gaussian sampling S ~= (K + nugget I)^{1/2} B by the block-Lanczos square root of
+ * Def. blansq (Sec. 5): block-Lanczos with full reorthogonalisation on (K, B) (block
+ * width m, the samples themselves are the start block), then
+ *   S = (2/pi) int_0^inf A bcg_t(z^2) dz,  A = K + nugget I,
+ * evaluated with the quadrature of bk_sqrt_quadrature on [nugget, Gershgorin bound of
+ * T_t + nugget] and the Lanczos relation A Q_t = Q_t T_t + Q_{t+1} B_t E_t^T:
+ *   S = Q_t (T_t + nugget) Ybar + Q_{t+1} B_t E_t^T Ybar,  Ybar = sum_j w_j Y_j,
+ *   Y_j = (T_t + (nugget + z_j^2) I)^{-1} E_1 R_0  (all n_quad shifts in one launch).
+ * Stops when S changes by at most tol (relative Frobenius norm) between checks made
+ * every check_every loads, or when K_t fills R^d.
+ *   K      BK_DENSE or BK_GRAM (FP32 or FP64 values); nugget >= 0 (if 0, K must be
+ *          positive definite and the interval starts at 1e-12 times its upper end)
+ *   B      d x m column-major doubles (host or device), 1 <= m <= 256; S: d x m output
+ *   n_quad quadrature nodes (1..1024; 32 gives about 1e-12 for a spectral ratio of 1e8)
+ *   info   loads, refinements (= checks made), rel_residual (= last relative change) */
+bk_status bk_sample(bk_ctx* ctx, const bk_operator* K, double nugget, int32_t m, const double* B, double* S,
+                    int32_t n_quad, const bk_opts* opts, bk_info* info);
+
+/* Quadrature for the square root (Sec. 1, Eq. sqrt_rational; Sec. 5 Def. blansq):
+ * nodes z_j^2 and weights w_j, j < n, with
+ *     sqrt(lambda) ~= sum_j w_j lambda / (lambda + z_j^2)   for lambda in [lo, hi],
+ * from the substitution z = sqrt(lo) sc(u | 1 - lo/hi), which maps [0, inf) onto
+ * [0, K(1 - lo/hi)] with dz / sqrt((lo + z^2)(hi + z^2)) = du / sqrt(hi) (the identity of
+ * Eq. ellipticK_eval), and the midpoint rule in u. The error decays geometrically in
+ * n: about 1e-12 relative at n = 32 for hi/lo = 1e8. Host computation (no device use):
+ * K by the arithmetic-geometric mean, sn/cn/dn by the descending recursion of
+ * Abramowitz & Stegun 16.4. z2, w: n doubles each (host). 0 < lo <= hi. */
+bk_status bk_sqrt_quadrature(double lo, double hi, int32_t n, double* z2, double* w);
+
 /* One block product with its Gram matrix (one "matrix-load", Sec. 1.2):
  *   Y = A P + mu P  and  G = P^T Y  (m x m, FP64, row-major).
  * P and Y are d x m blocks in the panel layout above (leading dimension ld), element type `dtype`

@@ -28,7 +28,8 @@ BK_PREC_FP64, BK_PREC_FP32 = 0, 1
 
 EXPORTS = ("bk_default_opts", "bk_create", "bk_destroy", "bk_set_stream", "bk_status_string", "bk_last_error",
            "bk_solve",
-           "bk_block_apply", "bk_gram", "bk_chol_solve", "bk_gaussian", "bk_block_apply_static", "bk_ridge_path")
+           "bk_block_apply", "bk_gram", "bk_chol_solve", "bk_gaussian", "bk_block_apply_static", "bk_ridge_path",
+           "bk_sqrt_quadrature", "bk_sample")
 
 
 class Operator(ctypes.Structure):
@@ -78,6 +79,9 @@ def _load():
         "bk_chol_solve": (i32, [vp, i64, vp, vp, vp]),
         "bk_gaussian": (i32, [vp, u64, ctypes.c_uint32, i64, i64, vp]),
         "bk_block_apply_static": (i32, [ctypes.POINTER(Operator), dbl, i32, i64, vp, vp, i64, vp, vp]),
+        "bk_sqrt_quadrature": (i32, [dbl, dbl, i32, vp, vp]),
+        "bk_sample": (i32, [vp, ctypes.POINTER(Operator), dbl, i32, vp, vp, i32, ctypes.POINTER(Opts),
+                            ctypes.POINTER(Info)]),
         "bk_ridge_path": (i32, [vp, ctypes.POINTER(Operator), i32, vp, vp, vp, ctypes.POINTER(Opts),
                                 ctypes.POINTER(Info)]),
     }
@@ -317,3 +321,28 @@ def block_apply_static(A: OperatorRef, mu: float, P, Y, G, m: int, ld: int, stre
     py, ky = _ptr(Y)
     pg, kg = _ptr(G)
     return _lib.bk_block_apply_static(ctypes.byref(A.op), float(mu), dt, int(m), pp, py, int(ld), pg, stream)
+
+
+def sqrt_quadrature(lo: float, hi: float, n: int):
+    """bk_sqrt_quadrature: (z_j^2, w_j) with sqrt(x) ~= sum_j w_j x / (x + z_j^2) on [lo, hi]."""
+    z2 = np.zeros(n)
+    w = np.zeros(n)
+    st = _lib.bk_sqrt_quadrature(float(lo), float(hi), int(n), z2.ctypes.data, w.ctypes.data)
+    if st != BK_OK:
+        raise BKError(st, "bk_sqrt_quadrature")
+    return z2, w
+
+
+def sample(ctx: Context, K: OperatorRef, nugget: float, B, S, n_quad: int = 32, opts: Opts | None = None,
+           check=True) -> Info:
+    """bk_sample: S ~= (K + nugget I)^{1/2} B (B, S d x m column-major)."""
+    info = Info()
+    pb, kb = _ptr(B)
+    ps, ks = _ptr(S)
+    m = B.shape[1]
+    o = opts if opts is not None else default_opts()
+    st = _lib.bk_sample(ctx.handle, ctypes.byref(K.op), float(nugget), int(m), pb, ps, int(n_quad),
+                        ctypes.byref(o), ctypes.byref(info))
+    if check and st != BK_OK:
+        raise BKError(st, "bk_sample", ctx.last_error())
+    return info

@@ -139,8 +139,9 @@ cudaError_t launch_band_put(int ldb, int bw, int m, int k, const double* A, cons
 cudaError_t launch_band_solve(int n, int bw, const double* band, int ldb, int L, const double* mus,
                               const double* rhs, const int* rhs_col, int nrhs, double* work, double* Z, int* flags,
                               cudaStream_t st);
-cudaError_t launch_band_mult(int n, int bw, const double* band, int ldb, const double* Y, int nc, double* out,
-                             cudaStream_t st);
+cudaError_t launch_band_mult(int n, int bw, const double* band, int ldb, double shift, const double* Y, int nc,
+                             double* out, cudaStream_t st);
+cudaError_t launch_band_gersh(int n, int bw, const double* band, int ldb, double* out, cudaStream_t st);
 cudaError_t launch_combine_shifts(int n, int nc, int L, const double* Z, const double* c, double* Y,
                                   cudaStream_t st);
 cudaError_t launch_lanczos_res(int n, int m, int L, int nrhs, const double* Blast, const double* Z, double* out,

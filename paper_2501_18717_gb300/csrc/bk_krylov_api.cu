@@ -215,7 +215,77 @@ cudaError_t apply_fp64(bk_ctx* c, const LzOp& o, const double* X, int64_t ld, in
                          c->stream);
 }
 
+// ---------------------------------------------------------------- sqrt quadrature
+// Complete elliptic integral of the first kind K(m) = pi / (2 AGM(1, sqrt(1 - m))),
+// 0 <= m < 1 (arithmetic-geometric mean).
+double ellip_k(double m) {
+  double a = 1.0, b = std::sqrt(1.0 - m);
+  for (int it = 0; it < 64 && std::fabs(a - b) > 1e-16 * a; ++it) {
+    const double an = 0.5 * (a + b);
+    b = std::sqrt(a * b);
+    a = an;
+  }
+  return 3.14159265358979323846 / (2.0 * a);
+}
+
+// Jacobi elliptic functions sn, cn, dn of parameter m by the arithmetic-geometric mean
+// scale and descending recursion of Abramowitz & Stegun 16.4: a_0 = 1, b_0 = sqrt(1-m),
+// c_0 = sqrt(m); phi_N = 2^N a_N u; phi_{n-1} = (phi_n + asin(c_n sin(phi_n) / a_n)) / 2;
+// sn = sin phi_0, cn = cos phi_0, dn = cos phi_0 / cos(phi_1 - phi_0).
+void ellip_j(double u, double m, double* sn, double* cn, double* dn) {
+  if (m < 1e-300) {
+    *sn = std::sin(u);
+    *cn = std::cos(u);
+    *dn = 1.0;
+    return;
+  }
+  double a[64], c[64];
+  a[0] = 1.0;
+  double b = std::sqrt(1.0 - m);
+  c[0] = std::sqrt(m);
+  int n = 0;
+  while (n < 62 && std::fabs(c[n]) > 1e-17) {
+    a[n + 1] = 0.5 * (a[n] + b);
+    c[n + 1] = 0.5 * (a[n] - b);
+    b = std::sqrt(a[n] * b);
+    ++n;
+  }
+  double phi = std::ldexp(a[n] * u, n);
+  double prev = phi;
+  for (int j = n; j > 0; --j) {
+    prev = phi;
+    phi = 0.5 * (phi + std::asin(c[j] * std::sin(phi) / a[j]));
+  }
+  *sn = std::sin(phi);
+  *cn = std::cos(phi);
+  *dn = (n > 0) ? std::cos(phi) / std::cos(prev - phi) : 1.0;
+}
+
+// Nodes and weights of (2/pi) int_0^inf lambda / (lambda + z^2) dz = sqrt(lambda) for
+// lambda in [lo, hi]: the substitution z = sqrt(lo) sc(u | 1 - lo/hi) maps [0, inf) to
+// [0, K] and turns dz / sqrt((lo + z^2)(hi + z^2)) into du / sqrt(hi) (the identity of
+// Eq. ellipticK_eval); the midpoint rule in u then converges geometrically for every
+// lambda in [lo, hi]. Returns z_j^2 and (2/pi) w_j.
+void sqrt_quadrature(double lo, double hi, int N, double* z2, double* w) {
+  const double m = 1.0 - lo / hi;
+  const double K = ellip_k(m);
+  for (int j = 0; j < N; ++j) {
+    const double u = (j + 0.5) * K / N;
+    double sn, cn, dn;
+    ellip_j(u, m, &sn, &cn, &dn);
+    const double z = std::sqrt(lo) * sn / cn;
+    z2[j] = z * z;
+    w[j] = (2.0 / 3.14159265358979323846) * (K / N) * std::sqrt(lo) * dn / (cn * cn);
+  }
+}
+
 }  // namespace
+
+extern "C" bk_status bk_sqrt_quadrature(double lo, double hi, int32_t n, double* z2, double* w) {
+  if (!z2 || !w || n < 1 || !(lo > 0.0) || !(hi >= lo) || !std::isfinite(hi)) return BK_ERR_ARG;
+  sqrt_quadrature(lo, hi, n, z2, w);
+  return BK_OK;
+}
 
 extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, const double* mus, const double* b,
                                    double* X, const bk_opts* opts_in, bk_info* info) {
@@ -375,6 +445,133 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
     info->refinements = refinements;
     info->residual_loads = residual_loads;
     info->rel_residual = worst;
+    info->ms_total = ms;
+  }
+  return result;
+}
+
+extern "C" bk_status bk_sample(bk_ctx* c, const bk_operator* Kop, double nugget, int32_t m, const double* B,
+                               double* S, int32_t n_quad, const bk_opts* opts_in, bk_info* info) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!c || !B || !S || m < 1 || m > 256 || n_quad < 1 || n_quad > 1024 || !(nugget >= 0.0) ||
+      !std::isfinite(nugget))
+    return BK_ERR_ARG;
+  err_ctx() = c;
+  c->last_error[0] = 0;
+  LzOp o;
+  bk_status s = check_lz_operator(Kop, &o);
+  if (s != BK_OK) return s;
+  bk_opts opts;
+  if (opts_in)
+    opts = *opts_in;
+  else
+    bk_default_opts(&opts);
+  if (!(opts.tol > 0.0) || opts.max_loads < 1 || opts.check_every < 1) return BK_ERR_ARG;
+  if (opts.inner != BK_PREC_FP64 && opts.inner != BK_PREC_FP32) return BK_ERR_UNSUPPORTED;
+  const int is64 = opts.inner == BK_PREC_FP64;
+  const int64_t d = o.d;
+  if (m > d) return BK_ERR_ARG;
+  BK_CK(cudaSetDevice(c->device));
+  cudaStream_t st = c->stream;
+  cudaEvent_t ev0, ev1;
+  BK_CK(cudaEventCreate(&ev0));
+  BK_CK(cudaEventCreate(&ev1));
+  BK_CK(cudaEventRecord(ev0, st));
+  const void* staged = nullptr;
+  BK_CK(stage_lz_values(c, Kop, &o, is64, &staged));
+  const double* Bd = nullptr;
+  BK_CK(stage_in(c, WS_B64, B, (size_t)d * m * 8, (const void**)&Bd));
+
+  const int tmax = (int)std::min<int64_t>((d + m - 1) / m + 1, opts.max_loads);
+  Lanczos lz;
+  BK_CK(lz.init(c, o, is64, m, tmax));
+  BK_CK(bk::launch_copy_cols(1, is64, d, m, Bd, d, lz.W, lz.ldq, st));
+  BK_CK(lz.start(lz.W));
+
+  const int N = n_quad;
+  double *dmu = nullptr, *rhs = nullptr, *bwork = nullptr, *Z = nullptr, *Ybar = nullptr, *M1 = nullptr;
+  double *Sd = nullptr, *Sprev = nullptr, *small = nullptr;
+  BK_CK(ws_get(c, WS_LSHIFT, (size_t)N * 8 * 2 + 8192, (void**)&dmu));
+  double* dw = dmu + N;
+  int* rhs_col = (int*)(dw + N);
+  int* flags = rhs_col + 1024;
+  BK_CK(cudaMemsetAsync(rhs_col, 0, (size_t)N * 4, st));
+  const int64_t nmax = lz.ncol_max;
+  BK_CK(ws_get(c, WS_LRHS, (size_t)nmax * m * 8 * 3 + (size_t)m * m * 8, (void**)&rhs));
+  Ybar = rhs + (size_t)nmax * m;
+  M1 = Ybar + (size_t)nmax * m;
+  small = M1 + (size_t)nmax * m;
+  BK_CK(ws_get(c, WS_LBWORK, (size_t)N * (m + 2) * nmax * 8, (void**)&bwork));
+  BK_CK(ws_get(c, WS_LZ, (size_t)N * nmax * m * 8, (void**)&Z));
+  BK_CK(ws_get(c, WS_LX, (size_t)d * m * 8, (void**)&Sd));
+  BK_CK(ws_get(c, WS_LAX, (size_t)d * m * 8, (void**)&Sprev));
+  double* normp = nullptr;
+  BK_CK(ws_get(c, WS_NORMP, kHostParts * 8, (void**)&normp));
+  std::vector<double> hz2(N), hw(N), hmu(N);
+
+  bk_status result = BK_NOT_CONVERGED;
+  double change = 1.0;
+  int checks = 0;
+  for (;;) {
+    BK_CK(lz.step());
+    const int n = lz.n();
+    const bool last = lz.t >= tmax || n >= d;
+    if (!last && (lz.t % opts.check_every) != 0) continue;
+    // spectrum interval of A = K + nugget I: [nugget, Gershgorin bound of T_t + nugget]
+    BK_CK(bk::launch_band_gersh(n, m, lz.band, lz.ldb(), small, st));
+    BK_CK(cudaMemcpyAsync(c->hparts, small, 8, cudaMemcpyDeviceToHost, st));
+    BK_CK(cudaStreamSynchronize(st));
+    const double hi = c->hparts[0] + nugget;
+    const double lo = nugget > 0.0 ? nugget : 1e-12 * hi;
+    sqrt_quadrature(lo, std::max(hi, lo), N, hz2.data(), hw.data());
+    for (int j = 0; j < N; ++j) hmu[j] = nugget + hz2[j];
+    BK_CK(cudaMemcpyAsync(dmu, hmu.data(), (size_t)N * 8, cudaMemcpyHostToDevice, st));
+    BK_CK(cudaMemcpyAsync(dw, hw.data(), (size_t)N * 8, cudaMemcpyHostToDevice, st));
+    // Y_j = (T_K + (nugget + z_j^2) I)^{-1} E_1 R_0 for all j in one launch
+    BK_CK(bk::launch_e1r0(n, m, lz.R0, rhs, st));
+    BK_CK(bk::launch_band_solve(n, m, lz.band, lz.ldb(), N, dmu, rhs, rhs_col, m, bwork, Z, flags, st));
+    // Ybar = sum_j w_j Y_j; S = Q_t (T_t + nugget) Ybar + Q_{t+1} B_t E_t^T Ybar
+    BK_CK(bk::launch_combine_shifts(n, m, N, Z, dw, Ybar, st));
+    BK_CK(bk::launch_band_mult(n, m, lz.band, lz.ldb(), nugget, Ybar, m, M1, st));
+    BK_CK(bk::launch_gemm(1, d, m, n, 1.0, lz.Q, is64, 1, lz.ldq, M1, 1, n, 0.0, Sd, d, st));
+    // small = B_t (rows n-m.. of Ybar): B_t row-major m x m, Ybar rows n-m..n-1 (ld n)
+    BK_CK(bk::launch_gemm(1, m, m, m, 1.0, lz.Bk, 1, m, 1, Ybar + (n - m), 1, n, 0.0, small, m, st));
+    if (is64) {
+      BK_CK(bk::launch_gemm(1, d, m, m, 1.0, lz.qblock(lz.t), 1, 1, lz.ldq, small, 1, m, 1.0, Sd, d, st));
+    } else {
+      BK_CK(bk::launch_gemm(1, d, m, m, 1.0, lz.qblock(lz.t), 0, 1, lz.ldq, small, 1, m, 1.0, Sd, d, st));
+    }
+    // relative change against the previous check (a-posteriori stopping, Sec. 4 remark)
+    int np = bk::residual_parts(d * m);
+    double s2 = 0.0, d2 = 0.0;
+    BK_CK(bk::launch_norm2_parts(d * m, Sd, normp, np, st));
+    BK_CK(host_sum(c, normp, np, &s2));
+    if (checks > 0) {
+      BK_CK(bk::launch_axpy(d * m, -1.0, Sd, Sprev, st));
+      BK_CK(bk::launch_norm2_parts(d * m, Sprev, normp, np, st));
+      BK_CK(host_sum(c, normp, np, &d2));
+      change = std::sqrt(d2 / std::max(s2, 1e-300));
+    }
+    ++checks;
+    BK_CK(cudaMemcpyAsync(Sprev, Sd, (size_t)d * m * 8, cudaMemcpyDeviceToDevice, st));
+    if ((checks > 1 && change <= opts.tol) || n >= d) {
+      result = BK_OK;
+      break;
+    }
+    if (last) break;
+  }
+  BK_CK(cudaMemcpyAsync(S, Sd, (size_t)d * m * 8, cudaMemcpyDefault, st));
+  BK_CK(cudaEventRecord(ev1, st));
+  BK_CK(cudaEventSynchronize(ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (info) {
+    info->status = result;
+    info->loads = lz.loads;
+    info->refinements = checks;
+    info->rel_residual = change;
     info->ms_total = ms;
   }
   return result;

@@ -218,13 +218,13 @@ __global__ void __launch_bounds__(256) k_band_solve(int n, int bw, const double*
   if (tid == 0) flags[j] = 0;
 }
 
-// out (n x nc, column-major) = T Y for the banded symmetric T (band storage).
-__global__ void k_band_mult(int n, int bw, const double* __restrict__ band, int ldb, const double* __restrict__ Y,
-                            int nc, double* out) {
+// out (n x nc, column-major) = (T + shift I) Y for the banded symmetric T.
+__global__ void k_band_mult(int n, int bw, const double* __restrict__ band, int ldb, double shift,
+                            const double* __restrict__ Y, int nc, double* out) {
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)n * nc;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx % n), q = (int)(idx / n);
-    double s = 0.0;
+    double s = shift * Y[(size_t)q * n + i];
     const int lo = max(0, i - bw), hi = min(n - 1, i + bw);
     for (int k = lo; k <= hi; ++k) {
       const double t = (k <= i) ? band[(size_t)(i - k) * ldb + k] : band[(size_t)(k - i) * ldb + i];
@@ -314,6 +314,26 @@ __global__ void k_e1r0(int n, int mb, const double* __restrict__ R0, double* rhs
   }
 }
 
+// Gershgorin bound max_i sum_k |T(i, k)| of the leading n x n part of the band (one CTA).
+__global__ void k_band_gersh(int n, int bw, const double* __restrict__ band, int ldb, double* out) {
+  __shared__ double red[32];
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    const int lo = max(0, i - bw), hi = min(n - 1, i + bw);
+    for (int k = lo; k <= hi; ++k) s += fabs((k <= i) ? band[(size_t)(i - k) * ldb + k] : band[(size_t)(k - i) * ldb + i]);
+    mx = fmax(mx, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) *out = v;
+  }
+}
+
 inline int cgrid(int64_t work, int th) {
   int64_t g = (work + th - 1) / th;
   if (g < 1) g = 1;
@@ -322,6 +342,11 @@ inline int cgrid(int64_t work, int th) {
 }
 
 }  // namespace
+
+cudaError_t launch_band_gersh(int n, int bw, const double* band, int ldb, double* out, cudaStream_t st) {
+  k_band_gersh<<<1, 1024, 0, st>>>(n, bw, band, ldb, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_e1r0(int n, int mb, const double* R0, double* rhs, cudaStream_t st) {
   k_e1r0<<<cgrid((int64_t)n * mb, 256), 256, 0, st>>>(n, mb, R0, rhs);
@@ -349,9 +374,9 @@ cudaError_t launch_band_solve(int n, int bw, const double* band, int ldb, int L,
   return cudaGetLastError();
 }
 
-cudaError_t launch_band_mult(int n, int bw, const double* band, int ldb, const double* Y, int nc, double* out,
-                             cudaStream_t st) {
-  k_band_mult<<<cgrid((int64_t)n * nc, 256), 256, 0, st>>>(n, bw, band, ldb, Y, nc, out);
+cudaError_t launch_band_mult(int n, int bw, const double* band, int ldb, double shift, const double* Y, int nc,
+                             double* out, cudaStream_t st) {
+  k_band_mult<<<cgrid((int64_t)n * nc, 256), 256, 0, st>>>(n, bw, band, ldb, shift, Y, nc, out);
   return cudaGetLastError();
 }
 

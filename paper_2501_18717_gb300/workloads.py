@@ -230,3 +230,28 @@ def ridge_workload(seed: int, n: int, d: int, noise_std: float, dtype=np.float32
     f = normals(seed, STREAM_RHS, n)
     b = Z.astype(np.float64).T @ f
     return Z, f, b
+
+
+# --------------------------------------------------------------------------------------
+# Gaussian sampling: RBF kernel on uniform points in [0, 1]^3.
+# --------------------------------------------------------------------------------------
+def rbf_points(seed: int, n: int) -> np.ndarray:
+    return uniforms(seed, STREAM_FACTORS, 3 * n).reshape(n, 3)
+
+
+def rbf_kernel(points: np.ndarray, lengthscale: float = 0.2, dtype=np.float64, chunk: int = 2048) -> np.ndarray:
+    """K_ij = exp(-||x_i - x_j||^2 / (2 lengthscale^2)), row-major, built in row chunks."""
+    n = points.shape[0]
+    K = np.empty((n, n), dtype=dtype)
+    sq = (points ** 2).sum(1)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        d2 = sq[s:e, None] + sq[None, :] - 2.0 * points[s:e] @ points.T
+        np.maximum(d2, 0.0, out=d2)
+        K[s:e] = np.exp(-d2 / (2.0 * lengthscale ** 2)).astype(dtype)
+    return K
+
+
+def sample_block(seed: int, d: int, m: int) -> np.ndarray:
+    """B (d x m, Fortran order) of standard normals from the right-hand-side stream."""
+    return normals(seed, STREAM_RHS, d * m).reshape(m, d).T.copy(order="F")
