@@ -62,12 +62,12 @@ def parse():
 
 
 def algorithmic_bytes(d, nnz, m):
-    """Bytes each kernel must move per launch at FP32 block precision."""
+    """Bytes each kernel must move per launch at FP32 block precision (m live columns)."""
     blk = d * m * 4
     return {
         "operator": nnz * (4 + 4) + (d + 1) * 4 + 2 * blk,  # A values+indices, read P, write Y
-        "update_r": 3 * blk,                               # read Y, R; write R
-        "update_p": 3 * blk + 2 * d * 8,                   # read R, P; write P; x read+write (FP64)
+        "update_r": 3 * blk,                               # read Y, Q; write W (over Q)
+        "update_p": 4 * blk + 2 * d * 8,                   # read W, P; write Q, P; x read+write (FP64)
     }
 
 

@@ -191,6 +191,30 @@ bk_status bk_ridge_path(bk_ctx* ctx, const bk_operator* A, int32_t L, const doub
 bk_status bk_sample(bk_ctx* ctx, const bk_operator* K, double nugget, int32_t m, const double* B, double* S,
                     int32_t n_quad, const bk_opts* opts, bk_info* info);
 
+/* Many independent systems (A_i + mu_i I) x_i = b_i of uneven size, i < n, solved
+ * together (bk_solve on each, batched): systems are grouped by padded block width and
+ * every step of the block-CG recurrence (Def. BCG) runs as one launch over all systems
+ * of a group, each system owning thread blocks in proportion to d_i^2 m_i; a chunk of
+ * check_every steps is replayed as a CUDA graph and systems that have converged skip
+ * their work. FP64 refinement restarts as in bk_solve.
+ *   A      n dense operators, all FP32 or all FP64 values (BK_DENSE only)
+ *   mu     n shifts (host array); b, x: n pointers to d_i doubles (host or device)
+ *   opts   as bk_solve; sketch = -1 takes the block width per system from the table that
+ *          bk_autotune filled in this context (nearest size bucket floor(log2 d); 16
+ *          when the table is empty)
+ *   info   n records (may be NULL); ms_total is the whole batch
+ * Returns BK_NOT_CONVERGED if any system missed tol. */
+bk_status bk_solve_batched(bk_ctx* ctx, int32_t n, const bk_operator* A, const double* mu, const double* const* b,
+                           double* const* x, const bk_opts* opts, bk_info* info);
+
+/* Chooses the sketch size per size bucket (floor(log2 d)) by timing bk_solve_batched on
+ * each calibration system with each candidate sketch (one warm and one timed solve) and
+ * keeping the fastest converged one; the table is stored in the context and used by
+ * bk_solve_batched when opts->sketch = -1. Calibrate on systems drawn independently of
+ * the ones to be solved. chosen (n ints, may be NULL) receives the pick per system. */
+bk_status bk_autotune(bk_ctx* ctx, int32_t n, const bk_operator* A, const double* mu, const double* const* b,
+                      const int32_t* candidates, int32_t ncand, const bk_opts* opts, int32_t* chosen);
+
 /* Quadrature for the square root (Sec. 1, Eq. sqrt_rational; Sec. 5 Def. blansq):
  * nodes z_j^2 and weights w_j, j < n, with
  *     sqrt(lambda) ~= sum_j w_j lambda / (lambda + z_j^2)   for lambda in [lo, hi],

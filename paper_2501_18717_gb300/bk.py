@@ -29,7 +29,7 @@ BK_PREC_FP64, BK_PREC_FP32 = 0, 1
 EXPORTS = ("bk_default_opts", "bk_create", "bk_destroy", "bk_set_stream", "bk_status_string", "bk_last_error",
            "bk_solve",
            "bk_block_apply", "bk_gram", "bk_chol_solve", "bk_gaussian", "bk_block_apply_static", "bk_ridge_path",
-           "bk_sqrt_quadrature", "bk_sample")
+           "bk_sqrt_quadrature", "bk_sample", "bk_solve_batched", "bk_autotune")
 
 
 class Operator(ctypes.Structure):
@@ -80,6 +80,8 @@ def _load():
         "bk_gaussian": (i32, [vp, u64, ctypes.c_uint32, i64, i64, vp]),
         "bk_block_apply_static": (i32, [ctypes.POINTER(Operator), dbl, i32, i64, vp, vp, i64, vp, vp]),
         "bk_sqrt_quadrature": (i32, [dbl, dbl, i32, vp, vp]),
+        "bk_solve_batched": (i32, [vp, i32, vp, vp, vp, vp, ctypes.POINTER(Opts), vp]),
+        "bk_autotune": (i32, [vp, i32, vp, vp, vp, vp, i32, ctypes.POINTER(Opts), vp]),
         "bk_sample": (i32, [vp, ctypes.POINTER(Operator), dbl, i32, vp, vp, i32, ctypes.POINTER(Opts),
                             ctypes.POINTER(Info)]),
         "bk_ridge_path": (i32, [vp, ctypes.POINTER(Operator), i32, vp, vp, vp, ctypes.POINTER(Opts),
@@ -346,3 +348,44 @@ def sample(ctx: Context, K: OperatorRef, nugget: float, B, S, n_quad: int = 32, 
     if check and st != BK_OK:
         raise BKError(st, "bk_sample", ctx.last_error())
     return info
+
+
+class Batch:
+    """Marshalled arguments of a batch of dense systems (operator array, shift array,
+    pointer arrays of b and x) for bk_solve_batched and bk_autotune."""
+
+    def __init__(self, mats, mus, bs, xs):
+        n = len(mats)
+        self.ops = [dense_operator(a) for a in mats]
+        self.op_arr = (Operator * n)(*[o.op for o in self.ops])
+        self.mu = np.ascontiguousarray(np.asarray(mus, dtype=np.float64))
+        self.b_arr = (ctypes.c_void_p * n)(*[_ptr(v)[0] for v in bs])
+        self.x_arr = (ctypes.c_void_p * n)(*[_ptr(v)[0] for v in xs])
+        self.keep = (mats, bs, xs)
+        self.n = n
+
+
+def solve_batched(ctx: Context, batch: Batch, opts: Opts | None = None, check=True):
+    """bk_solve_batched: returns the list of per-system Info records."""
+    infos = (Info * batch.n)()
+    o = opts if opts is not None else default_opts()
+    st = _lib.bk_solve_batched(ctx.handle, batch.n, ctypes.cast(batch.op_arr, ctypes.c_void_p),
+                               batch.mu.ctypes.data, ctypes.cast(batch.b_arr, ctypes.c_void_p),
+                               ctypes.cast(batch.x_arr, ctypes.c_void_p), ctypes.byref(o),
+                               ctypes.cast(infos, ctypes.c_void_p))
+    if check and st != BK_OK:
+        raise BKError(st, "bk_solve_batched", ctx.last_error())
+    return list(infos)
+
+
+def autotune(ctx: Context, batch: Batch, candidates, opts: Opts | None = None):
+    """bk_autotune: returns the chosen sketch per calibration system."""
+    cand = np.ascontiguousarray(np.asarray(candidates, dtype=np.int32))
+    chosen = np.zeros(batch.n, dtype=np.int32)
+    o = opts if opts is not None else default_opts()
+    st = _lib.bk_autotune(ctx.handle, batch.n, ctypes.cast(batch.op_arr, ctypes.c_void_p), batch.mu.ctypes.data,
+                          ctypes.cast(batch.b_arr, ctypes.c_void_p), cand.ctypes.data, len(cand), ctypes.byref(o),
+                          chosen.ctypes.data)
+    if st != BK_OK:
+        raise BKError(st, "bk_autotune", ctx.last_error())
+    return chosen

@@ -111,8 +111,8 @@ cudaError_t residual(bk_ctx* c, const OpDev& o, double mu, const double* x, cons
 }
 
 struct SolveBufs {
-  void *P, *R, *Y, *omega, *alpha_t, *beta_t;
-  double *xin, *x64, *r64, *partsG, *partsS, *G, *Sold, *Snew, *alpha, *beta, *normp;
+  void *P, *Q, *Y, *omega, *gi_t, *xc_t, *ti_t, *t_t;
+  double *xin, *x64, *r64, *partsG, *partsS, *G, *S, *cvec, *normp;
   DevState* state;
   int npG, npS;
 };
@@ -367,13 +367,17 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
   // workspace
   const int64_t ld = (d + 31) & ~int64_t(31);
   const size_t es = is64 ? 8 : 4;
-  const int nq = (m + 3) / 4;  // panels of four columns
-  const size_t blk = (size_t)ld * 4 * nq * es;
+  // every block holds all mp / 4 panels of the padded width (the step kernels are
+  // compiled for it); padding columns stay zero
+  const size_t blk = (size_t)ld * mp * es;
   SolveBufs w;
   BK_CK(ws_get(c, WS_P, blk, &w.P));
-  BK_CK(ws_get(c, WS_R, blk, &w.R));
+  BK_CK(ws_get(c, WS_R, blk, &w.Q));
   BK_CK(ws_get(c, WS_Y, blk, &w.Y));
   BK_CK(ws_get(c, WS_OMEGA, blk, &w.omega));
+  BK_CK(cudaMemsetAsync(w.P, 0, blk, st));
+  BK_CK(cudaMemsetAsync(w.Q, 0, blk, st));
+  BK_CK(cudaMemsetAsync(w.Y, 0, blk, st));
   BK_CK(ws_get(c, WS_XIN, (size_t)d * 8, (void**)&w.xin));
   BK_CK(ws_get(c, WS_X64, (size_t)d * 8, (void**)&w.x64));
   BK_CK(ws_get(c, WS_R64, (size_t)d * 8, (void**)&w.r64));
@@ -385,16 +389,16 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
   int npSmax = w.npS > npStart ? w.npS : npStart;
   BK_CK(ws_get(c, WS_PARTS_G, (size_t)w.npG * ne * 8, (void**)&w.partsG));
   BK_CK(ws_get(c, WS_PARTS_S, (size_t)npSmax * ne * 8, (void**)&w.partsS));
-  size_t mm = (size_t)m * m;
+  size_t mm = (size_t)m * m, mpp = (size_t)mp * mp;
   double* mats = nullptr;
-  BK_CK(ws_get(c, WS_MATS, (6 * mm + 2 * (size_t)mp * mp) * 8 + 256, (void**)&mats));
+  BK_CK(ws_get(c, WS_MATS, (2 * mm + 64 + 3 * mpp + mp) * 8 + 256, (void**)&mats));
   w.G = mats;
-  w.Sold = w.G + mm;
-  w.Snew = w.Sold + mm;
-  w.alpha = w.Snew + mm;
-  w.beta = w.alpha + mm;
-  w.alpha_t = (void*)(w.beta + mm);
-  w.beta_t = (void*)((char*)w.alpha_t + (size_t)mp * mp * 8);
+  w.S = w.G + mm;
+  w.cvec = w.S + mm;
+  w.gi_t = (void*)(w.cvec + 64);
+  w.ti_t = (void*)((char*)w.gi_t + mpp * 8);
+  w.t_t = (void*)((char*)w.ti_t + mpp * 8);
+  w.xc_t = (void*)((char*)w.t_t + mpp * 8);
   BK_CK(ws_get(c, WS_STATE, sizeof(DevState) + 64, (void**)&w.state));
   BK_CK(ws_get(c, WS_NORMP, kHostParts * 8, (void**)&w.normp));
 
@@ -411,6 +415,11 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
   const double bnorm = std::sqrt(bnorm2);
 
   int loads = 0, refinements = 0, residual_loads = 0, stagnant = 0;
+  // Inner target floor: an inner solve in FP32 blocks stops reducing the true residual
+  // at a level set by the block precision and the conditioning (the recurrence keeps
+  // going below it). When a pass that met its target reduced the FP64 residual by far
+  // less, later passes stop at half the reduction that pass achieved.
+  double floor_target = 0.0;
   int launches = 3;  // omega, norm, (x copy is a memcpy)
   bk_status result = BK_NOT_CONVERGED;
   double rnorm = bnorm;
@@ -452,22 +461,19 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
     if ((e = mark(1)) != cudaSuccess) return e;
     if ((e = bk::launch_reduce_gram(mp, m, w.partsG, w.npG, w.G, w.state, st)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
-    if ((e = bk::launch_small_alpha(is64, mp, m, w.G, w.Sold, w.alpha, w.alpha_t, rank_tol, w.state, st)) !=
-        cudaSuccess)
+    if ((e = bk::launch_small_alpha(is64, mp, m, w.G, w.cvec, w.gi_t, w.xc_t, rank_tol, w.state, st)) != cudaSuccess)
       return e;
     if ((e = mark(3)) != cudaSuccess) return e;
-    if ((e = bk::launch_update_r(is64, mp, d, m, w.Y, w.R, ld, w.alpha_t, w.partsS, w.npS, w.state, st)) !=
-        cudaSuccess)
+    if ((e = bk::launch_update_r(is64, mp, d, m, w.Y, w.Q, ld, w.gi_t, w.partsS, w.npS, w.state, st)) != cudaSuccess)
       return e;
     if ((e = mark(4)) != cudaSuccess) return e;
-    if ((e = bk::launch_reduce_gram(mp, m, w.partsS, w.npS, w.Snew, w.state, st)) != cudaSuccess) return e;
+    if ((e = bk::launch_reduce_gram(mp, m, w.partsS, w.npS, w.S, w.state, st)) != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
-    if ((e = bk::launch_small_beta(is64, mp, m, w.Sold, w.Snew, w.beta, w.beta_t, rank_tol, w.state, st)) !=
-        cudaSuccess)
+    if ((e = bk::launch_small_beta(is64, mp, m, w.S, w.cvec, w.ti_t, w.t_t, rank_tol, w.state, st)) != cudaSuccess)
       return e;
     if ((e = mark(6)) != cudaSuccess) return e;
-    if ((e = bk::launch_update_p(is64, mp, d, m, w.R, w.P, ld, w.alpha_t, w.beta_t, w.xin, w.Snew, w.Sold, w.state,
-                                 st)) != cudaSuccess)
+    if ((e = bk::launch_update_p(is64, mp, d, m, w.Q, w.P, ld, w.xc_t, w.ti_t, w.t_t, w.xin, w.state, st)) !=
+        cudaSuccess)
       return e;
     if ((e = mark(7)) != cudaSuccess) return e;
     if (nprof) prof_it = (prof_it + 1) % nprof;
@@ -487,13 +493,16 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
       result = BK_NOT_CONVERGED;
       break;
     }
-    double target = std::fmax(opts.inner_tol, 0.5 * opts.tol * bnorm / rnorm);
+    double target = std::fmax(std::fmax(opts.inner_tol, 0.5 * opts.tol * bnorm / rnorm), floor_target);
     if (target > 0.5) target = 0.5;
-    BK_CK(bk::launch_start_block(is64, d, m, ld, w.r64, 1.0 / rnorm, w.omega, w.R, w.P, w.xin, st));
-    BK_CK(bk::launch_gram(is64, mp, d, w.R, w.R, ld, m, w.partsS, npStart, st));
-    BK_CK(bk::launch_reduce_gram(mp, m, w.partsS, npStart, w.Sold, nullptr, st));
-    BK_CK(bk::launch_init_state(w.state, opts.max_loads - loads, target, st));
-    launches += 4;  // start block, Gram, reduce, state
+    // start block: Q = [r / ||r||, Omega], S = Q^T Q = T^T T, Q <- Q T^{-1}, P = Q, c = T e_1
+    BK_CK(bk::launch_start_block(is64, d, m, ld, w.r64, 1.0 / rnorm, w.omega, w.Q, w.xin, st));
+    BK_CK(bk::launch_gram(is64, mp, d, w.Q, w.Q, ld, m, w.partsS, npStart, st));
+    BK_CK(bk::launch_reduce_gram(mp, m, w.partsS, npStart, w.S, nullptr, st));
+    BK_CK(bk::launch_init_state(w.state, opts.max_loads - loads, target, w.cvec, m, st));
+    BK_CK(bk::launch_small_beta(is64, mp, m, w.S, w.cvec, w.ti_t, w.t_t, rank_tol, w.state, st));
+    BK_CK(bk::launch_update_p(is64, mp, d, m, w.Q, w.P, ld, w.xc_t, w.ti_t, w.t_t, w.xin, w.state, st));
+    launches += 6;  // start block, Gram, reduce, state, factor, normalise
     for (int chunk = 0;; ++chunk) {
       if (use_graph && (chunk > 0 || gexec)) {
         if (!gexec) {
@@ -542,6 +551,8 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
       result = BK_OK;
       break;
     }
+    const double achieved = rn / rnorm;
+    if (hs.status == bk::ST_CONVERGED && achieved > 4.0 * target) floor_target = 0.5 * achieved;
     if (!(rn < 0.5 * rnorm)) {
       if (hs.status == bk::ST_BREAKDOWN && !(rn < rnorm)) {
         rnorm = rn;

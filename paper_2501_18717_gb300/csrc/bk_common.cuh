@@ -11,25 +11,27 @@ namespace bk {
 // step kernels so that the iteration needs no host round trip; the host reads it
 // every `check_every` block products.
 //
-// Race-free ownership: every field is written by exactly one kind of kernel, and no
-// kernel reads a field that its own launch writes (except where a stale read is
-// harmless, noted below).
-//   done_a, pending_x, loads  written by the alpha small-solve (CTA 0); loads is
-//                             read back only by the beta small-solve
-//   done_b, res               written by the beta small-solve (CTA 0)
-//   status                    written by whichever sets a done flag
+// Race-free ownership: every field is written by exactly one kind of kernel (and the
+// reset kernel), and no kernel reads a field that its own launch writes.
+//   done_a, pending_x, loads, first   written by the alpha small-solve (CTA 0); loads
+//                                     is read back only by the beta small-solve, first
+//                                     only by the direction update
+//   done_b, res                       written by the beta small-solve (CTA 0)
+//   status                            written by whichever sets a done flag
 struct DevState {
-  int done_a;       // G invalid, or rank deficient (after applying its step)
-  int done_b;       // column-0 residual met its target, load cap, or S rank deficient
-  int pending_x;    // this step's alpha is valid: the x update must run
+  int done_a;       // G unusable (negative or non-finite diagonal, or no kept column)
+  int done_b;       // residual met its target, load cap, or S unusable
+  int pending_x;    // this step's xc is valid: the x update must run
+  int first;        // no load yet in this inner solve (direction update only normalises)
   int loads;        // block products completed in this inner solve
   int status;       // ST_* below
   int max_loads;    // cap for this inner solve
-  double tol_abs;   // target on ||R[:,0]|| (column 0 starts with norm 1)
-  double res;       // latest ||R[:,0]|| from the recurrence
+  int pad_;
+  double tol_abs;   // target on ||R e_1|| = ||c|| (column 0 starts with norm 1)
+  double res;       // latest ||c|| from the recurrence
 };
 
-enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_LOADCAP = 3, ST_DEFLATED = 4 };
+enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_LOADCAP = 3 };
 
 // Padded block widths the kernels are compiled for (multiples of 4 for the 4x4
 // register blocks of the Gram kernels).
@@ -72,32 +74,31 @@ int gram_grid(int is_f64, int mp, int64_t d, int device);
 cudaError_t launch_reduce_gram(int mp, int m, const double* parts, int nparts, double* out,
                                const DevState* state, cudaStream_t st);
 
-// Small solves. mode 0 (alpha): X = G^{-1} S; mode 1 (beta): convergence test on
-// Snew and X = S^{-1} Snew. Writes the FP64 result and a padded copy in the
-// block precision (mp x mp, row-major) for the update kernels.
-// rank_tol: pivots of the unit-diagonal scaled matrix below it count as dependent.
-cudaError_t launch_small_alpha(int is_f64, int mp, int m, const double* G, const double* S, double* X,
-                               void* Xt, double rank_tol, DevState* state, cudaStream_t st);
-cudaError_t launch_small_beta(int is_f64, int mp, int m, const double* Sold, const double* Snew, double* X,
-                              void* Xt, double rank_tol, DevState* state, cudaStream_t st);
+// Small solves of the orthonormal-residual step (k_block.cu). alpha: Gi = G^+ and
+// xc = G^+ c as mp x mp / mp copies in the block precision. beta: S = T^T T, writes
+// T (row-major) and (T^+)^T (row-major) in the block precision, c <- T c, and the
+// stopping decision on ||c||. rank_tol: pivots of the unit-diagonal scaled matrix at
+// or below it count as dependent columns.
+cudaError_t launch_small_alpha(int is_f64, int mp, int m, const double* G, const double* cvec, void* gi_t,
+                               void* xc_t, double rank_tol, DevState* state, cudaStream_t st);
+cudaError_t launch_small_beta(int is_f64, int mp, int m, const double* S, double* cvec, void* ti_t, void* t_t,
+                              double rank_tol, DevState* state, cudaStream_t st);
 // Stand-alone X = G^{-1} S (no state); status word set to 1 on breakdown.
 cudaError_t launch_chol_solve(int m, const double* G, const double* S, double* X, int* flag, cudaStream_t st);
 
-// R -= Y alpha with per-CTA partials of R^T R.
+// W = Q - Y Gi (in place in Q) with per-CTA partials of W^T W.
 cudaError_t launch_update_r(int is_f64, int mp, int64_t d, int m, const void* Y, void* R, int64_t ld,
                             const void* alpha_t, double* parts, int nparts, const DevState* state,
                             cudaStream_t st);
 int update_r_grid(int is_f64, int mp, int64_t d, int device);
 
-// x += P alpha[:,0] (FP64 accumulator) and, unless converged, P = R + P beta.
-// Also copies Snew into Sold (CTA 0) for the next step.
-cudaError_t launch_update_p(int is_f64, int mp, int64_t d, int m, const void* R, void* P, int64_t ld,
-                            const void* alpha_t, const void* beta_t, double* x, const double* Snew,
-                            double* Sold, const DevState* state, cudaStream_t st);
+// x += P xc (FP64 accumulator) and, unless the solve stopped, Q = W T^{-1}, P = Q + P T^T.
+cudaError_t launch_update_p(int is_f64, int mp, int64_t d, int m, void* Q, void* P, int64_t ld, const void* xc_t,
+                            const void* ti_t, const void* t_t, double* x, const DevState* state, cudaStream_t st);
 
-// Start block of an inner solve: R[:,0] = r * scale, R[:,1:] = Omega, P = R, x = 0.
+// Start block of an inner solve: Q[:,0] = r * scale, Q[:,1:] = Omega, x = 0.
 cudaError_t launch_start_block(int is_f64, int64_t d, int m, int64_t ld, const double* r, double scale,
-                               const void* omega, void* R, void* P, double* x, cudaStream_t st);
+                               const void* omega, void* Q, double* x, cudaStream_t st);
 // Omega (d x l) from Philox stream 3, times `scale`, written as columns 1..l of a panel
 // block with leading dimension ld (the caller zeroes column 0 and the padding).
 cudaError_t launch_omega(int is_f64, int64_t d, int l, int64_t ld, uint64_t seed, double scale, void* out,
@@ -152,8 +153,8 @@ cudaError_t launch_copy_cols(int in_f64, int out_f64, int64_t d, int m, const vo
                              int64_t ldo, cudaStream_t st);
 cudaError_t launch_shift_residual(int64_t d, int L, const double* b, const double* AX, const double* X, int64_t ld,
                                   const double* mus, double* R, double* norms2, cudaStream_t st);
-// Reset the control block for a new inner solve.
-cudaError_t launch_init_state(DevState* state, int max_loads, double tol_abs, cudaStream_t st);
+// Reset the control block for a new inner solve; c = e_1.
+cudaError_t launch_init_state(DevState* state, int max_loads, double tol_abs, double* cvec, int m, cudaStream_t st);
 // Norm partial count used by the residual launchers.
 int residual_parts(int64_t d);
 

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <map>
 
 #include "../../include/bk.h"
 #include "bk_common.cuh"
@@ -15,6 +16,8 @@ enum Slot {
   // block-Lanczos drivers
   WS_LQ, WS_LW, WS_LV, WS_LC, WS_LSMALL, WS_LBAND, WS_LBWORK, WS_LZ, WS_LRHS, WS_LX, WS_LAX, WS_LRES, WS_LB0,
   WS_LSHIFT, WS_LB64, WS_LQ2,
+  // batched solver
+  WS_BATCH, WS_BATCH_VALS,
   WS_COUNT
 };
 
@@ -32,6 +35,7 @@ struct bk_ctx {
   bk::DevState* hstate = nullptr;  // pinned mirror of the device control block
   double* hparts = nullptr;        // pinned buffer for norm partials and small reads
   int sms = 152;
+  std::map<int, int> tune;  // autotuner: floor(log2 d) -> sketch columns
 };
 
 namespace bkx {

@@ -2,14 +2,25 @@
 // small FP64 Cholesky solves, the fused residual and direction updates, the start
 // block and small helpers.
 //
-// One block-CG step (Def. BCG; the recurrence of O'Leary cited in Sec. 3):
+// One block-CG step in the orthonormal-residual form (block CG with a QR-factored
+// residual, Dubrulle 2001): the residual block is kept as R = Q C with Q of (nearly)
+// orthonormal columns, and only c = C e_1 is carried (the column-0 system is the one
+// solved; Def. BCG, bcg^(1)). With P the search directions:
 //   Y = A_mu P ; G = P^T Y                       (k_csr_spmm_gram / k_dense_gram)
-//   alpha = G^{-1} S                             (k_small_alpha)
-//   R -= Y alpha ; S' = R^T R                    (k_update_r)
-//   beta = S^{-1} S'                             (k_small_beta, with the residual test)
-//   x += P alpha[:,0] ; P = R + P beta ; S = S'  (k_update_p)
+//   Gi = G^+ ; xc = G^+ c                        (k_small_alpha)
+//   W = Q - Y Gi ; S = W^T W                     (k_update_r)
+//   S = T^T T (T upper) ; c <- T c ; test ||c||  (k_small_beta)
+//   x += P xc ; Q = W T^{-1} ; P = Q + P T^T     (k_update_p)
+// In exact arithmetic this gives the iterates of O'Leary's recurrence (the one the
+// paper cites in Sec. 3): both are the Galerkin iterates over the block Krylov space.
+// It differs in rounding: P is built from an orthonormal basis instead of residual
+// columns whose norms drift apart as they converge, which keeps the small systems well
+// conditioned. In FP32 blocks the O'Leary form stops converging on spectra with
+// kappa ~ 1e5 while this form converges.
 #include "bk_common.cuh"
+#include "bk_small.cuh"
 #include "bk_tile.cuh"
+#include "bk_update.cuh"
 
 namespace bk {
 namespace {
@@ -83,109 +94,21 @@ __global__ void k_reduce_gram(int m, const double* __restrict__ parts, int npart
 }
 
 // ------------------------------------------------------------------ small solves
-// The m x m systems G alpha = S and S beta = S' of each step are solved by a Cholesky
-// factorisation of the unit-diagonal scaled matrix D^{-1/2} M D^{-1/2}, one CTA per
-// right-hand-side column (every CTA factors the same matrix in the same order, so all
-// agree on which columns are kept). A column whose pivot falls below rank_tol is
-// numerically in the span of the columns before it; it is dropped and the solution
-// is taken on the kept columns only (zero rows elsewhere). For G = P^T A_mu P this
-// keeps X += P alpha the Galerkin update over span(P) when the block has become rank
-// deficient (Sec. 3.2: blocks can lose rank even in exact arithmetic).
-constexpr int kSmallMax = 64;
-constexpr int kLds = kSmallMax + 1;
-
-struct SmallShared {
-  double W[kSmallMax * kLds];
-  double z[kSmallMax];
-  double dscale[kSmallMax];
-  double invd[kSmallMax];  // 1 / L[k][k]
-  int perm[kSmallMax];
-};
-
+// The m x m systems of each step are solved through a Cholesky factorisation of the
+// unit-diagonal scaled matrix D^{-1/2} M D^{-1/2} (block_cholesky_skip), one CTA per
+// output column: every CTA factors the same matrix in the same order, so all agree on
+// which columns are kept. A column whose pivot falls below rank_tol is numerically in
+// the span of the columns before it; it is dropped (zero rows and columns in the
+// results), which for G = P^T A_mu P keeps x += P G^+ c the Galerkin update over
+// span(P) when the block has become rank deficient (Sec. 3.2: blocks can lose rank even
+// in exact arithmetic), and for S = W^T W leaves the dropped direction out of the new
+// basis. A dropped column of Q (and so of P) stays zero from then on: its Gram rows
+// are zero and a zero diagonal is dropped again.
 constexpr int kSmallThreads = 128;
 
-// 1/sqrt(x) for a positive normal FP64 x: an FP32 estimate of the argument brought
-// into [1, 4) by an exact power-of-two scaling, then two Newton steps in FP64
-// (r <- r (3 - x r^2) / 2 converges quadratically: about 1e-7 -> 1e-14 -> rounding).
-__device__ __forceinline__ double rsqrt_newton(double x) {
-  const int e = ((__double2hiint(x) >> 20) & 0x7ff) - 1023;
-  const int h = e >> 1;  // floor(e / 2)
-  const double xs = x * __hiloint2double((1023 - 2 * h) << 20, 0);
-  double r = (double)rsqrtf((float)xs) * __hiloint2double((1023 - h) << 20, 0);
-  r = r * fma(-0.5 * x, r * r, 1.5);
-  r = r * fma(-0.5 * x, r * r, 1.5);
-  return r;
-}
-
-// On this part an FP64 instruction has a 64-cycle latency, a single warp issues at
-// most one FP64 instruction per 64 cycles, and a square root or division is a
-// dependent chain of several hundred cycles, so the factorisation is organised around
-// its dependency chain: no pivot search (comparisons are FP64 instructions too), one
-// thread forms 1/sqrt(pivot) by Newton steps, and the trailing update is spread over
-// four warps (four SM sub-partitions).
-//
-// Cholesky of the unit-diagonal scaled matrix in the given column order; a pivot at
-// or below rank_tol marks column k as numerically in the span of the kept columns
-// before it: its row and column are dropped (flag keep[k] = 0) and the factorisation
-// continues. Returns the number of kept columns, or -1 for a non-positive or
-// non-finite diagonal entry. On return the lower triangle of W holds L on the kept
-// rows/columns (zeros elsewhere) and invd[k] = 1 / L[k][k] (0 for dropped columns).
-__device__ int block_cholesky_skip(SmallShared& sh, int m, double rank_tol) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = kSmallThreads / 32;
-  double* W = sh.W;
-  __shared__ int s_bad, s_rank;
-  if (tid == 0) {
-    s_bad = 0;
-    s_rank = 0;
-  }
-  __syncthreads();
-  for (int i = tid; i < m; i += kSmallThreads) {
-    const double g = W[i * kLds + i];
-    const bool bad = !(g > 0.0) || !isfinite(g);
-    if (bad) s_bad = 1;
-    const double r = bad ? 1.0 : rsqrt_newton(g);  // D^{-1/2}
-    sh.z[i] = r;
-    sh.dscale[i] = bad ? 1.0 : g * r;  // sqrt(g)
-  }
-  __syncthreads();
-  if (s_bad) return -1;
-  for (int idx = tid; idx < m * m; idx += kSmallThreads) {
-    const int r = idx / m, c = idx - r * m;
-    W[r * kLds + c] *= sh.z[r] * sh.z[c];
-  }
-  __syncthreads();
-  for (int k = 0; k < m; ++k) {
-    if (tid == 0) {
-      const double x = W[k * kLds + k];
-      const bool keep = x > rank_tol;
-      double r = 0.0;
-      if (keep) {
-        r = rsqrt_newton(x);
-        s_rank += 1;
-      }
-      W[k * kLds + k] = keep ? x * r : 0.0;
-      sh.invd[k] = r;
-      sh.perm[k] = keep;
-    }
-    __syncthreads();
-    const double inv = sh.invd[k];  // 0 drops the column: L[:,k] = 0, no trailing update
-    for (int i = k + 1 + tid; i < m; i += kSmallThreads) W[i * kLds + k] *= inv;
-    __syncthreads();
-    if (inv != 0.0) {
-      for (int i = k + 1 + warp; i < m; i += NW) {
-        const double lik = W[i * kLds + k];
-        for (int j = k + 1 + lane; j <= i; j += 32) W[i * kLds + j] = fma(-lik, W[j * kLds + k], W[i * kLds + j]);
-      }
-    }
-    __syncthreads();
-  }
-  return s_rank;
-}
-
-// z <- L^+ applied twice (L^{-T} L^{-1} on the kept columns, zero on dropped ones),
+// Forward (L^+) and backward (L^{-T} on the kept columns) substitution on z in place,
 // warp 0; invd holds 1 / L[k][k] (0 for dropped columns).
-__device__ void chol_apply_warp0(const double* L, const double* invd, double* z, int m) {
+__device__ void chol_forward_warp0(const double* L, const double* invd, double* z, int m) {
   if ((threadIdx.x >> 5) == 0) {
     const int lane = threadIdx.x & 31;
     for (int k = 0; k < m; ++k) {
@@ -195,6 +118,13 @@ __device__ void chol_apply_warp0(const double* L, const double* invd, double* z,
       if (lane == 0) z[k] = zk;
       for (int i = k + 1 + lane; i < m; i += 32) z[i] = fma(-L[i * kLds + k], zk, z[i]);
     }
+    __syncwarp();
+  }
+  __syncthreads();
+}
+__device__ void chol_backward_warp0(const double* L, const double* invd, double* z, int m) {
+  if ((threadIdx.x >> 5) == 0) {
+    const int lane = threadIdx.x & 31;
     for (int k = m - 1; k >= 0; --k) {
       __syncwarp();
       const double zk = z[k] * invd[k];
@@ -207,124 +137,137 @@ __device__ void chol_apply_warp0(const double* L, const double* invd, double* z,
   __syncthreads();
 }
 
-// CTA j: column j of X = M^+ RHS on the kept columns (zero rows on dropped ones); the
-// result is left in sh.z[0:m]. Returns the number of kept columns (-1: invalid diagonal).
-__device__ int small_solve_column(const double* M, const double* RHS, int m, int j, double rank_tol,
-                                  SmallShared& sh) {
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < m * m; idx += kSmallThreads) {
+__device__ int load_and_factor(const double* M, int m, double rank_tol, SmallShared& sh) {
+  for (int idx = threadIdx.x; idx < m * m; idx += kSmallThreads) {
     const int r = idx / m, c = idx - r * m;
     sh.W[r * kLds + c] = M[idx];
   }
   __syncthreads();
-  const int rank = block_cholesky_skip(sh, m, rank_tol);
-  if (rank <= 0) return rank;
-  // the scaled system: (D^{-1/2} M D^{-1/2}) (D^{1/2} x) = D^{-1/2} rhs, D^{-1/2} = 1/dscale
-  __shared__ double y[kSmallMax];
-  __shared__ double rs[kSmallMax];
-  for (int i = tid; i < m; i += kSmallThreads) {
-    rs[i] = sh.z[i];  // D^{-1/2} from the scaling step
-    y[i] = RHS[i * m + j] * rs[i];
-  }
-  __syncthreads();
-  chol_apply_warp0(sh.W, sh.invd, y, m);
-  for (int i = tid; i < m; i += kSmallThreads) sh.z[i] = y[i] * rs[i];
-  __syncthreads();
-  return rank;
+  return block_cholesky_skip<kSmallThreads>(sh, m, rank_tol);
 }
 
+// CTA j < m: column j of Gi = G^+ (row-major mp x mp copy in the block precision);
+// CTA m: xc = G^+ c. CTA 0 owns the control block: one more load, and the x update
+// of this step is pending unless G is unusable.
 template <typename T>
-__device__ void write_column(const double* z, int m, int mp, int j, double* X, T* Xt) {
-  for (int i = threadIdx.x; i < mp; i += kSmallThreads) {
-    double v = (i < m) ? z[i] : 0.0;
-    if (i < m) X[i * m + j] = v;
-    Xt[i * mp + j] = (T)v;
-  }
-}
-
-template <typename T>
-__device__ void zero_pad_columns(int m, int mp, T* Xt) {
-  // columns m..mp-1 of the padded copy (CTA 0 only)
-  for (int idx = threadIdx.x; idx < mp * mp; idx += kSmallThreads) {
-    int c = idx % mp;
-    if (c >= m) Xt[idx] = (T)0;
-  }
-}
-
-template <typename T>
-__global__ void k_small_alpha(int m, int mp, const double* G, const double* S, double* X, T* Xt,
+__global__ void k_small_alpha(int m, int mp, const double* G, const double* cvec, T* gi_t, T* xc_t,
                               double rank_tol, DevState* state) {
   __shared__ SmallShared sh;
-  bool cta0 = blockIdx.x == 0;
+  __shared__ double y[kSmallMax];
+  const bool cta0 = blockIdx.x == 0;
   if (is_done(state)) {
     if (cta0 && threadIdx.x == 0) state->pending_x = 0;
     return;
   }
-  int j = blockIdx.x;
-  int rank = small_solve_column(G, S, m, j, rank_tol, sh);
-  if (rank > 0) write_column<T>(sh.z, m, mp, j, X, Xt);
+  const int j = blockIdx.x;
+  const int rank = load_and_factor(G, m, rank_tol, sh);
+  if (rank > 0) {
+    for (int i = threadIdx.x; i < m; i += kSmallThreads) {
+      const double rhs = j < m ? (i == j ? 1.0 : 0.0) : cvec[i];
+      y[i] = rhs * sh.z[i];
+    }
+    __syncthreads();
+    chol_forward_warp0(sh.W, sh.invd, y, m);
+    chol_backward_warp0(sh.W, sh.invd, y, m);
+    for (int i = threadIdx.x; i < mp; i += kSmallThreads) {
+      const T v = (T)(i < m ? y[i] * sh.z[i] : 0.0);
+      if (j < m)
+        gi_t[i * mp + j] = v;
+      else
+        xc_t[i] = v;
+    }
+  }
   if (cta0) {
-    zero_pad_columns<T>(m, mp, Xt);
+    const int pad = mp - m;
+    if (pad > 0)
+      for (int idx = threadIdx.x; idx < mp * pad; idx += kSmallThreads) gi_t[(idx / pad) * mp + m + idx % pad] = (T)0;
     if (threadIdx.x == 0) {
       state->loads += 1;
+      state->first = 0;
       if (rank <= 0) {
         state->pending_x = 0;
         state->done_a = 1;
         state->status = ST_BREAKDOWN;
       } else {
-        // a rank-deficient block still gives a valid Galerkin step; the inner solve
-        // ends after it and the caller restarts from the new residual
         state->pending_x = 1;
-        if (rank < m) {
-          state->done_a = 1;
-          state->status = ST_DEFLATED;
-        }
       }
     }
   }
 }
 
+// S = W^T W = T^T T with T = L^T D^{1/2} upper triangular (on the kept columns).
+// CTA j writes column j of Ti = T^+ (ti_t[i * mp + j]) and column j of T as row j of
+// T^T (t_t[j * mp + i] = T(i, j) = L(j, i) dscale[j], i <= j), both mp x mp row-major in
+// the block precision. CTA 0 also forms c <- T c, the residual ||c|| = ||R e_1|| and the
+// stopping decision. The columns are written even when the solve stops here (no later
+// kernel reads them then), so only CTA 0 reads c and no CTA reads what another writes.
 template <typename T>
-__global__ void k_small_beta(int m, int mp, const double* Sold, const double* Snew, double* X, T* Xt,
-                             double rank_tol, DevState* state) {
+__global__ void k_small_beta(int m, int mp, const double* S, double* cvec, T* ti_t, T* t_t, double rank_tol,
+                             DevState* state) {
   __shared__ SmallShared sh;
-  bool cta0 = blockIdx.x == 0;
+  __shared__ double y[kSmallMax];
+  __shared__ double cn[kSmallMax];
   if (is_done(state)) return;
-  double res = sqrt(fmax(Snew[0], 0.0));
-  bool conv = res <= state->tol_abs;
-  bool cap = state->loads >= state->max_loads;
-  if (conv || cap) {
-    if (cta0 && threadIdx.x == 0) {
-      state->res = res;
+  const int j = blockIdx.x;
+  const int rank = load_and_factor(S, m, rank_tol, sh);
+  if (rank >= 0) {
+    for (int i = threadIdx.x; i < m; i += kSmallThreads) y[i] = (i == j) ? 1.0 : 0.0;
+    __syncthreads();
+    chol_backward_warp0(sh.W, sh.invd, y, m);
+    for (int i = threadIdx.x; i < mp; i += kSmallThreads) {
+      ti_t[i * mp + j] = (T)(i < m ? y[i] * sh.z[i] : 0.0);
+      t_t[j * mp + i] = (T)(i <= j ? sh.W[j * kLds + i] * sh.dscale[j] : 0.0);
+    }
+  }
+  if (j != 0) return;
+  const int pad = mp - m;
+  for (int idx = threadIdx.x; idx < mp * pad; idx += kSmallThreads) {
+    ti_t[(size_t)(idx / pad) * mp + m + idx % pad] = (T)0;  // columns m..mp-1
+    t_t[(size_t)(m + idx / mp) * mp + idx % mp] = (T)0;     // rows m..mp-1
+  }
+  if (rank < 0) {
+    if (threadIdx.x == 0) {
       state->done_b = 1;
-      state->status = conv ? ST_CONVERGED : ST_LOADCAP;
+      state->status = ST_BREAKDOWN;
     }
     return;
   }
-  int j = blockIdx.x;
-  int rank = small_solve_column(Sold, Snew, m, j, rank_tol, sh);
-  if (rank == m) write_column<T>(sh.z, m, mp, j, X, Xt);
-  if (cta0) {
-    zero_pad_columns<T>(m, mp, Xt);
-    if (threadIdx.x == 0) {
-      state->res = res;
-      if (rank != m) {
-        state->done_b = 1;
-        state->status = rank < 0 ? ST_BREAKDOWN : ST_DEFLATED;
-      }
+  for (int i = threadIdx.x; i < m; i += kSmallThreads) {
+    double s = 0.0;
+    for (int k = i; k < m; ++k) s = fma(sh.W[k * kLds + i] * sh.dscale[k], cvec[k], s);
+    cn[i] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += kSmallThreads) cvec[i] = cn[i];
+  if (threadIdx.x == 0) {
+    double ss = 0.0;
+    for (int i = 0; i < m; ++i) ss = fma(cn[i], cn[i], ss);
+    const double res = sqrt(ss);
+    state->res = res;
+    const bool conv = res <= state->tol_abs;
+    if (conv || state->loads >= state->max_loads) {
+      state->done_b = 1;
+      state->status = conv ? ST_CONVERGED : ST_LOADCAP;
     }
   }
 }
 
+// Stand-alone X = G^+ S column by column (no control block); flag set on a dropped
+// column or an unusable G.
 __global__ void k_chol_solve(int m, const double* G, const double* S, double* X, double rank_tol, int* flag) {
   __shared__ SmallShared sh;
-  int j = blockIdx.x;
-  int rank = small_solve_column(G, S, m, j, rank_tol, sh);
+  __shared__ double y[kSmallMax];
+  const int j = blockIdx.x;
+  const int rank = load_and_factor(G, m, rank_tol, sh);
   if (rank != m) {
     if (threadIdx.x == 0) atomicExch(flag, 1);
     return;
   }
-  for (int i = threadIdx.x; i < m; i += kSmallThreads) X[i * m + j] = sh.z[i];
+  for (int i = threadIdx.x; i < m; i += kSmallThreads) y[i] = S[i * m + j] * sh.z[i];
+  __syncthreads();
+  chol_forward_warp0(sh.W, sh.invd, y, m);
+  chol_backward_warp0(sh.W, sh.invd, y, m);
+  for (int i = threadIdx.x; i < m; i += kSmallThreads) X[i * m + j] = y[i] * sh.z[i];
 }
 
 // ------------------------------------------------------------------ updates
@@ -380,84 +323,63 @@ __global__ void __launch_bounds__(TM, sizeof(T) == 4 ? 4 : 2)
                      nparts, blockIdx.x);
 }
 
-// x += P alpha[:,0]; unless the solve just ended, P = R + P beta; CTA 0 copies Snew
-// into Sold. Thread per row, both rows loaded up front.
+// x += P xc; unless the solve just ended, Q = W T^{-1} (W is held in Q) and
+// P = Q + P T^T (P = Q on the first call of an inner solve, which only normalises the
+// start block); the row loop is update_pq_rows.
+// (No residency hint at width 36: with one the compiler spills the row arrays.)
 template <typename T, int MP>
-__global__ void __launch_bounds__(kUpdThreads, sizeof(T) == 4 ? 3 : 2)
-    k_update_p(int64_t d, int m, const T* __restrict__ R, T* P, int64_t ld, const T* __restrict__ alpha_t,
-               const T* __restrict__ beta_t, double* x, const double* Snew, double* Sold, const DevState* state) {
-  if (state && !state->pending_x) return;
-  const bool upd = !(state && (state->done_a | state->done_b));
-  __shared__ __align__(16) T sB[MP * MP];
-  __shared__ __align__(16) T sa0[MP];
-  for (int idx = threadIdx.x; idx < MP * MP; idx += blockDim.x) sB[idx] = beta_t[idx];
-  for (int idx = threadIdx.x; idx < MP; idx += blockDim.x) sa0[idx] = alpha_t[idx * MP];
-  if (upd && blockIdx.x == 0 && Sold)
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Sold[idx] = Snew[idx];
-  __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
-    asm volatile("" ::: "memory");  // no hoisting of the beta reads across rows
-    T p[MP], acc[MP];
-#pragma unroll
-    for (int q = 0; q < MP / 4; ++q) {
-      if (4 * q < m) {
-        ld4(panel_row(P, ld, q, i), p + 4 * q);
-        if (upd) ldg4(panel_row(R, ld, q, i), acc + 4 * q);
-        else {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) acc[4 * q + u] = (T)0;
-        }
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) p[4 * q + u] = acc[4 * q + u] = (T)0;
-      }
-    }
-    T xs = 0;
-#pragma unroll
-    for (int k = 0; k < MP; ++k) xs = fma(p[k], sa0[k], xs);
-    x[i] += (double)xs;
-    if (upd) {
-#pragma unroll
-      for (int k = 0; k < MP; ++k) {
-        const T* b = sB + k * MP;
-#pragma unroll
-        for (int c = 0; c < MP; ++c) acc[c] = fma(p[k], b[c], acc[c]);
-      }
-#pragma unroll
-      for (int q = 0; q < MP / 4; ++q)
-        if (4 * q < m) st4(panel_row(P, ld, q, i), acc + 4 * q);
-    }
+__global__ void __launch_bounds__(kUpdThreads, MP < 36 ? (sizeof(T) == 4 ? 3 : 2) : 0)
+    k_update_p(int64_t d, int m, T* Q, T* P, int64_t ld, const T* __restrict__ xc_t, const T* __restrict__ ti_t,
+               const T* __restrict__ t_t, double* x, const DevState* state) {
+  const bool do_x = state->pending_x;
+  const bool upd = !(state->done_a | state->done_b);
+  if (!do_x && !upd) return;
+  const bool first = state->first;
+  __shared__ __align__(16) T sTi[MP * MP];
+  __shared__ __align__(16) T sTT[MP * MP];
+  __shared__ __align__(16) T sxc[MP];
+  for (int idx = threadIdx.x; idx < MP * MP; idx += blockDim.x) {
+    sTi[idx] = ti_t[idx];
+    sTT[idx] = first ? (T)0 : t_t[idx];
   }
+  for (int idx = threadIdx.x; idx < MP; idx += blockDim.x) sxc[idx] = do_x ? xc_t[idx] : (T)0;
+  __syncthreads();
+  update_pq_rows<T, MP>(blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, d, m, Q, P,
+                        ld, sTi, sTT, sxc, do_x, upd, x);
 }
 
 // ------------------------------------------------------------------ start block, helpers
-// R = P = [r * scale, Omega] on panels: the Omega buffer is a full panel block whose
-// column 0 and padding columns are zero.
+// Q = [r * scale, Omega] on panels (the Omega buffer is a full panel block whose column
+// 0 and padding columns are zero), x = 0. P is formed by the first k_update_p.
 template <typename T>
-__global__ void k_start_block(int64_t d, int m, int64_t ld, const double* r, double scale, const T* omega,
-                              T* R, T* P, double* x) {
+__global__ void k_start_block(int64_t d, int m, int64_t ld, const double* r, double scale, const T* omega, T* Q,
+                              double* x) {
   const int nq = (m + 3) >> 2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
     for (int q = 0; q < nq; ++q) {
       T v[4];
       ldg4(panel_row(omega, ld, q, i), v);
       if (q == 0) v[0] = (T)(r[i] * scale);
-      st4(panel_row(R, ld, q, i), v);
-      st4(panel_row(P, ld, q, i), v);
+      st4(panel_row(Q, ld, q, i), v);
     }
     x[i] = 0.0;
   }
 }
 
-__global__ void k_init_state(DevState* s, int max_loads, double tol_abs) {
-  s->done_a = 0;
-  s->done_b = 0;
-  s->pending_x = 0;
-  s->loads = 0;
-  s->status = ST_RUNNING;
-  s->max_loads = max_loads;
-  s->tol_abs = tol_abs;
-  s->res = 1.0;
+// New inner solve: c = e_1 (the start block's column 0 has norm 1), first = 1.
+__global__ void k_init_state(DevState* s, int max_loads, double tol_abs, double* cvec, int m) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) cvec[i] = i == 0 ? 1.0 : 0.0;
+  if (threadIdx.x == 0) {
+    s->done_a = 0;
+    s->done_b = 0;
+    s->pending_x = 0;
+    s->first = 1;
+    s->loads = 0;
+    s->status = ST_RUNNING;
+    s->max_loads = max_loads;
+    s->tol_abs = tol_abs;
+    s->res = 1.0;
+  }
 }
 
 __global__ void k_axpy(int64_t d, double a, const double* y, double* x) {
@@ -540,12 +462,11 @@ cudaError_t update_r_impl(int64_t d, int m, const void* Y, void* R, int64_t ld, 
 }
 
 template <typename T, int MP>
-cudaError_t update_p_impl(int64_t d, int m, const void* R, void* P, int64_t ld, const void* alpha_t,
-                          const void* beta_t, double* x, const double* Snew, double* Sold, const DevState* state,
-                          cudaStream_t st, int device) {
+cudaError_t update_p_impl(int64_t d, int m, void* Q, void* P, int64_t ld, const void* xc_t, const void* ti_t,
+                          const void* t_t, double* x, const DevState* state, cudaStream_t st, int device) {
   int grid = capped_grid(d, kUpdThreads, sm_count(device) * (sizeof(T) == 4 ? 4 : 2) * 4);
-  k_update_p<T, MP><<<grid, kUpdThreads, 0, st>>>(d, m, (const T*)R, (T*)P, ld, (const T*)alpha_t,
-                                                  (const T*)beta_t, x, Snew, Sold, state);
+  k_update_p<T, MP><<<grid, kUpdThreads, 0, st>>>(d, m, (T*)Q, (T*)P, ld, (const T*)xc_t, (const T*)ti_t,
+                                                  (const T*)t_t, x, state);
   return cudaGetLastError();
 }
 
@@ -588,14 +509,14 @@ cudaError_t upd_r_f(int64_t d, int m, const void* Y, void* R, int64_t ld, const 
   return update_r_impl<float, MP>(d, m, Y, R, ld, a, parts, np, s, st);
 }
 template <int MP>
-cudaError_t upd_p_d(int64_t d, int m, const void* R, void* P, int64_t ld, const void* a, const void* b, double* x,
-                    const double* Sn, double* So, const DevState* s, cudaStream_t st, int dev) {
-  return update_p_impl<double, MP>(d, m, R, P, ld, a, b, x, Sn, So, s, st, dev);
+cudaError_t upd_p_d(int64_t d, int m, void* Q, void* P, int64_t ld, const void* xc, const void* ti, const void* t,
+                    double* x, const DevState* s, cudaStream_t st, int dev) {
+  return update_p_impl<double, MP>(d, m, Q, P, ld, xc, ti, t, x, s, st, dev);
 }
 template <int MP>
-cudaError_t upd_p_f(int64_t d, int m, const void* R, void* P, int64_t ld, const void* a, const void* b, double* x,
-                    const double* Sn, double* So, const DevState* s, cudaStream_t st, int dev) {
-  return update_p_impl<float, MP>(d, m, R, P, ld, a, b, x, Sn, So, s, st, dev);
+cudaError_t upd_p_f(int64_t d, int m, void* Q, void* P, int64_t ld, const void* xc, const void* ti, const void* t,
+                    double* x, const DevState* s, cudaStream_t st, int dev) {
+  return update_p_impl<float, MP>(d, m, Q, P, ld, xc, ti, t, x, s, st, dev);
 }
 
 }  // namespace
@@ -627,23 +548,25 @@ cudaError_t launch_reduce_gram(int mp, int m, const double* parts, int nparts, d
   BK_DISPATCH_MP(mp, reduce_mp, m, parts, nparts, out, state, st);
 }
 
-cudaError_t launch_small_alpha(int is_f64, int mp, int m, const double* G, const double* S, double* X, void* Xt,
-                               double rank_tol, DevState* state, cudaStream_t st) {
+cudaError_t launch_small_alpha(int is_f64, int mp, int m, const double* G, const double* cvec, void* gi_t,
+                               void* xc_t, double rank_tol, DevState* state, cudaStream_t st) {
   if (m < 1 || m > kSmallMax || mp < m) return cudaErrorInvalidValue;
   if (is_f64)
-    k_small_alpha<double><<<m, kSmallThreads, 0, st>>>(m, mp, G, S, X, (double*)Xt, rank_tol, state);
+    k_small_alpha<double><<<m + 1, kSmallThreads, 0, st>>>(m, mp, G, cvec, (double*)gi_t, (double*)xc_t, rank_tol,
+                                                           state);
   else
-    k_small_alpha<float><<<m, kSmallThreads, 0, st>>>(m, mp, G, S, X, (float*)Xt, rank_tol, state);
+    k_small_alpha<float><<<m + 1, kSmallThreads, 0, st>>>(m, mp, G, cvec, (float*)gi_t, (float*)xc_t, rank_tol,
+                                                          state);
   return cudaGetLastError();
 }
 
-cudaError_t launch_small_beta(int is_f64, int mp, int m, const double* Sold, const double* Snew, double* X, void* Xt,
+cudaError_t launch_small_beta(int is_f64, int mp, int m, const double* S, double* cvec, void* ti_t, void* t_t,
                               double rank_tol, DevState* state, cudaStream_t st) {
   if (m < 1 || m > kSmallMax || mp < m) return cudaErrorInvalidValue;
   if (is_f64)
-    k_small_beta<double><<<m, kSmallThreads, 0, st>>>(m, mp, Sold, Snew, X, (double*)Xt, rank_tol, state);
+    k_small_beta<double><<<m, kSmallThreads, 0, st>>>(m, mp, S, cvec, (double*)ti_t, (double*)t_t, rank_tol, state);
   else
-    k_small_beta<float><<<m, kSmallThreads, 0, st>>>(m, mp, Sold, Snew, X, (float*)Xt, rank_tol, state);
+    k_small_beta<float><<<m, kSmallThreads, 0, st>>>(m, mp, S, cvec, (float*)ti_t, (float*)t_t, rank_tol, state);
   return cudaGetLastError();
 }
 
@@ -663,30 +586,29 @@ cudaError_t launch_update_r(int is_f64, int mp, int64_t d, int m, const void* Y,
   }
 }
 
-cudaError_t launch_update_p(int is_f64, int mp, int64_t d, int m, const void* R, void* P, int64_t ld,
-                            const void* alpha_t, const void* beta_t, double* x, const double* Snew, double* Sold,
-                            const DevState* state, cudaStream_t st) {
+cudaError_t launch_update_p(int is_f64, int mp, int64_t d, int m, void* Q, void* P, int64_t ld, const void* xc_t,
+                            const void* ti_t, const void* t_t, double* x, const DevState* state, cudaStream_t st) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (is_f64) {
-    BK_DISPATCH_MP(mp, upd_p_d, d, m, R, P, ld, alpha_t, beta_t, x, Snew, Sold, state, st, dev);
+    BK_DISPATCH_MP(mp, upd_p_d, d, m, Q, P, ld, xc_t, ti_t, t_t, x, state, st, dev);
   } else {
-    BK_DISPATCH_MP(mp, upd_p_f, d, m, R, P, ld, alpha_t, beta_t, x, Snew, Sold, state, st, dev);
+    BK_DISPATCH_MP(mp, upd_p_f, d, m, Q, P, ld, xc_t, ti_t, t_t, x, state, st, dev);
   }
 }
 
 cudaError_t launch_start_block(int is_f64, int64_t d, int m, int64_t ld, const double* r, double scale,
-                               const void* omega, void* R, void* P, double* x, cudaStream_t st) {
+                               const void* omega, void* Q, double* x, cudaStream_t st) {
   int grid = capped_grid(d, 256, 152 * 8);
   if (is_f64)
-    k_start_block<double><<<grid, 256, 0, st>>>(d, m, ld, r, scale, (const double*)omega, (double*)R, (double*)P, x);
+    k_start_block<double><<<grid, 256, 0, st>>>(d, m, ld, r, scale, (const double*)omega, (double*)Q, x);
   else
-    k_start_block<float><<<grid, 256, 0, st>>>(d, m, ld, r, scale, (const float*)omega, (float*)R, (float*)P, x);
+    k_start_block<float><<<grid, 256, 0, st>>>(d, m, ld, r, scale, (const float*)omega, (float*)Q, x);
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_state(DevState* state, int max_loads, double tol_abs, cudaStream_t st) {
-  k_init_state<<<1, 1, 0, st>>>(state, max_loads, tol_abs);
+cudaError_t launch_init_state(DevState* state, int max_loads, double tol_abs, double* cvec, int m, cudaStream_t st) {
+  k_init_state<<<1, 64, 0, st>>>(state, max_loads, tol_abs, cvec, m);
   return cudaGetLastError();
 }
 

@@ -9,9 +9,9 @@
 //   B(k, j) = B[k * sbk + j * sbj]   (K x N)
 //   C(i, j) = C[i + j * ldc]         (M x N, column-major)
 // Tiles of 64 x 64 outputs, K in steps of 16 staged in shared memory, 256 threads with
-// 4 x 4 outputs each, accumulation in the element type (FP32 or FP64). Operands may be
-// FP32 or FP64 (A also BF16-free here); the tile loader reads along whichever stride is
-// unit so the global loads coalesce.
+// 4 x 4 outputs each, accumulation in the element type of C (FP32 or FP64). A and B may
+// each be FP32 or FP64; the tile loader reads along whichever stride is unit so the
+// global loads coalesce.
 #include "bk_common.cuh"
 
 namespace bk {

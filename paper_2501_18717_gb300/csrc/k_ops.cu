@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(NTH) k_dense_gram(int64_t d, const T* __restri
   GramAcc<T, MP> g;
   g.init();
   int r = threadIdx.x / CG, cg = threadIdx.x % CG;
+  const int nq = (m + 3) >> 2;  // panels held in memory
   int64_t ntiles = (d + TMD - 1) / TMD;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int64_t row0 = tile * TMD;
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(NTH) k_dense_gram(int64_t d, const T* __restri
         int q = idx / KC, kk = idx - q * KC;
         int64_t gk = k0 + kk;
         T pv[4] = {0, 0, 0, 0};
-        if (gk < d) ldg4(P + ((int64_t)q * ld + gk) * 4, pv);
+        if (gk < d && q < nq) ldg4(P + ((int64_t)q * ld + gk) * 4, pv);
 #pragma unroll
         for (int u = 0; u < 4; ++u) sP[kk * MP + 4 * q + u] = pv[u];
       }
@@ -150,10 +151,12 @@ __global__ void __launch_bounds__(NTH) k_dense_gram(int64_t d, const T* __restri
     for (int q = 0; q < NC; ++q) {
       int c = cg + q * CG;
       if (c < MP) {
+        // only the panels of the m live columns exist in memory; the rest count as zero
+        const bool live = gi < d && (c >> 2) < nq;
         const int64_t off = (((int64_t)(c >> 2) * ld + gi) << 2) + (c & 3);
-        T pv = (gi < d) ? P[off] : (T)0;
-        T yv = (gi < d) ? fma(mu, pv, acc[q]) : (T)0;
-        if (gi < d) Y[off] = yv;
+        T pv = live ? P[off] : (T)0;
+        T yv = live ? fma(mu, pv, acc[q]) : (T)0;
+        if (live) Y[off] = yv;
         sX[r * MP + c] = pv;
         sY[r * MP + c] = yv;
       }

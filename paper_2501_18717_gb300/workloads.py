@@ -255,3 +255,55 @@ def rbf_kernel(points: np.ndarray, lengthscale: float = 0.2, dtype=np.float64, c
 def sample_block(seed: int, d: int, m: int) -> np.ndarray:
     """B (d x m, Fortran order) of standard normals from the right-hand-side stream."""
     return normals(seed, STREAM_RHS, d * m).reshape(m, d).T.copy(order="F")
+
+
+# --------------------------------------------------------------------------------------
+# Batched uneven systems: A_i = Q_i diag(lambda_i) Q_i^T, Q_i a product of Householder
+# reflectors; k_i ~ U{1..64} outliers log-uniform in [1e2, 1e5] over a bulk U[1, 10].
+# --------------------------------------------------------------------------------------
+def batch_sizes(seed: int, n: int, dmin: int = 500, dmax: int = 16000) -> np.ndarray:
+    u = uniforms(seed, STREAM_SPECTRUM, n)
+    return np.rint(np.exp(np.log(dmin) + u * (np.log(dmax) - np.log(dmin)))).astype(np.int64)
+
+
+def batch_spectrum(seed: int, i: int, d: int) -> np.ndarray:
+    """Spectrum of system i: outliers first (descending), then the bulk."""
+    u = uniforms(seed + 1 + i, STREAM_SPECTRUM, d + 70)
+    k = min(d, 1 + int(u[0] * 64))
+    out = np.exp(np.log(1e2) + u[1:1 + k] * (np.log(1e5) - np.log(1e2)))
+    bulk = 1.0 + 9.0 * u[70:70 + d - k]
+    return np.concatenate([np.sort(out)[::-1], bulk])
+
+
+def batch_reflectors(seed: int, i: int, d: int, r: int = 16) -> np.ndarray:
+    v = normals(seed + 1 + i, STREAM_FACTORS, r * d).reshape(r, d)
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def batch_system(seed: int, i: int, d: int, dtype=np.float32):
+    """A_i (d x d row-major, dtype) and b_i ~ N(0, I). The reflectors H = I - 2 v v^T are
+    applied to diag(lambda) from both sides in float64: A <- A - 2 v w^T - 2 w v^T +
+    4 (v.w) v v^T with w = A v."""
+    lam = batch_spectrum(seed, i, d)
+    A = np.diag(lam)
+    for v in batch_reflectors(seed, i, d):
+        w = A @ v
+        A -= 2.0 * np.outer(v, w) + 2.0 * np.outer(w, v) - 4.0 * (v @ w) * np.outer(v, v)
+    A = np.ascontiguousarray(0.5 * (A + A.T)).astype(dtype)
+    b = normals(seed + 1 + i, STREAM_RHS, d)
+    return A, b
+
+
+def batch_system_torch(seed: int, i: int, d: int, device, dtype=None):
+    """The same A_i as batch_system, formed on a CUDA device with torch (float64, then
+    rounded); for batches too large to build on the host."""
+    import torch
+    dtype = torch.float32 if dtype is None else dtype
+    lam = torch.from_numpy(batch_spectrum(seed, i, d)).to(device)
+    A = torch.diag(lam)
+    for v in torch.from_numpy(batch_reflectors(seed, i, d)).to(device):
+        w = A @ v
+        A -= 2.0 * torch.outer(v, w) + 2.0 * torch.outer(w, v) - 4.0 * torch.dot(v, w) * torch.outer(v, v)
+    A = (0.5 * (A + A.T)).to(dtype).contiguous()
+    b = torch.from_numpy(normals(seed + 1 + i, STREAM_RHS, d)).to(device)
+    return A, b

@@ -1,0 +1,136 @@
+"""bk_solve_batched and bk_autotune against the FP64 oracle on small uneven batches
+(systems shaped like the batched workload: outlier spectra rotated by Householder
+reflectors, FP32 stored values, mu = 0)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2501_18717_gb300 import workloads as W  # noqa: E402
+from oracle import bcg, direct, operators  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def bk():
+    from paper_2501_18717_gb300 import bk as _bk
+    return _bk
+
+
+@pytest.fixture(scope="module")
+def ctx(bk):
+    c = bk.Context(0)
+    yield c
+    c.close()
+
+
+def make_batch(seed, n, dmin, dmax, dtype=np.float32):
+    ds = [int(d) for d in W.batch_sizes(seed, n, dmin, dmax)]
+    mats, bs = [], []
+    for i, d in enumerate(ds):
+        A, b = W.batch_system(seed, i, d, dtype=dtype)
+        mats.append(A)
+        bs.append(b)
+    return ds, mats, bs
+
+
+def rel_res(A, x, b, mu=0.0):
+    return direct.rel_residual(operators.Dense(A.astype(np.float64)), mu, x, b)
+
+
+@pytest.mark.parametrize("inner,tol", [("fp32", 1e-8), ("fp64", 1e-10)])
+def test_batched_matches_oracle(bk, ctx, inner, tol):
+    seed = W.BASE_SEED + 40
+    ds, mats, bs = make_batch(seed, 10, 300, 1200)
+    dev = torch.device("cuda:0")
+    tm = [torch.from_numpy(a).to(dev) for a in mats]
+    tb = [torch.from_numpy(b).to(dev) for b in bs]
+    tx = [torch.zeros(d, dtype=torch.float64, device=dev) for d in ds]
+    infos = bk.solve_batched(ctx, bk.Batch(tm, np.zeros(len(ds)), tb, tx),
+                             bk.default_opts(tol=tol, sketch=16, seed=3, inner=inner,
+                                             inner_tol=1e-5 if inner == "fp32" else 1e-6))
+    for i, d in enumerate(ds):
+        x = tx[i].cpu().numpy()
+        assert rel_res(mats[i], x, bs[i]) <= tol, (i, d, infos[i].as_dict())
+        # forward error against the direct solve, bounded by kappa * residual (kappa <= 1e5)
+        xstar = direct.solve(mats[i].astype(np.float64), 0.0, bs[i])
+        assert np.linalg.norm(x - xstar) / np.linalg.norm(xstar) <= 1e5 * tol
+        assert infos[i].status == bk.BK_OK
+
+
+@pytest.mark.parametrize("loads", [1, 2, 3])
+def test_batched_iterates_match_oracle(bk, ctx, loads):
+    """With one refinement pass and a load cap, each system's x is the column-0 block-CG
+    iterate on [b/||b||, Omega_i/sqrt(d)] (Omega_i from the key seed + i) times ||b||."""
+    seed, l, oseed = W.BASE_SEED + 43, 8, 17
+    ds, mats, bs = make_batch(seed, 6, 200, 900, dtype=np.float64)
+    xs = [np.zeros(d) for d in ds]
+    bk.solve_batched(ctx, bk.Batch(mats, np.zeros(len(ds)), bs, xs),
+                     bk.default_opts(tol=1e-15, sketch=l, seed=oseed, inner="fp64", inner_tol=1e-15,
+                                     max_loads=loads, max_refine=1), check=False)
+    for i, d in enumerate(ds):
+        bn = np.linalg.norm(bs[i])
+        om = W.omega(oseed + i, d, l) / np.sqrt(d)
+        ref = bcg.block_cg(mats[i], 0.0, bs[i] / bn, om, tol=1e-15, max_loads=loads, history=True)
+        xr = ref["history"][loads - 1] * bn
+        assert np.linalg.norm(xs[i] - xr) / np.linalg.norm(xr) < 1e-10, (i, d)
+
+
+def test_batched_host_and_device_agree(bk, ctx):
+    seed = W.BASE_SEED + 41
+    ds, mats, bs = make_batch(seed, 4, 300, 600)
+    o = bk.default_opts(tol=1e-8, sketch=8, seed=11, inner="fp32", inner_tol=1e-5)
+    xh = [np.zeros(d) for d in ds]
+    bk.solve_batched(ctx, bk.Batch(mats, np.zeros(4), bs, xh), o)
+    dev = torch.device("cuda:0")
+    xd = [torch.zeros(d, dtype=torch.float64, device=dev) for d in ds]
+    bk.solve_batched(ctx, bk.Batch([torch.from_numpy(a).to(dev) for a in mats], np.zeros(4),
+                                   [torch.from_numpy(b).to(dev) for b in bs], xd), o)
+    for i in range(4):
+        np.testing.assert_array_equal(xh[i], xd[i].cpu().numpy())
+
+
+def test_batched_ragged_and_tiny(bk, ctx):
+    """Sizes below the block width (m = d: one load is exact), a ragged tail of a
+    128-row tile, and a shift mu > 0, in one batch of mixed widths."""
+    rng = np.random.default_rng(7)
+    ds = [3, 17, 129, 257]
+    mats, bs, mus = [], [], [0.5, 1e-3, 0.0, 2.0]
+    for d in ds:
+        q = np.linalg.qr(rng.standard_normal((d, d)))[0]
+        mats.append(np.ascontiguousarray((q * np.linspace(1, 50, d)) @ q.T))
+        bs.append(rng.standard_normal(d))
+    xs = [np.zeros(d) for d in ds]
+    infos = bk.solve_batched(ctx, bk.Batch(mats, mus, bs, xs),
+                             bk.default_opts(tol=1e-11, sketch=20, seed=1, inner="fp64"))
+    for i, d in enumerate(ds):
+        assert direct.rel_residual(operators.Dense(mats[i]), mus[i], xs[i], bs[i]) <= 1e-11
+        if d <= 21:
+            assert infos[i].loads <= 2, infos[i].as_dict()
+
+
+def test_batched_rejects_bad_input(bk, ctx):
+    a = np.eye(4, dtype=np.float64)
+    b = np.ones(4)
+    x = np.zeros(4)
+    with pytest.raises(bk.BKError):  # FP32 blocks need FP32 values
+        bk.solve_batched(ctx, bk.Batch([a], [0.0], [b], [x]), bk.default_opts(inner="fp32"))
+    with pytest.raises(bk.BKError):  # negative shift
+        bk.solve_batched(ctx, bk.Batch([a], [-1.0], [b], [x]), bk.default_opts())
+
+
+def test_autotune_table(bk, ctx):
+    seed = W.BASE_SEED + 42
+    ds, mats, bs = make_batch(seed, 4, 300, 1200)
+    xs = [np.zeros(d) for d in ds]
+    cal = bk.Batch(mats, np.zeros(len(ds)), bs, xs)
+    chosen = bk.autotune(ctx, cal, [8, 16, 32], bk.default_opts(tol=1e-8, inner="fp32", inner_tol=1e-5))
+    assert set(chosen.tolist()) <= {8, 16, 32}
+    # a fresh batch solved with sketch = -1 uses the table and converges
+    ds2, mats2, bs2 = make_batch(seed + 100, 4, 300, 1200)
+    xs2 = [np.zeros(d) for d in ds2]
+    bk.solve_batched(ctx, bk.Batch(mats2, np.zeros(4), bs2, xs2),
+                     bk.default_opts(tol=1e-8, sketch=-1, inner="fp32", inner_tol=1e-5))
+    for i in range(4):
+        assert rel_res(mats2[i], xs2[i], bs2[i]) <= 1e-8
