@@ -42,7 +42,7 @@ OMEGA_SEED = W.BASE_SEED + 3
 METRIC = "solves/s at rel. residual 1e-8 and HBM GB/s per iteration, mixed vs FP64 plain"
 WORKLOAD = "csr_diffusion_128^3_d2097152_nnz14581760_mu1e-4_l32"
 KERNEL_SOURCES = ["paper_2501_18717_gb300/csrc/k_ops.cu", "paper_2501_18717_gb300/csrc/k_block.cu",
-                  "paper_2501_18717_gb300/csrc/bk_tile.cuh"]
+                  "paper_2501_18717_gb300/csrc/bk_tile.cuh", "paper_2501_18717_gb300/csrc/bk_update.cuh"]
 
 
 def parse():
