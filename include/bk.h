@@ -147,7 +147,12 @@ const char* bk_last_error(const bk_ctx* ctx);
  *   info may be NULL
  * With inner = BK_PREC_FP32 the block products use an FP32 copy of the values
  * (made by the library from FP64 values, or the values themselves when dtype is
- * FP32) and the refinement residual uses the values as given. */
+ * FP32) and the refinement residual uses the values as given. Dense FP32 products run
+ * on the tensor cores (TF32 with split operands and FP32 sums of 32-wide K slices,
+ * FP32 accuracy) when the rows are 16-byte aligned (base 16-byte aligned, ld a
+ * multiple of 4; the library's own FP32 copy always is), else on FFMA.
+ * Returns BK_TIMEOUT (x holds the last refined iterate) if a tensor-core pipeline
+ * wait gave up. */
 bk_status bk_solve(bk_ctx* ctx, const bk_operator* A, double mu, const double* b, double* x,
                    const bk_opts* opts, bk_info* info);
 
@@ -197,7 +202,10 @@ bk_status bk_sample(bk_ctx* ctx, const bk_operator* K, double nugget, int32_t m,
  * of a group, each system owning thread blocks in proportion to d_i^2 m_i; a chunk of
  * check_every steps is replayed as a CUDA graph and systems that have converged skip
  * their work. FP64 refinement restarts as in bk_solve.
- *   A      n dense operators, all FP32 or all FP64 values (BK_DENSE only)
+ *   A      n dense operators, all FP32 or all FP64 values (BK_DENSE only). With FP32
+ *          blocks, a width group whose matrices all have 16-byte aligned rows (device
+ *          base 16-byte aligned, ld a multiple of 4) runs its block products on the
+ *          tensor cores (TF32 with split operands, FP32 accuracy); otherwise on FFMA.
  *   mu     n shifts (host array); b, x: n pointers to d_i doubles (host or device)
  *   opts   as bk_solve; sketch = -1 takes the block width per system from the table that
  *          bk_autotune filled in this context (nearest size bucket floor(log2 d); 16

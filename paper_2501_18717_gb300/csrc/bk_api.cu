@@ -112,6 +112,7 @@ cudaError_t residual(bk_ctx* c, const OpDev& o, double mu, const double* x, cons
 
 struct SolveBufs {
   void *P, *Q, *Y, *omega, *gi_t, *xc_t, *ti_t, *t_t;
+  float* pt = nullptr;  // P^T head/tail for the tensor-core dense product
   double *xin, *x64, *r64, *partsG, *partsS, *G, *S, *cvec, *normp;
   DevState* state;
   int npG, npS;
@@ -307,22 +308,38 @@ bk_status bk_block_apply(bk_ctx* c, const bk_operator* A, double mu, int32_t dty
   bool ydev = is_device_ptr(Y);
   void* yo = Y;
   if (!ydev) BK_CK(ws_get(c, WS_TMP_S, bytes, &yo));
+  const bool use_tc = o.kind == BK_DENSE && !is64 && bk::dense_tc_usable(d, vin, lda_in, mp);
   int np = (o.kind == BK_CSR) ? bk::csr_spmm_gram_grid(is64, mp, d, c->device)
-                              : bk::dense_gram_grid(is64, mp, d, c->device);
+                              : (use_tc ? bk::dense_tc_tiles(d) : bk::dense_gram_grid(is64, mp, d, c->device));
   double* parts = nullptr;
   BK_CK(ws_get(c, WS_PARTS_G, (size_t)np * bk::gram_entries(mp) * 8, (void**)&parts));
   bool gdev = is_device_ptr(G);
   double* go = G;
   if (!gdev) BK_CK(ws_get(c, WS_TMP_OUT, (size_t)m * m * 8, (void**)&go));
+  int* tcerr = nullptr;
   if (o.kind == BK_CSR)
     BK_CK(bk::launch_csr_spmm_gram(is64, mp, d, o.rowptr, o.colidx, vin, mu, p, yo, ld, (int)m, parts, np, nullptr,
                                    c->stream));
-  else
+  else if (use_tc) {
+    float* pt = nullptr;
+    BK_CK(ws_get(c, WS_PT, bk::dense_tc_pt_bytes(d, mp), (void**)&pt));
+    BK_CK(ws_get(c, WS_TCERR, 64, (void**)&tcerr));
+    BK_CK(cudaMemsetAsync(tcerr, 0, sizeof(int), c->stream));
+    BK_CK(bk::launch_dense_gram_tc(mp, d, (const float*)vin, lda_in, mu, (const float*)p, (float*)yo, ld, (int)m,
+                                   parts, np, nullptr, pt, tcerr, c->stream));
+  } else
     BK_CK(bk::launch_dense_gram(is64, mp, d, vin, lda_in, mu, p, yo, ld, (int)m, parts, np, nullptr, c->stream));
   BK_CK(bk::launch_reduce_gram(mp, (int)m, parts, np, go, nullptr, c->stream));
   if (!ydev) BK_CK(cudaMemcpyAsync(Y, yo, bytes, cudaMemcpyDeviceToHost, c->stream));
   if (!gdev) BK_CK(cudaMemcpyAsync(G, go, (size_t)m * m * 8, cudaMemcpyDeviceToHost, c->stream));
+  int herr = 0;
+  if (tcerr) BK_CK(cudaMemcpyAsync(c->hparts, tcerr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   BK_CK(cudaStreamSynchronize(c->stream));
+  if (tcerr) std::memcpy(&herr, c->hparts, sizeof(int));
+  if (herr) {
+    std::snprintf(c->last_error, sizeof(c->last_error), "tensor-core pipeline wait timed out");
+    return BK_TIMEOUT;
+  }
   return BK_OK;
 }
 
@@ -381,8 +398,11 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
   BK_CK(ws_get(c, WS_XIN, (size_t)d * 8, (void**)&w.xin));
   BK_CK(ws_get(c, WS_X64, (size_t)d * 8, (void**)&w.x64));
   BK_CK(ws_get(c, WS_R64, (size_t)d * 8, (void**)&w.r64));
+  // dense FP32 products run on the tensor cores when the matrix layout allows TMA
+  const bool use_tc = o.kind == BK_DENSE && !is64 && bk::dense_tc_usable(d, vin, lda_in, mp);
   w.npG = (o.kind == BK_CSR) ? bk::csr_spmm_gram_grid(is64, mp, d, c->device)
-                             : bk::dense_gram_grid(is64, mp, d, c->device);
+                             : (use_tc ? bk::dense_tc_tiles(d) : bk::dense_gram_grid(is64, mp, d, c->device));
+  if (use_tc) BK_CK(ws_get(c, WS_PT, bk::dense_tc_pt_bytes(d, mp), (void**)&w.pt));
   w.npS = bk::update_r_grid(is64, mp, d, c->device);
   int npStart = bk::gram_grid(is64, mp, d, c->device);
   int ne = bk::gram_entries(mp);
@@ -455,6 +475,9 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
     if (o.kind == BK_CSR)
       e = bk::launch_csr_spmm_gram(is64, mp, d, o.rowptr, o.colidx, vin, mu, w.P, w.Y, ld, m, w.partsG, w.npG,
                                    w.state, st);
+    else if (use_tc)
+      e = bk::launch_dense_gram_tc(mp, d, (const float*)vin, lda_in, mu, (const float*)w.P, (float*)w.Y, ld, m,
+                                   w.partsG, w.npG, w.state, w.pt, &w.state->timeout, st);
     else
       e = bk::launch_dense_gram(is64, mp, d, vin, lda_in, mu, w.P, w.Y, ld, m, w.partsG, w.npG, w.state, st);
     if (e != cudaSuccess) return e;
@@ -541,6 +564,11 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
     const DevState hs = *c->hstate;
     loads += hs.loads;
     refinements += 1;
+    if (hs.timeout) {
+      std::snprintf(c->last_error, sizeof(c->last_error), "tensor-core pipeline wait timed out");
+      result = BK_TIMEOUT;
+      break;
+    }
     BK_CK(bk::launch_axpy(d, rnorm, w.xin, w.x64, st));
     double rn = 0.0;
     BK_CK(residual(c, o, mu, w.x64, bd, w.r64, w.normp, &rn));

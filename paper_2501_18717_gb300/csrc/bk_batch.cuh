@@ -23,16 +23,34 @@ struct BSys {
   void *P, *Q, *Y;          // panel blocks (directions, residual basis, A_mu P)
   double *xin, *x64, *r64;  // inner iterate, solution, FP64 residual
   const double* b;
-  double *Gp, *Sp;          // per-CTA Gram partials (entries x ncta)
+  double *Gp, *Sp;          // per-CTA Gram partials (entries x npG, entries x ncta)
+  int npG;                  // partials of G: ncta, or the row tiles of the tensor-core product
+  float* pt;                // P^T head/tail for the tensor-core product (or null)
   double* cvec;             // c = C e_1 (R = Q C), FP64
   void *gi_t, *xc_t;        // G^+ (mp x mp) and G^+ c (mp) in the block precision
   void *ti_t, *t_t;         // (T^+)^T and T (mp x mp, row-major) in the block precision
   DevState* st;
 };
 
-// One block-CG step for every system of a group with padded width mp.
+// Tensor-core block product for a group whose systems all qualify (FP32 values,
+// 16-byte aligned rows): CTA i computes row tile tile_row[i] of system tile_sys[i];
+// maps holds two CUtensorMaps per system (A, then P^T head/tail), 64-byte aligned.
+struct BatchTc {
+  const int* tile_sys = nullptr;
+  const int* tile_row = nullptr;
+  int ntiles = 0;
+  const void* maps = nullptr;
+};
+cudaError_t launch_batch_dense_tc(int mp, BSys* sys, const int* cta_sys, int ncta, const BatchTc& tc,
+                                  cudaStream_t st);
+// Host: the two tensor maps of one system (A: d x d, row pitch lda; P^T: 2N x d, pitch
+// round_up(d, 32)) written to out[0], out[1].
+cudaError_t tc_make_maps(int mp, int64_t d, const float* A, int64_t lda, const float* pt, void* out);
+
+// One block-CG step for every system of a group with padded width mp (tc: the group's
+// tensor-core product, or null for the FFMA product).
 cudaError_t launch_batch_step(int is_f64, int vals_f64, int mp, BSys* sys, int nsys, const int* cta_sys, int ncta,
-                              double rank_tol, cudaStream_t st);
+                              double rank_tol, const BatchTc* tc, cudaStream_t st);
 // Start blocks of the active systems (Q = [r/||r||, Omega/sqrt(d)] normalised, P = Q,
 // c = T e_1); resets their control blocks.
 cudaError_t launch_batch_start(int is_f64, int mp, BSys* sys, int nsys, const int* cta_sys, int ncta, uint64_t seed,

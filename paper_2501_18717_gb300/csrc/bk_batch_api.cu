@@ -2,6 +2,7 @@
 // Systems are grouped by padded block width; each group advances with one launch per
 // step kernel (k_batch.cu), a chunk of steps replayed as a CUDA graph, and the host
 // polls the per-system control blocks between chunks. FP64 refinement as in bk_solve.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,6 +29,11 @@ struct Group {
   int* cta_sys = nullptr;    // device copy of hcta
   int ncta = 0;
   cudaGraphExec_t gexec = nullptr;
+  // tensor-core block product (all systems of the group qualify)
+  bool tc = false;
+  std::vector<int> htile;        // tile_sys then tile_row
+  std::vector<CUtensorMap> hmaps;  // two per system
+  bk::BatchTc btc;
 };
 
 int size_bucket(int64_t d) {
@@ -128,6 +134,14 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
     Group& g = kv.second;
     g.mp = kv.first;
     glist.push_back(&g);
+    // the tensor-core product needs FP32 values with 16-byte aligned rows (host values
+    // are staged to 256-byte aligned buffers with the caller's lda)
+    g.tc = !is64;
+    for (int i : g.members) {
+      const bool dev = bkx::is_device_ptr(A[i].vals);
+      const void* probe = dev ? A[i].vals : reinterpret_cast<const void*>(uintptr_t(256));
+      g.tc = g.tc && bk::dense_tc_usable(A[i].rows, probe, A[i].ld, g.mp);
+    }
     // thread blocks per system: proportional to d^2 m, at least one, at most its row tiles
     double wsum = 0.0;
     for (int i : g.members) wsum += (double)A[i].rows * A[i].rows * ms[i];
@@ -155,9 +169,24 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
       // compiled for that width and read or write the padding panels as zeros
       const size_t blk = up256((size_t)s.ld * g.mp * es);
       const int ne = bk::gram_entries(g.mp);
-      arena += 3 * blk + 4 * up256((size_t)d * 8) + 2 * up256((size_t)ne * nc * 8) + up256((size_t)s.m * 8) +
-               3 * up256((size_t)g.mp * g.mp * es) + up256((size_t)g.mp * es);
+      const int rtiles = bk::dense_tc_tiles(d);
+      s.npG = g.tc ? rtiles : nc;
+      arena += 3 * blk + 4 * up256((size_t)d * 8) + up256((size_t)ne * s.npG * 8) + up256((size_t)ne * nc * 8) +
+               up256((size_t)s.m * 8) + 3 * up256((size_t)g.mp * g.mp * es) + up256((size_t)g.mp * es);
+      if (g.tc) {
+        arena += up256(bk::dense_tc_pt_bytes(d, g.mp));
+        for (int t = 0; t < rtiles; ++t) g.htile.push_back((int)k);
+      }
       g.hs.push_back(s);
+    }
+    if (g.tc) {
+      const size_t nt = g.htile.size();
+      g.htile.resize(2 * nt);
+      size_t t = 0;
+      for (size_t k = 0; k < g.hs.size(); ++k)
+        for (int r = 0; r < bk::dense_tc_tiles(g.hs[k].d); ++r) g.htile[nt + t++] = r;
+      g.btc.ntiles = (int)nt;
+      arena += up256(sizeof(int) * 2 * nt) + up256(sizeof(CUtensorMap) * 2 * g.hs.size());
     }
     arena += up256(sizeof(bk::BSys) * g.hs.size()) + up256(sizeof(int) * g.hcta.size());
     total_cta = std::max(total_cta, g.ncta);
@@ -202,17 +231,35 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
       s.x64 = (double*)take((size_t)d * 8);
       s.r64 = (double*)take((size_t)d * 8);
       double* bcopy = (double*)take((size_t)d * 8);
-      s.Gp = (double*)take((size_t)ne * s.ncta * 8);
+      s.Gp = (double*)take((size_t)ne * s.npG * 8);
       s.Sp = (double*)take((size_t)ne * s.ncta * 8);
       s.cvec = (double*)take((size_t)s.m * 8);
       s.gi_t = take((size_t)g->mp * g->mp * es);
       s.ti_t = take((size_t)g->mp * g->mp * es);
       s.t_t = take((size_t)g->mp * g->mp * es);
       s.xc_t = take((size_t)g->mp * es);
+      s.pt = nullptr;
+      if (g->tc) s.pt = (float*)take(bk::dense_tc_pt_bytes(d, g->mp));
       BK_CKG(cudaMemcpyAsync(bcopy, b[i], (size_t)d * 8, cudaMemcpyDefault, st));
       s.b = bcopy;
       BK_CKG(cudaMemsetAsync(s.x64, 0, (size_t)d * 8, st));
     }
+  }
+  // tensor-core groups: tile tables and the two tensor maps of every system
+  for (Group* g : glist) {
+    if (!g->tc) continue;
+    int* tiles = (int*)take(sizeof(int) * g->htile.size());
+    CUtensorMap* maps = (CUtensorMap*)take(sizeof(CUtensorMap) * 2 * g->hs.size());
+    g->hmaps.resize(2 * g->hs.size());
+    for (size_t k = 0; k < g->hs.size(); ++k) {
+      const bk::BSys& s = g->hs[k];
+      BK_CKG(bk::tc_make_maps(g->mp, s.d, (const float*)s.A, s.lda, s.pt, &g->hmaps[2 * k]));
+    }
+    BK_CKG(cudaMemcpyAsync(tiles, g->htile.data(), sizeof(int) * g->htile.size(), cudaMemcpyHostToDevice, st));
+    BK_CKG(cudaMemcpyAsync(maps, g->hmaps.data(), sizeof(CUtensorMap) * g->hmaps.size(), cudaMemcpyHostToDevice, st));
+    g->btc.tile_sys = tiles;
+    g->btc.tile_row = tiles + g->btc.ntiles;
+    g->btc.maps = maps;
   }
   std::vector<double> hparts(total_cta + 16);
   std::vector<bk::DevState> hst(n);
@@ -276,7 +323,7 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
             cudaError_t ce = cudaSuccess;
             for (int it = 0; it < opts.check_every && ce == cudaSuccess; ++it)
               ce = bk::launch_batch_step(is64, vals_f64, g->mp, g->ds, (int)g->hs.size(), g->cta_sys, g->ncta,
-                                         rank_tol, st);
+                                         rank_tol, g->tc ? &g->btc : nullptr, st);
             cudaError_t ee = cudaStreamEndCapture(st, &graph);
             BK_CKG(ce);
             BK_CKG(ee);
@@ -288,7 +335,7 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
         } else {
           for (int it = 0; it < opts.check_every; ++it)
             BK_CKG(bk::launch_batch_step(is64, vals_f64, g->mp, g->ds, (int)g->hs.size(), g->cta_sys, g->ncta,
-                                         rank_tol, st));
+                                         rank_tol, g->tc ? &g->btc : nullptr, st));
         }
       }
       BK_CKG(cudaMemcpyAsync(hst.data(), dstates, sizeof(bk::DevState) * n, cudaMemcpyDeviceToHost, st));

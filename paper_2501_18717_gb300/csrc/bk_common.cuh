@@ -26,7 +26,7 @@ struct DevState {
   int loads;        // block products completed in this inner solve
   int status;       // ST_* below
   int max_loads;    // cap for this inner solve
-  int pad_;
+  int timeout;      // set by a kernel whose bounded wait on a pipeline barrier gave up
   double tol_abs;   // target on ||R e_1|| = ||c|| (column 0 starts with norm 1)
   double res;       // latest ||c|| from the recurrence
 };
@@ -64,6 +64,17 @@ cudaError_t launch_dense_gram(int is_f64, int mp, int64_t d, const void* A, int6
                               const void* P, void* Y, int64_t ld, int m, double* parts, int nparts,
                               const DevState* state, cudaStream_t st);
 int dense_gram_grid(int is_f64, int mp, int64_t d, int device);
+
+// Tensor-core variant for FP32 values (k_tc.cu): usable when A is 16-byte aligned, lda
+// is a multiple of 4 and mp <= 36. One CTA per 128-row tile (nparts = dense_tc_tiles(d));
+// pt is scratch for P^T head and tail (dense_tc_pt_bytes). *err is set to 1 if a
+// pipeline wait timed out (the product is then invalid).
+bool dense_tc_usable(int64_t d, const void* A, int64_t lda, int mp);
+int dense_tc_tiles(int64_t d);
+size_t dense_tc_pt_bytes(int64_t d, int mp);
+cudaError_t launch_dense_gram_tc(int mp, int64_t d, const float* A, int64_t lda, double mu, const float* P, float* Y,
+                                 int64_t ld, int m, double* parts, int nparts, const DevState* state, float* pt,
+                                 int* err, cudaStream_t st);
 
 // Partials of G = X^T Y.
 cudaError_t launch_gram(int is_f64, int mp, int64_t d, const void* X, const void* Y, int64_t ld, int m,

@@ -18,6 +18,8 @@ enum Slot {
   WS_LSHIFT, WS_LB64, WS_LQ2,
   // batched solver
   WS_BATCH, WS_BATCH_VALS,
+  // tensor-core dense product: P^T head/tail, timeout flag
+  WS_PT, WS_TCERR,
   WS_COUNT
 };
 

@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kBSmall) k_bsmall(BSys* __restrict__ sys, int 
     if (mode == 0 && threadIdx.x == 0) st->pending_x = 0;
     return;
   }
-  reduce_parts<MP>(mode == 0 ? S.Gp : S.Sp, S.ncta, m, sh.W);
+  reduce_parts<MP>(mode == 0 ? S.Gp : S.Sp, mode == 0 ? S.npG : S.ncta, m, sh.W);
   __syncthreads();
   const int rank = block_cholesky_skip<kBSmall>(sh, m, rank_tol);
   if (mode == 0) {
@@ -377,6 +377,7 @@ __global__ void k_bstart(BSys* __restrict__ sys, const int* __restrict__ cta_sys
       st->loads = 0;
       st->status = S.active ? ST_RUNNING : ST_CONVERGED;
       st->max_loads = S.max_loads;
+      st->timeout = 0;
       st->tol_abs = S.tol_abs;
       st->res = 1.0;
     }
@@ -457,9 +458,12 @@ size_t bop_smem() {
 }
 
 template <typename T, typename VA, int MP>
-cudaError_t step_impl(BSys* sys, int nsys, const int* cta_sys, int ncta, double rank_tol, cudaStream_t st) {
+cudaError_t step_impl(BSys* sys, int nsys, const int* cta_sys, int ncta, double rank_tol, const BatchTc* tc,
+                      cudaStream_t st) {
   cudaError_t e;
-  {
+  if (tc) {
+    if ((e = launch_batch_dense_tc(MP, sys, cta_sys, ncta, *tc, st)) != cudaSuccess) return e;
+  } else {
     auto k = k_bop<T, VA, MP, 16, 64, 128>;
     size_t sm = bop_smem<T, MP>();
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess) return e;
@@ -501,13 +505,14 @@ cudaError_t start_impl(BSys* sys, int nsys, const int* cta_sys, int ncta, uint64
 }  // namespace
 
 cudaError_t launch_batch_step(int is_f64, int vals_f64, int mp, BSys* sys, int nsys, const int* cta_sys, int ncta,
-                              double rank_tol, cudaStream_t st) {
+                              double rank_tol, const BatchTc* tc, cudaStream_t st) {
   if (!is_f64 && vals_f64) return cudaErrorInvalidValue;  // FP32 blocks take FP32 values
-#define BK_B(MPV)                                                                                  \
-  case MPV:                                                                                        \
-    return is_f64 ? (vals_f64 ? step_impl<double, double, MPV>(sys, nsys, cta_sys, ncta, rank_tol, st) \
-                              : step_impl<double, float, MPV>(sys, nsys, cta_sys, ncta, rank_tol, st))  \
-                  : step_impl<float, float, MPV>(sys, nsys, cta_sys, ncta, rank_tol, st);
+  if (tc && is_f64) return cudaErrorInvalidValue;          // the tensor-core product is FP32
+#define BK_B(MPV)                                                                                           \
+  case MPV:                                                                                                 \
+    return is_f64 ? (vals_f64 ? step_impl<double, double, MPV>(sys, nsys, cta_sys, ncta, rank_tol, nullptr, st) \
+                              : step_impl<double, float, MPV>(sys, nsys, cta_sys, ncta, rank_tol, nullptr, st))  \
+                  : step_impl<float, float, MPV>(sys, nsys, cta_sys, ncta, rank_tol, tc, st);
   switch (mp) {
     BK_B(4)
     BK_B(8)

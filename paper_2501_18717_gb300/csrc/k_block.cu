@@ -377,6 +377,7 @@ __global__ void k_init_state(DevState* s, int max_loads, double tol_abs, double*
     s->loads = 0;
     s->status = ST_RUNNING;
     s->max_loads = max_loads;
+    s->timeout = 0;
     s->tol_abs = tol_abs;
     s->res = 1.0;
   }

@@ -294,9 +294,11 @@ def batch_system(seed: int, i: int, d: int, dtype=np.float32):
     return A, b
 
 
-def batch_system_torch(seed: int, i: int, d: int, device, dtype=None):
+def batch_system_torch(seed: int, i: int, d: int, device, dtype=None, pitch: int = 32):
     """The same A_i as batch_system, formed on a CUDA device with torch (float64, then
-    rounded); for batches too large to build on the host."""
+    rounded); for batches too large to build on the host. Rows are stored with a pitch
+    rounded up to a multiple of `pitch` elements (a strided view), so every row starts
+    on a 16-byte boundary."""
     import torch
     dtype = torch.float32 if dtype is None else dtype
     lam = torch.from_numpy(batch_spectrum(seed, i, d)).to(device)
@@ -304,6 +306,10 @@ def batch_system_torch(seed: int, i: int, d: int, device, dtype=None):
     for v in torch.from_numpy(batch_reflectors(seed, i, d)).to(device):
         w = A @ v
         A -= 2.0 * torch.outer(v, w) + 2.0 * torch.outer(w, v) - 4.0 * torch.dot(v, w) * torch.outer(v, v)
-    A = (0.5 * (A + A.T)).to(dtype).contiguous()
+    A = (0.5 * (A + A.T)).to(dtype)
+    ldp = (d + pitch - 1) // pitch * pitch
+    buf = torch.zeros((d, ldp), dtype=dtype, device=device)
+    buf[:, :d] = A
+    del A
     b = torch.from_numpy(normals(seed + 1 + i, STREAM_RHS, d)).to(device)
-    return A, b
+    return buf[:, :d], b
