@@ -5,22 +5,27 @@
 // and accumulating three products (A_hi P_hi + A_hi P_lo + A_lo P_hi; the dropped
 // A_lo P_lo is ~2^-26 relative).
 //
-// One CTA computes one 128-row tile of Y over all columns:
-//   warp 0      TMA producer: A tile (128 rows x 32 K, 128-byte swizzle) and the two
-//               32 x N slices of P^T (head and tail) per stage, 4 stages;
-//   warp 1      allocates tensor memory and issues the MMAs (M = 128, N = 16/32/48,
-//               K = 8 per instruction, 12 per stage) into one of two accumulators,
-//               then commits to the stage's "empty" and the accumulator's "full"
-//               barrier;
-//   warps 2-5   split each A tile in place into head and tail (the split is
-//               elementwise, so the swizzled layout is kept), and drain the
-//               accumulator of the previous stage into FP32 registers (one row per
-//               thread). The tensor core's FP32 accumulation does not round to
-//               nearest, and its error grows with the number of accumulation steps;
-//               summing 32-wide K slices in registers keeps the product at FFMA
-//               accuracy. The epilogue adds mu P, writes Y in the panel layout and
-//               stages P and Y rows for the Gram.
-// All threads then form the per-CTA Gram partial (bk_tile.cuh).
+// One CTA computes one 128-row tile of Y over all columns. A tiles land in a ring of
+// 5 stages that is refilled as soon as the split warps have read a tile; the P^T
+// slices have their own ring of 6 stages that the MMAs release, so neither load
+// stream waits on the MMAs of the stage it refills; the split head/tail tiles live
+// in 2 working stages that the MMAs read.
+//   warp 0      TMA producer for A (128 rows x 32 K, 128-byte swizzle);
+//   warp 2      TMA producer for the P^T head and tail slices (adjacent rows, from L2);
+//   warp 1      allocates tensor memory and issues the MMAs into one of two
+//               accumulators: per 8-wide K step A_hi [P_hi; P_lo] (2N columns) and
+//               A_lo P_hi added to the first N columns; then commits to the working
+//               stage's "empty" and the accumulator's "full" barrier;
+//   warps 3-10  split each A tile into head and tail (elementwise, so the swizzled
+//               layout is kept), and drain the accumulator of the previous stage into
+//               FP32 registers: each tensor-memory lane quarter is read by two warps,
+//               one per half of the columns. The tensor core's FP32 accumulation does
+//               not round to nearest and its error grows with the number of
+//               accumulation steps; summing 32-wide K slices in registers keeps the
+//               product at FFMA accuracy.
+// The epilogue joins the column halves in shared memory, adds mu P, writes Y in the
+// panel layout and stages P and Y rows; all threads then form the per-CTA Gram
+// partial (bk_tile.cuh).
 //
 // P^T is prepared once per product by k_pt_split: rows [0, N) hold the TF32 heads of
 // the columns of P, rows [N, 2N) the tails, leading dimension ldk = round_up(d, 32).
@@ -40,19 +45,32 @@ namespace {
 
 using namespace sm100;
 
-constexpr int kTcThreads = 192;
+constexpr int kTcThreads = 352;  // warp 0 A loads, warp 1 MMA, warp 2 P^T loads, warps 3-10 split / drain
 
 template <int MP>
 struct TcShape {
-  static constexpr int N = MP <= 16 ? 16 : (MP <= 32 ? 32 : 48);  // MMA width (multiple of 16)
-  static constexpr int S = 4;                                     // pipeline stages
-  static constexpr int kA = 128 * 32 * 4;                         // one A tile (head or tail)
-  static constexpr int kB = N * 32 * 4;                           // one P^T slice (head or tail)
-  static constexpr int kStage = 2 * kA + 2 * kB;
-  static constexpr int kBar = S * kStage;  // barrier area after the stages
-  static constexpr int kSmem = kBar + 256 + 1024;  // + barriers, + alignment slack
-  static constexpr uint32_t kTmemCols = 128;  // two accumulators of 64 columns
-  static_assert(kB % 1024 == 0, "operand tiles must stay on 1024-byte boundaries");
+  static constexpr int N = MP <= 16 ? 16 : (MP <= 32 ? 32 : 48);  // columns of P (multiple of 16)
+  static constexpr int KS = 64;                                   // K per pipeline step (two 32-wide boxes)
+  static constexpr int R = 4;                                     // A landing stages
+  static constexpr int RB = 3;                                    // P^T slice stages
+  static constexpr int W = 2;                                     // A head/tail stages in tensor memory
+  static constexpr int kBox = 128 * 32 * 4;                       // one A box: 128 rows x 32 K
+  static constexpr int kA = 2 * kBox;                             // one A stage as loaded
+  static constexpr int kBBox = 2 * N * 32 * 4;                    // one P^T box: head N rows, tail N rows
+  static constexpr int kB = 2 * kBBox;                            // one P^T stage
+  static constexpr int kOffB = R * kA;                            // P^T ring
+  static constexpr int kBar = kOffB + RB * kB;                    // barrier area after the buffers
+  static constexpr int kSmem = kBar + 512 + 1024;                 // + barriers, + alignment slack
+  static constexpr uint32_t kAccCols = 128;                       // one accumulator: 2N <= 96 columns
+  static constexpr uint32_t kACols = 128;                         // one A stage: head 64 + tail 64 columns
+  static constexpr uint32_t kAOff = 2 * kAccCols;                 // A stages after the two accumulators
+  static constexpr uint32_t kTmemCols = 512;
+  static_assert(kAOff + W * kACols <= kTmemCols, "tensor memory budget");
+  static_assert(kBBox % 1024 == 0, "operand tiles must stay on 1024-byte boundaries");
+  static_assert((N / 2) % 8 == 0, "each drain warp reads whole 8-column groups");
+  static_assert((128 * (N + 1) * 4) % 16 == 0, "Gram staging stays 16-byte aligned");
+  static_assert(kSmem <= 232448, "shared memory per CTA");
+  static_assert(128 * (N + 1 + 2 * MP) * 4 <= kOffB, "epilogue staging fits in the A ring");
 };
 
 __device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
@@ -92,34 +110,49 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
                                               int tile, const float* __restrict__ P, float* __restrict__ Y,
                                               int64_t ld, int m, float mu, double* parts, int nparts, int* err) {
   using SH = TcShape<MP>;
-  constexpr int N = SH::N, S = SH::S;
+  constexpr int N = SH::N, R = SH::R, RB = SH::RB, W = SH::W, NH = N / 2;
+  constexpr int kConv = kTcThreads - 96;  // split / drain threads (warps 3..10)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + SH::kBar);
-  uint64_t* split = full + S;
-  uint64_t* empty = split + S;
-  uint64_t* acc_full = empty + S;   // [2]
+  uint8_t* raw = base;                 // R x kA: A tiles as loaded (128-byte swizzle)
+  uint8_t* bring = base + SH::kOffB;   // RB x 2 kB: P^T head + tail slices
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(base + SH::kBar);
+  uint64_t* raw_empty = raw_full + R;
+  uint64_t* b_full = raw_empty + R;    // [RB]
+  uint64_t* b_empty = b_full + RB;     // [RB]
+  uint64_t* w_split = b_empty + RB;    // [W]
+  uint64_t* w_empty = w_split + W;     // [W]
+  uint64_t* acc_full = w_empty + W;    // [2]
   uint64_t* acc_empty = acc_full + 2;  // [2]
   uint64_t* cleanup = acc_empty + 2;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(cleanup + 1);
   volatile int* s_abort = reinterpret_cast<volatile int*>(tmem_holder + 1);
-  volatile int* s_consumed = s_abort + 1;
+  volatile int* s_a_consumed = s_abort + 1;  // A tiles read by the split warps
+  volatile int* s_b_consumed = s_abort + 2;  // P^T slices taken by the MMA thread
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nk = (int)((d + 31) / 32);
+  const int nk = (int)((d + SH::KS - 1) / SH::KS);  // pipeline steps of KS columns
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(full + s, 1);
-      mbar_init(split + s, 128);
-      mbar_init(empty + s, 1);
+    for (int s = 0; s < R; ++s) {
+      mbar_init(raw_full + s, 1);
+      mbar_init(raw_empty + s, kConv);
+    }
+    for (int t = 0; t < RB; ++t) {
+      mbar_init(b_full + t, 1);
+      mbar_init(b_empty + t, 1);
+    }
+    for (int w = 0; w < W; ++w) {
+      mbar_init(w_split + w, kConv);
+      mbar_init(w_empty + w, 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full + b, 1);
-      mbar_init(acc_empty + b, 128);
+      mbar_init(acc_empty + b, kConv);
     }
     mbar_init(cleanup, 1);
     *s_abort = 0;
-    *s_consumed = 0;
+    *s_a_consumed = 0;
+    *s_b_consumed = 0;
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(tmem_holder, SH::kTmemCols);
@@ -128,90 +161,133 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
-  int issued = 0;  // k-blocks whose loads warp 0 issued
-  float sum[N];    // warps 2-5: this thread's row of the product
+  int issued = 0;  // loads issued by this producer thread (warp 0: A tiles, warp 2: P^T slices)
+  float sum[NH];   // warps 3..10: half a row of the product (this warp's columns)
   if (warp == 0) {
-    if (lane == 0) {
+    if (lane == 0) {  // A tiles, up to R ahead of the split warps
       tma_prefetch_desc(amap_p);
-      tma_prefetch_desc(bmap_p);
       for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % S;
-        const uint32_t r = (uint32_t)(kb / S);
+        const int s = kb % R;
         if (*s_abort) break;
-        if (r > 0 && !mbar_wait(empty + s, (r - 1) & 1)) {
+        if (kb >= R && !mbar_wait(raw_empty + s, (uint32_t)((kb / R) - 1) & 1)) {
           *s_abort = 1;
           break;
         }
-        uint8_t* st = base + s * SH::kStage;
-        mbar_arrive_expect_tx(full + s, SH::kA + 2 * SH::kB);
-        tma_load_2d(st, amap_p, full + s, kb * 32, tile * 128);
-        tma_load_2d(st + 2 * SH::kA, bmap_p, full + s, kb * 32, 0);
-        tma_load_2d(st + 2 * SH::kA + SH::kB, bmap_p, full + s, kb * 32, N);
+        mbar_arrive_expect_tx(raw_full + s, SH::kA);
+        tma_load_2d(raw + s * SH::kA, amap_p, raw_full + s, kb * SH::KS, tile * 128);
+        tma_load_2d(raw + s * SH::kA + SH::kBox, amap_p, raw_full + s, kb * SH::KS + 32, tile * 128);
+        issued = kb + 1;
+      }
+    }
+  } else if (warp == 2) {
+    if (lane == 0) {  // P^T head and tail slices (L2-resident), up to RB ahead of the MMAs
+      tma_prefetch_desc(bmap_p);
+      for (int kb = 0; kb < nk; ++kb) {
+        const int t = kb % RB;
+        if (*s_abort) break;
+        if (kb >= RB && !mbar_wait(b_empty + t, (uint32_t)((kb / RB) - 1) & 1)) {
+          *s_abort = 1;
+          break;
+        }
+        uint8_t* bs = bring + t * SH::kB;
+        mbar_arrive_expect_tx(b_full + t, SH::kB);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {  // box j: head rows, then tail rows
+          tma_load_2d(bs + j * SH::kBBox, bmap_p, b_full + t, kb * SH::KS + 32 * j, 0);
+          tma_load_2d(bs + j * SH::kBBox + SH::kBBox / 2, bmap_p, b_full + t, kb * SH::KS + 32 * j, N);
+        }
         issued = kb + 1;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(128, N);
+      // per 8-wide K step: A_hi [P_hi; P_lo] (2N columns: head products in [0, N),
+      // tail products in [N, 2N)), then A_lo P_hi accumulated into [0, N)
+      constexpr uint32_t idesc2 = idesc_tf32(128, 2 * N);
+      constexpr uint32_t idesc1 = idesc_tf32(128, N);
       for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % S;
-        const uint32_t r = (uint32_t)(kb / S);
-        const int b = kb & 1;
+        const int w = kb % W, t = kb % RB, b = kb & 1;
         if (*s_abort) break;
         if (kb >= 2 && !mbar_wait(acc_empty + b, (uint32_t)((kb >> 1) - 1) & 1)) {
           *s_abort = 1;
           break;
         }
-        if (!mbar_wait(split + s, r & 1)) {
+        if (!mbar_wait(b_full + t, (uint32_t)(kb / RB) & 1)) {
+          *s_abort = 1;
+          break;
+        }
+        *s_b_consumed = kb + 1;
+        if (!mbar_wait(w_split + w, (uint32_t)(kb / W) & 1)) {
           *s_abort = 1;
           break;
         }
         tc_fence_after();
-        uint8_t* st = base + s * SH::kStage;
-        const uint32_t ahi = smem_u32(st), alo = smem_u32(st + SH::kA);
-        const uint32_t bhi = smem_u32(st + 2 * SH::kA), blo = smem_u32(st + 2 * SH::kA + SH::kB);
-        const uint32_t acc = tmem + 64u * b;
+        const uint32_t ahi = tmem + SH::kAOff + SH::kACols * w, alo = ahi + 64;  // tensor-memory A
+        const uint32_t bst = smem_u32(bring + t * SH::kB);
+        const uint32_t acc = tmem + SH::kAccCols * b;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint32_t off = 32u * k;  // 8 TF32 elements of K
-          mma_tf32(acc, desc_kmajor_sw128(ahi + off), desc_kmajor_sw128(bhi + off), idesc, k != 0);
-          mma_tf32(acc, desc_kmajor_sw128(ahi + off), desc_kmajor_sw128(blo + off), idesc, 1u);
-          mma_tf32(acc, desc_kmajor_sw128(alo + off), desc_kmajor_sw128(bhi + off), idesc, 1u);
+        for (int k = 0; k < 8; ++k) {
+          // 8 TF32 elements of K: 8 columns of A; 32 bytes into box k / 4 of P^T (its
+          // P_hi rows followed by its P_lo rows)
+          const uint64_t bd = desc_kmajor_sw128(bst + SH::kBBox * (k >> 2) + 32u * (k & 3));
+          mma_tf32_ts(acc, ahi + 8u * k, bd, idesc2, k != 0);
+          mma_tf32_ts(acc, alo + 8u * k, bd, idesc1, 1u);
         }
-        mma_commit(empty + s);
+        mma_commit(w_empty + w);
+        mma_commit(b_empty + t);
         mma_commit(acc_full + b);
       }
     }
   } else {
-    const int ct = threadIdx.x - 64;  // 0..127
-    const int qd = warp & 3;          // tensor-memory lane quarter of this warp
+    const int ct = threadIdx.x - 96;       // 0 .. kConv - 1
+    const int qd = warp & 3;               // tensor-memory lane quarter of this warp
+    const int half = (warp - 3) >> 2;      // which half of the columns this warp drains
 #pragma unroll
-    for (int c = 0; c < N; ++c) sum[c] = 0.f;
+    for (int c = 0; c < NH; ++c) sum[c] = 0.f;
     for (int kb = 0; kb <= nk; ++kb) {
       // every exit decision below is warp-uniform: the warp runs collective
       // tensor-memory loads
       if (__any_sync(0xffffffffu, *s_abort != 0)) break;
       if (kb < nk) {
-        const int s = kb % S;
-        const uint32_t r = (uint32_t)(kb / S);
-        if (!__all_sync(0xffffffffu, mbar_wait(full + s, r & 1))) {
+        const int s = kb % R, w = kb % W;
+        if (!__all_sync(0xffffffffu, mbar_wait(raw_full + s, (uint32_t)(kb / R) & 1))) {
           *s_abort = 1;
           break;
         }
-        uint8_t* st = base + s * SH::kStage;
-        float4* h = reinterpret_cast<float4*>(st);
-        float4* l = reinterpret_cast<float4*>(st + SH::kA);
-#pragma unroll
-        for (int j = 0; j < SH::kA / 16 / 128; ++j) {
-          const int idx = ct + 128 * j;
-          const float4 v = h[idx];
-          const float4 hv = make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
-          h[idx] = hv;
-          l[idx] = make_float4(v.x - hv.x, v.y - hv.y, v.z - hv.z, v.w - hv.w);
+        if (kb >= W && !__all_sync(0xffffffffu, mbar_wait(w_empty + w, (uint32_t)((kb / W) - 1) & 1))) {
+          *s_abort = 1;
+          break;
         }
-        fence_proxy_async_smem();
-        mbar_arrive(split + s);
-        if (ct == 0) *s_consumed = kb + 1;
+        // this thread's row of the tile and its half of the 64 K columns (box `half`):
+        // 8 chunks of 16 bytes, chunk c of row r stored at chunk position c ^ (r % 8)
+        const int row = 32 * qd + lane;
+        const uint8_t* rrow = raw + s * SH::kA + half * SH::kBox + row * 128;
+        float4 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = *reinterpret_cast<const float4*>(rrow + ((j ^ (row & 7)) << 4));
+        mbar_arrive(raw_empty + s);  // the A tile is in registers: its buffer can refill
+        if (ct == 0) *s_a_consumed = kb + 1;
+        const uint32_t arow = tmem + ((uint32_t)(32 * qd) << 16) + SH::kAOff + SH::kACols * w + 32u * half;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {  // 16 columns at a time
+          uint32_t hv[16], lv[16];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 q = v[4 * g + j];
+            const float x[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float h = tf32_head(x[u]);
+              hv[4 * j + u] = __float_as_uint(h);
+              lv[4 * j + u] = __float_as_uint(x[u] - h);
+            }
+          }
+          tmem_st16(arow + 16u * g, hv);       // head
+          tmem_st16(arow + 64 + 16u * g, lv);  // tail
+        }
+        tmem_st_wait();
+        tc_fence_before();
+        mbar_arrive(w_split + w);
       }
       if (kb >= 1) {  // drain the accumulator of k-block kb - 1
         const int kp = kb - 1, b = kp & 1;
@@ -220,12 +296,17 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
           break;
         }
         tc_fence_after();
-        uint32_t rr[N / 16][16];
+        const uint32_t row_addr = tmem + ((uint32_t)(32 * qd) << 16) + SH::kAccCols * b + NH * half;
+        uint32_t rh[NH / 8][8], rt[NH / 8][8];
 #pragma unroll
-        for (int c = 0; c < N / 16; ++c) tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + 64u * b + 16u * c, rr[c]);
+        for (int c = 0; c < NH / 8; ++c) {
+          tmem_ld8(row_addr + 8u * c, rh[c]);      // A_hi P_hi + A_lo P_hi
+          tmem_ld8(row_addr + N + 8u * c, rt[c]);  // A_hi P_lo
+        }
         tmem_ld_wait();
 #pragma unroll
-        for (int c = 0; c < N; ++c) sum[c] += __uint_as_float(rr[c / 16][c % 16]);
+        for (int c = 0; c < NH; ++c)
+          sum[c] += __uint_as_float(rh[c / 8][c % 8]) + __uint_as_float(rt[c / 8][c % 8]);
         tc_fence_before();
         mbar_arrive(acc_empty + b);
       }
@@ -238,7 +319,9 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
   if (aborted) {
     // let issued loads land and issued MMAs finish before the memory is reused or freed
     if (warp == 0 && lane == 0)
-      for (int kb = *s_consumed; kb < issued; ++kb) mbar_wait(full + kb % S, (uint32_t)(kb / S) & 1);
+      for (int kb = *s_a_consumed; kb < issued; ++kb) mbar_wait(raw_full + kb % R, (uint32_t)(kb / R) & 1);
+    if (warp == 2 && lane == 0)
+      for (int kb = *s_b_consumed; kb < issued; ++kb) mbar_wait(b_full + kb % RB, (uint32_t)(kb / RB) & 1);
     if (warp == 1 && lane == 0) {
       mma_commit(cleanup);
       mbar_wait(cleanup, 0);
@@ -247,15 +330,20 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
   }
   __syncthreads();
 
-  // ---- epilogue: rows of the accumulator -> Y, and the Gram tiles
-  float* sX = reinterpret_cast<float*>(base);
+  // ---- epilogue: the two column halves of each row meet in shared memory
+  constexpr int SA = N + 1;                      // odd row stride: conflict-free column access
+  float* sAcc = reinterpret_cast<float*>(base);  // 128 x SA
+  float* sX = sAcc + 128 * SA;                   // 128 x MP
   float* sY = sX + 128 * MP;
-  if (warp >= 2) {
+  if (warp >= 3) {
+    const int row = 32 * (warp & 3) + lane, half = (warp - 3) >> 2;
+#pragma unroll
+    for (int c = 0; c < NH; ++c) sAcc[row * SA + NH * half + c] = aborted ? 0.f : sum[c];
+  }
+  __syncthreads();
+  if (warp >= 3 && warp < 7) {
     const int row = 32 * (warp & 3) + lane;
     const int64_t gi = (int64_t)tile * 128 + row;
-    float acc[N];
-#pragma unroll
-    for (int c = 0; c < N; ++c) acc[c] = aborted ? 0.f : sum[c];
     const int nq = (m + 3) >> 2;
     float pv[MP], yv[MP];
 #pragma unroll
@@ -268,7 +356,10 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
         for (int u = 0; u < 4; ++u) pv[4 * q + u] = 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) yv[4 * q + u] = live ? fmaf(mu, pv[4 * q + u], acc[4 * q + u]) : 0.f;
+      for (int u = 0; u < 4; ++u) {
+        const int c = 4 * q + u;
+        yv[c] = live ? fmaf(mu, pv[c], sAcc[row * SA + c]) : 0.f;
+      }
       if (live) st4(panel_row(Y, ld, q, gi), yv + 4 * q);
     }
     store_row<MP>(sX, row, pv);
