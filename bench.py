@@ -56,7 +56,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="diffusion", choices=["diffusion", "batched"])
+    ap.add_argument("--workload", default="diffusion", choices=["diffusion", "batched", "dense-product"])
+    ap.add_argument("--dense-d", type=int, default=16384)
+    ap.add_argument("--dense-m", type=int, default=33)
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--fp64-subset", type=int, default=32)
     ap.add_argument("--fp64-steps", type=int, default=1)
@@ -326,6 +328,54 @@ def run_batched(args, world, rank, local, dev):
     return 0
 
 
+def run_dense_product(args, world, rank, local, dev):
+    """One dense FP32 block product Y = A P + mu P with its Gram P^T Y (the tensor-core
+    kernel when the rows are 16-byte aligned): A d x d Gaussian, P d x m. value = GB/s
+    of A streamed per product (A is larger than L2 from d = 6000 on)."""
+    import torch
+    from paper_2501_18717_gb300 import bk
+
+    d, m = args.dense_d, args.dense_m
+    g = torch.Generator(device=dev)
+    g.manual_seed(BATCH_SEED)
+    A = torch.randn((d, d), device=dev, dtype=torch.float32, generator=g)
+    ld = (d + 31) // 32 * 32
+    nq = (m + 3) // 4
+    P = torch.randn((nq, ld, 4), device=dev, dtype=torch.float32, generator=g)
+    P[:, d:, :] = 0
+    if m % 4:
+        P[-1, :, m % 4:] = 0
+    Y = torch.zeros_like(P)
+    G = torch.zeros((m, m), dtype=torch.float64, device=dev)
+    ctx = bk.Context(local)
+    stream = torch.cuda.Stream(dev)
+    ctx.set_stream(stream.cuda_stream)
+    op = bk.dense_operator(A)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            bk.block_apply(ctx, op, 0.0, P, Y, G, m, ld)
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            bk.block_apply(ctx, op, 0.0, P, Y, G, m, ld)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    gbs = 4.0 * d * d / (ms / 1e3) / 1e9
+    peak, src = measured_peaks()
+    if rank == 0:
+        print(json.dumps({"metric": "dense FP32 block product, GB/s of A per product", "value": gbs, "unit": "GB/s",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (3xTF32)",
+                          "data": "synthetic", "config": {"workload": f"dense_product_d{d}_m{m}"},
+                          "note": "each step is one bk_block_apply call (includes its host synchronisation)",
+                          "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                       "frac": gbs / peak, "traffic": None, "peak_source": src}}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_init()
@@ -342,6 +392,8 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     if args.workload == "batched":
         return run_batched(args, world, rank, local, dev)
+    if args.workload == "dense-product":
+        return run_dense_product(args, world, rank, local, dev)
 
     def barrier():
         if world > 1:

@@ -23,15 +23,26 @@ int sm_count_ops(int device) {
 }
 
 // ------------------------------------------------------------------ CSR
-// Thread per row. The row's nonzeros (up to KMAX, more are read in a tail loop) are
-// held in registers; the panels are walked one at a time, each step keeping nnz
-// independent 16-byte gathers in flight. Each panel row of the result goes to Y and,
-// as one 16-byte store, to the row-major shared tile used by the fused Gram.
+// Thread per row; the grid strides over row tiles, so for a stencil the tiles whose
+// rows a tile gathers are being read at the same time by other CTAs and are served
+// from L2. The row's nonzeros (up to KMAX, more are read in a tail loop) are held in
+// registers; the panels are walked QU at a time, and all loads of a group
+// (the row's own panel rows and nnz 16-byte gathers per panel) are issued before any
+// of them is used, so up to QU (KMAX + 1) loads per thread are in flight. Each panel
+// row of the result goes to Y and, as one 16-byte store, to the row-major shared tile
+// used by the fused Gram.
+template <int MP>
+__host__ __device__ constexpr int csr_group() { return (MP / 4) % 3 == 0 ? 3 : 2; }
+template <typename T, int MP>
+__host__ __device__ constexpr int csr_blocks() { return sizeof(T) == 4 ? 3 : 2; }
+
 template <typename T, int MP, int TM, int KMAX>
-__global__ void __launch_bounds__(TM, sizeof(T) == 4 ? 5 : 3)
+__global__ void __launch_bounds__(TM, (csr_blocks<T, MP>()))
     k_csr_spmm_gram(int64_t d, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                     const T* __restrict__ vals, T mu, const T* __restrict__ P, T* __restrict__ Y, int64_t ld, int m,
                     double* parts, int nparts, const DevState* state) {
+  constexpr int QU = csr_group<MP>();
+  constexpr int NQ = MP / 4;
   if (is_done(state)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sX = reinterpret_cast<T*>(smem_raw);
@@ -58,33 +69,55 @@ __global__ void __launch_bounds__(TM, sizeof(T) == 4 ? 5 : 3)
       off[k] = on ? colidx[k0 + k] : 0;
     }
 #pragma unroll 1
-    for (int q = 0; q < MP / 4; ++q) {
-      T a[4] = {0, 0, 0, 0}, pv[4] = {0, 0, 0, 0};
-      if (ok && q < nq) {
-        const T* pq = P + (int64_t)q * ld * 4;
-        ldg4(pq + i * 4, pv);
+    for (int q0 = 0; q0 < NQ; q0 += QU) {
+      T pv[QU][4], gv[QU][KMAX][4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = mu * pv[u];
+      for (int j = 0; j < QU; ++j) {  // every load of the group first
+        const int q = q0 + j;
+        const bool live = ok && q < NQ && q < nq;
+        const T* pq = P + (int64_t)(q < NQ ? q : 0) * ld * 4;
+        if (live)
+          ldg4(pq + i * 4, pv[j]);
+        else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) pv[j][u] = (T)0;
+        }
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-          if (k < nz) {
-            T gv[4];
-            ldg4(pq + (int64_t)off[k] * 4, gv);
+          if (live && k < nz)
+            ldg4(pq + (int64_t)off[k] * 4, gv[j][k]);
+          else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) a[u] = fma(v[k], gv[u], a[u]);
+            for (int u = 0; u < 4; ++u) gv[j][k][u] = (T)0;
           }
         }
-        for (int k = KMAX; k < nz; ++k) {
-          T gv[4];
-          ldg4(pq + (int64_t)colidx[k0 + k] * 4, gv);
-          const T vk = vals[k0 + k];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) a[u] = fma(vk, gv[u], a[u]);
-        }
-        st4(Y + ((int64_t)q * ld + i) * 4, a);
       }
-      store4<MP>(sX, t, q, pv);
-      store4<MP>(sY, t, q, a);
+#pragma unroll
+      for (int j = 0; j < QU; ++j) {
+        const int q = q0 + j;
+        if (q >= NQ) break;
+        const bool live = ok && q < nq;
+        T a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = mu * pv[j][u];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a[u] = fma(v[k], gv[j][k][u], a[u]);
+        if (live) {
+          const T* pq = P + (int64_t)q * ld * 4;
+          for (int k = KMAX; k < nz; ++k) {
+            T gt[4];
+            ldg4(pq + (int64_t)colidx[k0 + k] * 4, gt);
+            const T vk = vals[k0 + k];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = fma(vk, gt[u], a[u]);
+          }
+          st4(Y + ((int64_t)q * ld + i) * 4, a);
+        }
+        store4<MP>(sX, t, q, pv[j]);
+        store4<MP>(sY, t, q, a);
+      }
     }
     __syncthreads();
     g.tile(sX, sY, TM);
@@ -240,7 +273,7 @@ cudaError_t csr_impl(int64_t d, const int* rowptr, const int* colidx, const void
                      void* Y, int64_t ld, int m, double* parts, int nparts, const DevState* state, cudaStream_t st) {
   constexpr int TM = csr_tm<T, MP>();
   size_t smem = gram_smem_bytes<T, MP>(TM, TM);
-  auto kern = k_csr_spmm_gram<T, MP, TM, 8>;
+  auto kern = k_csr_spmm_gram<T, MP, TM, 7>;  // 7 nonzeros per row in registers (7-point stencils)
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<nparts, TM, smem, st>>>(d, rowptr, colidx, (const T*)vals, (T)mu, (const T*)P, (T*)Y, ld, m, parts, nparts,
@@ -307,7 +340,7 @@ cudaError_t dense_f(int64_t d, const void* A, int64_t lda, double mu, const void
 int csr_spmm_gram_grid(int is_f64, int mp, int64_t d, int device) {
   int tm = 128;
   int64_t ntiles = (d + tm - 1) / tm;
-  int cap = sm_count_ops(device) * (is_f64 ? 3 : 5);
+  int cap = sm_count_ops(device) * (is_f64 ? 2 : 3);  // resident CTAs per SM (launch bounds)
   if (ntiles < 1) ntiles = 1;
   return (int)(ntiles < cap ? ntiles : cap);
 }
