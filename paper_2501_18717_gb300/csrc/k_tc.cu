@@ -1,28 +1,28 @@
 // Tensor-core dense block product Y = A P + mu P with the fused Gram G = P^T Y, for
 // FP32 matrices (Sec. 1.2: the loads of A are the cost of the method). 5th-generation
 // tensor cores (tcgen05) with TF32 inputs and an FP32 accumulator in tensor memory;
-// FP32 accuracy is kept by splitting both operands into a TF32 head and an FP32 tail
-// and accumulating three products (A_hi P_hi + A_hi P_lo + A_lo P_hi; the dropped
-// A_lo P_lo is ~2^-26 relative).
+// FP32 accuracy is kept by splitting both operands into a TF32 head and a TF32 tail
+// (both rounded to nearest, tf32_split) and accumulating three products (A_hi P_hi +
+// A_hi P_lo + A_lo P_hi; the dropped A_lo P_lo is ~2^-24 relative).
 //
-// One CTA computes one 128-row tile of Y over all columns. A tiles land in a ring of
-// 5 stages that is refilled as soon as the split warps have read a tile; the P^T
-// slices have their own ring of 6 stages that the MMAs release, so neither load
-// stream waits on the MMAs of the stage it refills; the split head/tail tiles live
-// in 2 working stages that the MMAs read.
-//   warp 0      TMA producer for A (128 rows x 32 K, 128-byte swizzle);
+// One CTA computes one 128-row tile of Y over all columns, in pipeline steps of 64
+// columns of K (two 128-byte swizzle boxes). A tiles land in a ring of 4 stages that
+// is refilled as soon as the split warps have read a tile; the P^T slices have their
+// own ring of 3 stages that the MMAs release; the split head/tail of A lives in tensor
+// memory (two stages), which the MMAs read as their A operand.
+//   warp 0      TMA producer for A (128 rows x 32 K per box, 128-byte swizzle);
 //   warp 2      TMA producer for the P^T head and tail slices (adjacent rows, from L2);
 //   warp 1      allocates tensor memory and issues the MMAs into one of two
 //               accumulators: per 8-wide K step A_hi [P_hi; P_lo] (2N columns) and
-//               A_lo P_hi added to the first N columns; then commits to the working
-//               stage's "empty" and the accumulator's "full" barrier;
-//   warps 3-10  split each A tile into head and tail (elementwise, so the swizzled
-//               layout is kept), and drain the accumulator of the previous stage into
-//               FP32 registers: each tensor-memory lane quarter is read by two warps,
-//               one per half of the columns. The tensor core's FP32 accumulation does
-//               not round to nearest and its error grows with the number of
-//               accumulation steps; summing 32-wide K slices in registers keeps the
-//               product at FFMA accuracy.
+//               A_lo P_hi added to the first N columns; then commits to the A stage's
+//               "empty", the P^T stage's "empty" and the accumulator's "full" barrier;
+//   warps 3-10  read their rows of the swizzled A tile, split them into head and tail
+//               and store both into tensor memory; then drain the accumulator of the
+//               previous step into FP32 registers (each lane quarter is read by two
+//               warps, one per half of the columns). The tensor core's FP32
+//               accumulation does not round to nearest and its error grows with the
+//               number of accumulation steps; summing 64-wide K slices in registers
+//               keeps the product at FFMA accuracy.
 // The epilogue joins the column halves in shared memory, adds mu P, writes Y in the
 // panel layout and stages P and Y rows; all threads then form the per-CTA Gram
 // partial (bk_tile.cuh).
@@ -73,7 +73,20 @@ struct TcShape {
   static_assert(128 * (N + 1 + 2 * MP) * 4 <= kOffB, "epilogue staging fits in the A ring");
 };
 
-__device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// TF32 value nearest to x (round to nearest, ties away from zero).
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+// x = h + l + e with h, l exact TF32 values and |e| <= 2^-24 |x| (about FP32 rounding):
+// h is x rounded to TF32 (|x - h| <= 2^-12 |x|) and l is that difference rounded to
+// TF32. A truncated head leaves a 13-bit tail that the MMA would truncate again (error
+// up to 2^-22 |x|), which showed as more block-CG iterations.
+__device__ __forceinline__ void tf32_split(float x, float& h, float& l) {
+  h = tf32_rn(x);
+  l = tf32_rn(x - h);
+}
 
 // P (panels) -> P^T head and tail rows, zero beyond d and beyond m.
 template <int MP>
@@ -95,9 +108,10 @@ __global__ void k_pt_split(int64_t d, const float* __restrict__ P, int64_t ld, i
 #pragma unroll
     for (int c = 0; c < N; ++c) {
       const float x = (c < MP) ? v[c < MP ? c : 0] : 0.f;
-      const float h = tf32_head(x);
+      float h, l;
+      tf32_split(x, h, l);
       PT[(int64_t)c * ldk + k] = h;
-      PT[(int64_t)(N + c) * ldk + k] = x - h;
+      PT[(int64_t)(N + c) * ldk + k] = l;
     }
   }
 }
@@ -277,9 +291,10 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
             const float x[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const float h = tf32_head(x[u]);
+              float h, l;
+              tf32_split(x[u], h, l);
               hv[4 * j + u] = __float_as_uint(h);
-              lv[4 * j + u] = __float_as_uint(x[u] - h);
+              lv[4 * j + u] = __float_as_uint(l);
             }
           }
           tmem_st16(arow + 16u * g, hv);       // head
@@ -420,9 +435,10 @@ __global__ void k_bpt_split(const BSys* __restrict__ sys, const int* __restrict_
 #pragma unroll
     for (int c = 0; c < N; ++c) {
       const float x = (c < MP) ? v[c < MP ? c : 0] : 0.f;
-      const float h = tf32_head(x);
+      float h, l;
+      tf32_split(x, h, l);
       S.pt[(int64_t)c * ldk + k] = h;
-      S.pt[(int64_t)(N + c) * ldk + k] = x - h;
+      S.pt[(int64_t)(N + c) * ldk + k] = l;
     }
   }
 }
