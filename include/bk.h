@@ -215,11 +215,15 @@ bk_status bk_sample(bk_ctx* ctx, const bk_operator* K, double nugget, int32_t m,
 bk_status bk_solve_batched(bk_ctx* ctx, int32_t n, const bk_operator* A, const double* mu, const double* const* b,
                            double* const* x, const bk_opts* opts, bk_info* info);
 
-/* Chooses the sketch size per size bucket (floor(log2 d)) by timing bk_solve_batched on
- * each calibration system with each candidate sketch (one warm and one timed solve) and
- * keeping the fastest converged one; the table is stored in the context and used by
- * bk_solve_batched when opts->sketch = -1. Calibrate on systems drawn independently of
- * the ones to be solved. chosen (n ints, may be NULL) receives the pick per system. */
+/* Chooses the sketch size per size bucket (floor(log2 d)) from timed calibration
+ * solves and stores the table in the context; bk_solve_batched uses it when
+ * opts->sketch = -1. The calibration systems of each bucket are solved together with
+ * bk_solve_batched, repeated in one batch until it streams about 1 GB of matrix per
+ * block product (at most 64 copies), so the timing reflects throughput inside a large
+ * batch; each candidate is timed as the best of three solves after a warm one, and
+ * the fastest candidate that converges on every system wins. Calibrate on systems
+ * drawn independently of the ones to be solved. chosen (n ints, may be NULL) receives
+ * the pick per system. Host memory for the copies' x vectors is allocated here. */
 bk_status bk_autotune(bk_ctx* ctx, int32_t n, const bk_operator* A, const double* mu, const double* const* b,
                       const int32_t* candidates, int32_t ncand, const bk_opts* opts, int32_t* chosen);
 

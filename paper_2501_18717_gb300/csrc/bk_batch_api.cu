@@ -400,33 +400,62 @@ extern "C" bk_status bk_autotune(bk_ctx* c, int32_t n, const bk_operator* A, con
     opts = *opts_in;
   else
     bk_default_opts(&opts);
-  // total time per (size bucket, candidate) over the calibration systems of that bucket;
-  // a candidate that fails to converge on any of them is out for the bucket
-  std::map<int, std::vector<double>> tsum;
-  std::vector<double> xs;
+  // Per size bucket, the bucket's calibration systems are solved together as one batch,
+  // repeated until the batch streams at least kBatchBytes of matrix per load (up to
+  // kMaxCopies copies, each with its own x), so that the timing reflects the systems'
+  // cost inside a large batch rather than the per-step latency of a tiny one. Each
+  // candidate is timed three times after a warm solve (best of three); a candidate
+  // that leaves any system unconverged is out for the bucket.
+  constexpr double kBatchBytes = 1e9;
+  constexpr int kMaxCopies = 64;
+  std::map<int, std::vector<int>> buckets;
   for (int i = 0; i < n; ++i) {
-    xs.assign((size_t)A[i].rows, 0.0);
-    double* xp = xs.data();
-    std::vector<double>& t = tsum[size_bucket(A[i].rows)];
-    if (t.empty()) t.assign(ncand, 0.0);
+    if (A[i].rows < 1) return BK_ERR_ARG;
+    buckets[size_bucket(A[i].rows)].push_back(i);
+  }
+  for (int k = 0; k < ncand; ++k)
+    if (candidates[k] < 1) return BK_ERR_ARG;
+  for (auto& kv : buckets) {
+    const std::vector<int>& mem = kv.second;
+    double bytes = 0.0;
+    for (int i : mem) bytes += (double)A[i].rows * A[i].rows * (A[i].dtype == BK_F64 ? 8 : 4);
+    const int copies = (int)std::min<double>(kMaxCopies, std::max(1.0, std::ceil(kBatchBytes / bytes)));
+    std::vector<bk_operator> ops;
+    std::vector<double> mus;
+    std::vector<const double*> bs;
+    std::vector<std::vector<double>> xs;
+    for (int r = 0; r < copies; ++r)
+      for (int i : mem) {
+        ops.push_back(A[i]);
+        mus.push_back(mu[i]);
+        bs.push_back(b[i]);
+        xs.emplace_back((size_t)A[i].rows, 0.0);
+      }
+    std::vector<double*> xp(xs.size());
+    for (size_t q = 0; q < xs.size(); ++q) xp[q] = xs[q].data();
+    const int nb = (int)ops.size();
+    std::vector<bk_info> infos((size_t)nb);
+    double best_t = INFINITY;
+    int best_k = -1;
     for (int k = 0; k < ncand; ++k) {
-      if (candidates[k] < 1) return BK_ERR_ARG;
       bk_opts o = opts;
       o.sketch = candidates[k];
-      bk_info info;
-      // a warm solve, then the timed one
-      bk_status s = bk_solve_batched(c, 1, A + i, mu + i, b + i, &xp, &o, &info);
-      if (s != BK_OK && s != BK_NOT_CONVERGED) return s;
-      s = bk_solve_batched(c, 1, A + i, mu + i, b + i, &xp, &o, &info);
-      if (s != BK_OK && s != BK_NOT_CONVERGED) return s;
-      t[k] += (s == BK_OK) ? info.ms_total : INFINITY;
+      double t = INFINITY;
+      for (int rep = 0; rep < 4; ++rep) {  // a warm solve, then three timed ones
+        bk_status s = bk_solve_batched(c, nb, ops.data(), mus.data(), bs.data(), xp.data(), &o, infos.data());
+        if (s != BK_OK && s != BK_NOT_CONVERGED) return s;
+        if (s != BK_OK) {
+          t = INFINITY;
+          break;
+        }
+        if (rep > 0) t = std::min(t, (double)infos[0].ms_total);
+      }
+      if (t < best_t) {
+        best_t = t;
+        best_k = k;
+      }
     }
-  }
-  for (auto& kv : tsum) {
-    int kb = -1;
-    for (int k = 0; k < ncand; ++k)
-      if (std::isfinite(kv.second[k]) && (kb < 0 || kv.second[k] < kv.second[kb])) kb = k;
-    if (kb >= 0) c->tune[kv.first] = candidates[kb];
+    if (best_k >= 0) c->tune[kv.first] = candidates[best_k];
   }
   if (chosen)
     for (int i = 0; i < n; ++i) {
