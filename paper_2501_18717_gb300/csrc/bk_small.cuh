@@ -38,6 +38,19 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
   return r;
 }
 
+// 1/x for a pivot of the unit-diagonal scaled matrix (rank_tol < x, x about 1 or
+// smaller, well inside FP32 range): an FP32 reciprocal and two FP64 Newton steps,
+// rounding-level accurate. On this part a warp issues one FP64 instruction per 64
+// cycles; this chain is on the critical path of every column, so it is kept to four
+// fused multiply-adds (the square roots of the pivots are formed afterwards, off it).
+__device__ __forceinline__ double recip_pivot(double x) {
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 // Cholesky of the unit-diagonal scaled matrix in the given column order; a pivot at
 // or below rank_tol marks column k as numerically in the span of the kept columns
 // before it: its row and column are dropped (invd[k] = 0) and the factorisation
@@ -50,8 +63,7 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
 // on the kept columns, D = diag(dscale)^2.
 template <int NTH>
 __device__ int block_cholesky_skip(SmallShared& sh, int m, double rank_tol) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = NTH / 32;
+  const int tid = threadIdx.x;
   double* W = sh.W;
   __shared__ int s_bad, s_rank;
   if (tid == 0) {
@@ -75,31 +87,59 @@ __device__ int block_cholesky_skip(SmallShared& sh, int m, double rank_tol) {
     W[r * kLds + c] *= sh.z[r] * sh.z[c];
   }
   __syncthreads();
+  // Right-looking, one block barrier per column, on the pivots x_k themselves: the
+  // trailing update is W[i][j] -= W[i][k] W[j][k] / x_k, which needs only 1 / x_k; the
+  // square roots (L[k][k] and 1 / L[k][k]) and the scaling of the columns follow in
+  // one parallel pass at the end. The pivot thread (lane 0 of the last warp) updates
+  // the next diagonal entry and forms its reciprocal; the other pairs (i, j),
+  // k < j <= i, of the trailing triangle are spread evenly over the other threads, so
+  // the pivot chain does not wait on a warp that also carries update work.
+  constexpr int PW = NTH - 32;
+  auto pivot = [&](int k) {  // keep column k if its pivot is above rank_tol
+    const double x = W[k * kLds + k];
+    const bool keep = x > rank_tol;
+    sh.invd[k] = keep ? recip_pivot(x) : 0.0;  // 1 / x_k during the factorisation
+    sh.perm[k] = keep;
+    if (keep) s_rank += 1;
+  };
+  if (tid == PW) pivot(0);
+  __syncthreads();
   for (int k = 0; k < m; ++k) {
-    if (tid == 0) {
-      const double x = W[k * kLds + k];
-      const bool keep = x > rank_tol;
-      double r = 0.0;
-      if (keep) {
-        r = rsqrt_newton(x);
-        s_rank += 1;
-      }
-      W[k * kLds + k] = keep ? x * r : 0.0;
-      sh.invd[k] = r;
-      sh.perm[k] = keep;
-    }
-    __syncthreads();
-    const double inv = sh.invd[k];  // 0 drops the column: L[:,k] = 0, no trailing update
-    for (int i = k + 1 + tid; i < m; i += NTH) W[i * kLds + k] *= inv;
-    __syncthreads();
-    if (inv != 0.0) {
-      for (int i = k + 1 + warp; i < m; i += NW) {
-        const double lik = W[i * kLds + k];
-        for (int j = k + 1 + lane; j <= i; j += 32) W[i * kLds + j] = fma(-lik, W[j * kLds + k], W[i * kLds + j]);
+    const double rx = sh.invd[k];  // 0 drops the column: no trailing update
+    const int n = m - 1 - k;       // rows below k
+    if (n > 0) {
+      if (tid < PW) {
+        if (rx != 0.0) {
+          const int npairs = n * (n + 1) / 2 - 1;  // all but the diagonal (k+1, k+1)
+          for (int p = tid; p < npairs; p += PW) {
+            const int q = p + 1;  // index in the triangle, row-major: (r, c), c <= r
+            int r = (int)((sqrtf(8.f * q + 1.f) - 1.f) * 0.5f);
+            while ((r + 1) * (r + 2) / 2 <= q) ++r;
+            while (r * (r + 1) / 2 > q) --r;
+            const int i = k + 1 + r, j = k + 1 + (q - r * (r + 1) / 2);
+            W[i * kLds + j] = fma(-W[i * kLds + k] * rx, W[j * kLds + k], W[i * kLds + j]);
+          }
+        }
+      } else if (tid == PW) {
+        const int i = k + 1;
+        if (rx != 0.0) W[i * kLds + i] = fma(-W[i * kLds + k] * rx, W[i * kLds + k], W[i * kLds + i]);
+        pivot(i);
       }
     }
     __syncthreads();
   }
+  for (int k = tid; k < m; k += NTH) {  // L[k][k] = sqrt(x_k), invd[k] = 1 / L[k][k]
+    const double x = W[k * kLds + k];
+    const double r = sh.perm[k] ? rsqrt_newton(x) : 0.0;
+    W[k * kLds + k] = sh.perm[k] ? x * r : 0.0;
+    sh.invd[k] = r;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < m * m; idx += NTH) {  // L[i][k] = W[i][k] / L[k][k], i > k
+    const int i = idx / m, k = idx - i * m;
+    if (i > k) W[i * kLds + k] *= sh.invd[k];
+  }
+  __syncthreads();
   return s_rank;
 }
 
