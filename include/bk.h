@@ -59,8 +59,12 @@ typedef enum { BK_F64 = 0, BK_F32 = 1 } bk_dtype;
 
 /* Precision of the inner block-CG iteration (block vectors, block products,
  * updates). Gram matrices, the small Cholesky solves, the solution accumulator and
- * the refinement residual are FP64 in both modes. */
-typedef enum { BK_PREC_FP64 = 0, BK_PREC_FP32 = 1 } bk_prec;
+ * the refinement residual are FP64 in every mode.
+ *   BK_PREC_F32X2: FP64 blocks; block products of FP32-stored values (16-byte aligned
+ *   rows) in compensated FP32-pair arithmetic on the FP32 pipe (each product exact,
+ *   sums to about 2^-44 of sum |a_ik p_k|). Lanczos drivers only (bk_ridge_path,
+ *   bk_sample); bk_solve and bk_solve_batched return BK_ERR_UNSUPPORTED. */
+typedef enum { BK_PREC_FP64 = 0, BK_PREC_FP32 = 1, BK_PREC_F32X2 = 2 } bk_prec;
 
 /* The matrix A (without the shift mu).
  *   BK_DENSE: vals is rows x cols row-major with leading dimension ld, rows = cols = d.
@@ -105,6 +109,8 @@ enum {
   BK_K_UPDATE_R = 3,  /* R -= Y alpha with the Gram R^T R */
   BK_K_BETA = 4,      /* residual test and small solve beta = S^+ S' */
   BK_K_UPDATE_P = 5,  /* x += P alpha e_1, P = R + P beta */
+  BK_K_RESIDUAL = 6,  /* Lanczos drivers: FP64-accurate refinement residual products */
+  BK_K_ORTH = 7,      /* Lanczos drivers: reorthogonalisation, block QR and Grams */
   BK_K_CLASSES = 8
 };
 
@@ -192,7 +198,9 @@ bk_status bk_ridge_path(bk_ctx* ctx, const bk_operator* A, int32_t L, const doub
  *          positive definite and the interval starts at 1e-12 times its upper end)
  *   B      d x m column-major doubles (host or device), 1 <= m <= 256; S: d x m output
  *   n_quad quadrature nodes (1..1024; 32 gives about 1e-12 for a spectral ratio of 1e8)
- *   info   loads, refinements (= checks made), rel_residual (= last relative change) */
+ *   info   loads, refinements (= checks made), rel_residual (= last relative change)
+ * Returns BK_BREAKDOWN if a shifted projected system T_t + (nugget + z_j^2) I is not
+ * positive definite (K + nugget I indefinite in its stored precision). */
 bk_status bk_sample(bk_ctx* ctx, const bk_operator* K, double nugget, int32_t m, const double* B, double* S,
                     int32_t n_quad, const bk_opts* opts, bk_info* info);
 

@@ -142,6 +142,25 @@ cudaError_t launch_dense_to_f32(int64_t d, const double* in, int64_t lda, float*
 cudaError_t launch_gemm(int is_f64, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int a_f64,
                         int64_t sai, int64_t sak, const void* B, int64_t sbk, int64_t sbj, double beta, void* C,
                         int64_t ldc, cudaStream_t st);
+// Split-K form of launch_gemm for few output tiles and a long K (tall Gram products):
+// the K range is cut into chunks whose partial products go to `work` and are added in
+// chunk order in FP64. Falls back to launch_gemm when splitting does not pay or `work`
+// is too small (gemm_split_work_bytes gives the size it wants).
+cudaError_t launch_gemm_split(int is_f64, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int a_f64,
+                              int64_t sai, int64_t sak, const void* B, int64_t sbk, int64_t sbj, double beta, void* C,
+                              int64_t ldc, void* work, size_t work_bytes, int sms, cudaStream_t st);
+size_t gemm_split_work_bytes(int is_f64, int64_t M, int64_t N, int64_t K, int sms);
+// ---- tall-skinny products of the Lanczos drivers (k_tsm.cu)
+// df = 0: FP32 B / T and output; df = 1: FP64 B / T and output with compensated FP32
+// arithmetic (FP64-accurate for FP32 A / Z). A and Z must be 16-byte aligned with
+// leading dimensions a multiple of 4 floats (FP32 B / T likewise); tsm_supported checks.
+bool tsm_supported(const void* A, int64_t lda, const void* B, int64_t ldb, int b_f64);
+cudaError_t launch_tsm_nn(int df, int64_t M, int N, int64_t K, double alpha, const float* A, int64_t lda,
+                          const void* B, int64_t ldb, double beta, void* C, int64_t ldc, cudaStream_t st);
+cudaError_t launch_tsm_tn(int df, int64_t R, int64_t D, int N, const float* Z, int64_t ldz, const void* T,
+                          int64_t ldt, double alpha, double beta, void* Y, int64_t ldy, void* work, size_t work_bytes,
+                          int sms, cudaStream_t st);
+size_t tsm_tn_work_bytes(int64_t R, int64_t D, int N, int df, int sms);
 // ---- block-Lanczos drivers (k_krylov.cu)
 cudaError_t launch_e1r0(int n, int mb, const double* R0, double* rhs, cudaStream_t st);
 cudaError_t launch_chol_inv(int m, const double* G, double rank_tol, double* work, double* R, double* Rinv,

@@ -26,6 +26,47 @@ struct LzOp {
   int vals_f64 = 0;
 };
 
+// CUDA events around kernel groups of a profiled driver call (opts.profile): one pair
+// per group, summed per class (BK_K_*) once the call has finished.
+struct Prof {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  std::vector<cudaEvent_t> ev[BK_K_CLASSES];
+  cudaEvent_t open = nullptr;
+  void begin() {
+    if (!on) return;
+    cudaEventCreate(&open);
+    cudaEventRecord(open, st);
+  }
+  void end(int cls) {
+    if (!on || !open) return;
+    cudaEvent_t e1 = nullptr;
+    cudaEventCreate(&e1);
+    cudaEventRecord(e1, st);
+    ev[cls].push_back(open);
+    ev[cls].push_back(e1);
+    open = nullptr;
+  }
+  // after the stream has been synchronised
+  void report(bk_info* info) {
+    for (int k = 0; k < BK_K_CLASSES; ++k) {
+      double ms = 0.0;
+      for (size_t i = 0; i + 1 < ev[k].size(); i += 2) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, ev[k][i], ev[k][i + 1]) == cudaSuccess) ms += t;
+      }
+      if (info) {
+        info->ms_kernel[k] += ms;
+        info->launches[k] += (int)(ev[k].size() / 2);
+      }
+      for (cudaEvent_t e : ev[k]) cudaEventDestroy(e);
+      ev[k].clear();
+    }
+    if (open) cudaEventDestroy(open);
+    open = nullptr;
+  }
+};
+
 // Block-Lanczos with full reorthogonalisation (classical Gram-Schmidt twice against
 // every previous block) and CholQR2 for the block QR (Sec. 3.2, Thm. cost). Blocks are
 // column-major with leading dimension ldq, in the precision of the run (FP32 or FP64);
@@ -37,11 +78,13 @@ struct Lanczos {
   size_t es = 8;
   LzOp op;
   int m = 0, tmax = 0;
-  int64_t d = 0, ldq = 0, ncol_max = 0;
+  int64_t d = 0, ldq = 0, ncol_max = 0, ldv = 0;
   void *Q = nullptr, *W = nullptr, *V = nullptr, *C = nullptr, *Rt = nullptr;
   double *G = nullptr, *R1 = nullptr, *R2 = nullptr, *Ri1 = nullptr, *Ri2 = nullptr, *work = nullptr;
   double *Ak = nullptr, *Bk = nullptr, *R0 = nullptr, *band = nullptr;
   int *keep = nullptr, *rank = nullptr;
+  Prof* prof = nullptr;  // optional event timing
+  int df = 0;            // FP64 blocks: FP32 values through the compensated products
   int t = 0;      // blocks in T_t
   int loads = 0;  // operator applications
   double rank_tol = 1e-12;
@@ -65,8 +108,9 @@ struct Lanczos {
     cudaError_t e;
     if ((e = ws_get(c, WS_LQ, (size_t)ldq * ncol_max * es, &Q)) != cudaSuccess) return e;
     if ((e = ws_get(c, WS_LW, (size_t)ldq * m * es, &W)) != cudaSuccess) return e;
+    ldv = (op.nrows + 3) & ~int64_t(3);
     if (op.kind == BK_GRAM)
-      if ((e = ws_get(c, WS_LV, (size_t)op.nrows * m * es, &V)) != cudaSuccess) return e;
+      if ((e = ws_get(c, WS_LV, (size_t)ldv * m * es, &V)) != cudaSuccess) return e;
     if ((e = ws_get(c, WS_LC, (size_t)ncol_max * m * es, &C)) != cudaSuccess) return e;
     double* sm = nullptr;
     const size_t mm = (size_t)m * m;
@@ -90,19 +134,52 @@ struct Lanczos {
     return cudaSuccess;
   }
 
-  // Y (d x nc, ldy) = A X (d x nc, ldx), block precision.
+  // Y (d x nc, ldy) = A X (d x nc, ldx), block precision. FP32 runs use the tall-skinny
+  // product kernels (k_tsm.cu); FP64 runs the general GEMM.
   cudaError_t apply(const void* X, int64_t ldx, void* Y, int64_t ldy, int nc) {
     cudaError_t e;
     const int af = op.vals_f64;  // 1: FP64 values, 0: FP32 values
     if (!is64 && af) return cudaErrorInvalidValue;  // FP32 runs use FP32 values
+    if (is64 && df && !af && bk::tsm_supported(op.vals, op.ld, X, ldx, 1)) {
+      const float* A = (const float*)op.vals;
+      if (op.kind == BK_DENSE) return bk::launch_tsm_nn(1, d, nc, d, 1.0, A, op.ld, X, ldx, 0.0, Y, ldy, st);
+      if ((e = bk::launch_tsm_nn(1, op.nrows, nc, d, 1.0, A, op.ld, X, ldx, 0.0, V, ldv, st)) != cudaSuccess) return e;
+      void* wk = nullptr;
+      const size_t wb = bk::tsm_tn_work_bytes(op.nrows, d, nc, 1, c->sms);
+      if ((e = ws_get(c, WS_TSM, wb, &wk)) != cudaSuccess) return e;
+      return bk::launch_tsm_tn(1, op.nrows, d, nc, A, op.ld, V, ldv, 1.0, 0.0, Y, ldy, wk, wb, c->sms, st);
+    }
+    if (!is64 && bk::tsm_supported(op.vals, op.ld, X, ldx, 0)) {
+      const float* A = (const float*)op.vals;
+      if (op.kind == BK_DENSE) return bk::launch_tsm_nn(0, d, nc, d, 1.0, A, op.ld, X, ldx, 0.0, Y, ldy, st);
+      if ((e = bk::launch_tsm_nn(0, op.nrows, nc, d, 1.0, A, op.ld, X, ldx, 0.0, V, ldv, st)) != cudaSuccess) return e;
+      void* wk = nullptr;
+      const size_t wb = bk::tsm_tn_work_bytes(op.nrows, d, nc, 0, c->sms);
+      if ((e = ws_get(c, WS_TSM, wb, &wk)) != cudaSuccess) return e;
+      return bk::launch_tsm_tn(0, op.nrows, d, nc, A, op.ld, V, ldv, 1.0, 0.0, Y, ldy, wk, wb, c->sms, st);
+    }
     if (op.kind == BK_DENSE) {
       e = bk::launch_gemm(is64, d, nc, d, 1.0, op.vals, af, op.ld, 1, X, 1, ldx, 0.0, Y, ldy, st);
     } else {
-      e = bk::launch_gemm(is64, op.nrows, nc, d, 1.0, op.vals, af, op.ld, 1, X, 1, ldx, 0.0, V, op.nrows, st);
+      e = bk::launch_gemm(is64, op.nrows, nc, d, 1.0, op.vals, af, op.ld, 1, X, 1, ldx, 0.0, V, ldv, st);
       if (e != cudaSuccess) return e;
-      e = bk::launch_gemm(is64, d, nc, op.nrows, 1.0, op.vals, af, 1, op.ld, V, 1, op.nrows, 0.0, Y, ldy, st);
+      e = bk::launch_gemm(is64, d, nc, op.nrows, 1.0, op.vals, af, 1, op.ld, V, 1, ldv, 0.0, Y, ldy, st);
     }
     return e;
+  }
+
+  // Split-K general product for tall reductions (Grams, Q^T W): K = d is long and the
+  // output has few tiles.
+  cudaError_t gemm_k(int out64, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int a_f64, int64_t sai,
+                     int64_t sak, const void* B, int64_t sbk, int64_t sbj, double beta, void* C, int64_t ldc) {
+    const size_t wb = bk::gemm_split_work_bytes(out64, M, N, K, c->sms);
+    void* wk = nullptr;
+    if (wb) {
+      cudaError_t e = ws_get(c, WS_SPLIT, wb, &wk);
+      if (e != cudaSuccess) return e;
+    }
+    return bk::launch_gemm_split(out64, M, N, K, alpha, A, a_f64, sai, sak, B, sbk, sbj, beta, C, ldc, wk, wb, c->sms,
+                                 st);
   }
 
   // CholQR2: Wb (d x m) = Qout Bout, Bout upper triangular (m x m row-major FP64).
@@ -113,7 +190,7 @@ struct Lanczos {
       const void* src = pass == 0 ? Wb : Qout;
       double* R = pass == 0 ? R1 : R2;
       double* Ri = pass == 0 ? Ri1 : Ri2;
-      if ((e = bk::launch_gemm(1, m, m, d, 1.0, src, gaf, ldq, 1, src, 1, ldq, 0.0, G, m, st)) != cudaSuccess)
+      if ((e = gemm_k(1, m, m, d, 1.0, src, gaf, ldq, 1, src, 1, ldq, 0.0, G, m)) != cudaSuccess)
         return e;
       if ((e = bk::launch_chol_inv(m, G, rank_tol, work, R, Ri, keep, rank, st)) != cudaSuccess) return e;
       // Qout = src * Ri (Ri row-major: element (k, j) at Ri[k m + j])
@@ -139,20 +216,24 @@ struct Lanczos {
     cudaError_t e;
     const int k = t;
     const void* Qk = qblock(k);
+    if (prof) prof->begin();
     if ((e = apply(Qk, ldq, W, ldq, m)) != cudaSuccess) return e;
+    if (prof) prof->end(BK_K_OPERATOR);
     ++loads;
+    if (prof) prof->begin();
     // A_k = Q_k^T (A Q_k) with FP64 accumulation
     const int gaf = is64 ? 1 : 2;
-    if ((e = bk::launch_gemm(1, m, m, d, 1.0, Qk, gaf, ldq, 1, W, 1, ldq, 0.0, Ak, m, st)) != cudaSuccess) return e;
+    if ((e = gemm_k(1, m, m, d, 1.0, Qk, gaf, ldq, 1, W, 1, ldq, 0.0, Ak, m)) != cudaSuccess) return e;
     // full reorthogonalisation against Q_0..Q_k, twice
     const int64_t nk = (int64_t)(k + 1) * m;
     for (int pass = 0; pass < 2; ++pass) {
-      if ((e = bk::launch_gemm(is64, nk, m, d, 1.0, Q, is64, ldq, 1, W, 1, ldq, 0.0, C, nk, st)) != cudaSuccess)
+      if ((e = gemm_k(is64, nk, m, d, 1.0, Q, is64, ldq, 1, W, 1, ldq, 0.0, C, nk)) != cudaSuccess)
         return e;
-      if ((e = bk::launch_gemm(is64, d, m, nk, -1.0, Q, is64, 1, ldq, C, 1, nk, 1.0, W, ldq, st)) != cudaSuccess)
+      if ((e = gemm_k(is64, d, m, nk, -1.0, Q, is64, 1, ldq, C, 1, nk, 1.0, W, ldq)) != cudaSuccess)
         return e;
     }
     if ((e = qr(W, qblock(k + 1), Bk)) != cudaSuccess) return e;
+    if (prof) prof->end(BK_K_ORTH);
     if ((e = bk::launch_band_put(ldb(), m, m, k, Ak, Bk, band, st)) != cudaSuccess) return e;
     ++t;
     return cudaSuccess;
@@ -205,7 +286,21 @@ cudaError_t stage_lz_values(bk_ctx* c, const bk_operator* A, LzOp* o, int want_f
 }
 
 // FP64 products A X for L columns (refinement residuals): X, AX d x L column-major (ld).
-cudaError_t apply_fp64(bk_ctx* c, const LzOp& o, const double* X, int64_t ld, int L, double* AX, double* Vw) {
+// With allow_df, FP32 values go through the compensated tall-skinny products (about
+// 2^-44 relative to sum |a_ik x_k|, on the FP32 pipe); otherwise, and for FP64 values,
+// through the FP64 GEMM.
+cudaError_t apply_fp64(bk_ctx* c, const LzOp& o, const double* X, int64_t ld, int L, double* AX, double* Vw,
+                       bool allow_df) {
+  if (allow_df && !o.vals_f64 && bk::tsm_supported(o.vals, o.ld, X, ld, 1)) {
+    const float* A = (const float*)o.vals;
+    if (o.kind == BK_DENSE) return bk::launch_tsm_nn(1, o.d, L, o.d, 1.0, A, o.ld, X, ld, 0.0, AX, ld, c->stream);
+    cudaError_t e = bk::launch_tsm_nn(1, o.nrows, L, o.d, 1.0, A, o.ld, X, ld, 0.0, Vw, o.nrows, c->stream);
+    if (e != cudaSuccess) return e;
+    void* wk = nullptr;
+    const size_t wb = bk::tsm_tn_work_bytes(o.nrows, o.d, L, 1, c->sms);
+    if ((e = ws_get(c, WS_TSM, wb, &wk)) != cudaSuccess) return e;
+    return bk::launch_tsm_tn(1, o.nrows, o.d, L, A, o.ld, Vw, o.nrows, 1.0, 0.0, AX, ld, wk, wb, c->sms, c->stream);
+  }
   if (o.kind == BK_DENSE) return bk::launch_gemm(1, o.d, L, o.d, 1.0, o.vals, o.vals_f64, o.ld, 1, X, 1, ld, 0.0, AX,
                                                  ld, c->stream);
   cudaError_t e =
@@ -302,7 +397,8 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
   else
     bk_default_opts(&opts);
   if (!(opts.tol > 0.0) || opts.sketch < 0 || opts.max_loads < 1 || opts.max_refine < 1) return BK_ERR_ARG;
-  if (opts.inner != BK_PREC_FP64 && opts.inner != BK_PREC_FP32) return BK_ERR_UNSUPPORTED;
+  if (opts.inner != BK_PREC_FP64 && opts.inner != BK_PREC_FP32 && opts.inner != BK_PREC_F32X2)
+    return BK_ERR_UNSUPPORTED;
   std::vector<double> hmu(L);
   BK_CK(cudaSetDevice(c->device));
   cudaStream_t st = c->stream;
@@ -310,9 +406,12 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
   BK_CK(cudaMemcpy(hmu.data(), mus, (size_t)L * 8, cudaMemcpyDefault));
   for (double v : hmu)
     if (!(v >= 0.0) || !std::isfinite(v)) return BK_ERR_ARG;
-  const int is64 = opts.inner == BK_PREC_FP64;
+  const int is64 = opts.inner != BK_PREC_FP32;
   const int64_t d = o.d;
   const int m = (int)std::min<int64_t>((int64_t)opts.sketch + 1, d);
+  Prof prof;
+  prof.on = opts.profile != 0;
+  prof.st = st;
   if (m > 256) return BK_ERR_UNSUPPORTED;
   cudaEvent_t ev0, ev1;
   BK_CK(cudaEventCreate(&ev0));
@@ -352,6 +451,9 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
   int loads = 0, residual_loads = 0, refinements = 0;
   bk_status result = BK_NOT_CONVERGED;
   double worst = 1.0;
+  // compensated FP32 residual products allowed (not on the plain FP64 path) and still
+  // accurate enough
+  bool df_ok = opts.inner != BK_PREC_FP64;
   if (bnorm == 0.0) {
     result = BK_OK;
     worst = 0.0;
@@ -367,6 +469,8 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
     Lanczos lz;
     LzOp ol = o;
     BK_CK(lz.init(c, ol, is64, mb, tmax));
+    lz.prof = &prof;
+    lz.df = opts.inner == BK_PREC_F32X2;
     const size_t es = is64 ? 8 : 4;
     // start block into W (block precision), column scales applied in FP64 first
     double* B0d = nullptr;
@@ -419,16 +523,38 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
     loads += lz.loads;
     // X += Q_t Z (pass 0 scaled back by ||b||: the start column was b / ||b||)
     const int n = lz.n();
-    BK_CK(bk::launch_gemm(1, d, L, n, pass == 0 ? bnorm : 1.0, lz.Q, is64, 1, lz.ldq, Z, 1, n, 1.0, Xd, ldx, st));
+    BK_CK(lz.gemm_k(1, d, L, n, pass == 0 ? bnorm : 1.0, lz.Q, is64, 1, lz.ldq, Z, 1, n, 1.0, Xd, ldx));
     ++refinements;
-    // FP64 residuals of every shift
-    BK_CK(apply_fp64(c, o64, Xd, ldx, L, AX, Vw));
-    BK_CK(bk::launch_shift_residual(d, L, bd, AX, Xd, ldx, dmu, Rres, norms, st));
-    residual_loads += 1;
-    BK_CK(cudaMemcpyAsync(c->hparts, norms, (size_t)L * 8, cudaMemcpyDeviceToHost, st));
-    BK_CK(cudaStreamSynchronize(st));
-    worst = 0.0;
-    for (int j = 0; j < L; ++j) worst = std::max(worst, std::sqrt(c->hparts[j]) / bnorm);
+    // FP64 residuals of every shift. The compensated FP32 products carry about 44 bits:
+    // their error in b - A_mu x is about 1e-13 ||A|| ||X|| (cancellation when x is
+    // large). Use them only while that floor is below tol / 10 (||A|| <= the
+    // Gershgorin bound of T_t, ||X|| <= its Frobenius norm), and take the FP64 GEMM
+    // once a pass stops reducing the residual.
+    if (df_ok && !o64.vals_f64) {
+      double xn2 = 0.0;
+      const int npx = bk::residual_parts(d * L);
+      BK_CK(bk::launch_norm2_parts(d * L, Xd, normp, npx, st));
+      BK_CK(host_sum(c, normp, npx, &xn2));
+      BK_CK(bk::launch_band_gersh(n, mb, lz.band, lz.ldb(), norms, st));
+      BK_CK(cudaMemcpyAsync(c->hparts, norms, 8, cudaMemcpyDeviceToHost, st));
+      BK_CK(cudaStreamSynchronize(st));
+      if (1e-13 * c->hparts[0] * std::sqrt(xn2) > 0.1 * opts.tol * bnorm) df_ok = false;
+    }
+    const double prev_worst = worst;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      prof.begin();
+      BK_CK(apply_fp64(c, o64, Xd, ldx, L, AX, Vw, df_ok));
+      prof.end(BK_K_RESIDUAL);
+      BK_CK(bk::launch_shift_residual(d, L, bd, AX, Xd, ldx, dmu, Rres, norms, st));
+      residual_loads += 1;
+      BK_CK(cudaMemcpyAsync(c->hparts, norms, (size_t)L * 8, cudaMemcpyDeviceToHost, st));
+      BK_CK(cudaStreamSynchronize(st));
+      worst = 0.0;
+      for (int j = 0; j < L; ++j) worst = std::max(worst, std::sqrt(c->hparts[j]) / bnorm);
+      const bool stalled = pass > 0 && worst > 0.25 * prev_worst && worst > opts.tol;
+      if (!(df_ok && !o64.vals_f64 && stalled)) break;
+      df_ok = false;  // recompute this residual in FP64
+    }
     if (worst <= opts.tol) result = BK_OK;
     (void)es;
   }
@@ -447,6 +573,7 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
     info->rel_residual = worst;
     info->ms_total = ms;
   }
+  prof.report(info);
   return result;
 }
 
@@ -467,8 +594,9 @@ extern "C" bk_status bk_sample(bk_ctx* c, const bk_operator* Kop, double nugget,
   else
     bk_default_opts(&opts);
   if (!(opts.tol > 0.0) || opts.max_loads < 1 || opts.check_every < 1) return BK_ERR_ARG;
-  if (opts.inner != BK_PREC_FP64 && opts.inner != BK_PREC_FP32) return BK_ERR_UNSUPPORTED;
-  const int is64 = opts.inner == BK_PREC_FP64;
+  if (opts.inner != BK_PREC_FP64 && opts.inner != BK_PREC_FP32 && opts.inner != BK_PREC_F32X2)
+    return BK_ERR_UNSUPPORTED;
+  const int is64 = opts.inner != BK_PREC_FP32;
   const int64_t d = o.d;
   if (m > d) return BK_ERR_ARG;
   BK_CK(cudaSetDevice(c->device));
@@ -483,8 +611,13 @@ extern "C" bk_status bk_sample(bk_ctx* c, const bk_operator* Kop, double nugget,
   BK_CK(stage_in(c, WS_B64, B, (size_t)d * m * 8, (const void**)&Bd));
 
   const int tmax = (int)std::min<int64_t>((d + m - 1) / m + 1, opts.max_loads);
+  Prof prof;
+  prof.on = opts.profile != 0;
+  prof.st = st;
   Lanczos lz;
   BK_CK(lz.init(c, o, is64, m, tmax));
+  lz.prof = &prof;
+  lz.df = opts.inner == BK_PREC_F32X2;
   BK_CK(bk::launch_copy_cols(1, is64, d, m, Bd, d, lz.W, lz.ldq, st));
   BK_CK(lz.start(lz.W));
 
@@ -530,6 +663,19 @@ extern "C" bk_status bk_sample(bk_ctx* c, const bk_operator* Kop, double nugget,
     // Y_j = (T_K + (nugget + z_j^2) I)^{-1} E_1 R_0 for all j in one launch
     BK_CK(bk::launch_e1r0(n, m, lz.R0, rhs, st));
     BK_CK(bk::launch_band_solve(n, m, lz.band, lz.ldb(), N, dmu, rhs, rhs_col, m, bwork, Z, flags, st));
+    {
+      // a shifted T_t that is not positive definite (A indefinite in the stored
+      // precision) leaves that shift's solve unfinished: stop with BK_BREAKDOWN
+      int* hf = (int*)c->hparts;
+      BK_CK(cudaMemcpyAsync(hf, flags, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
+      BK_CK(cudaStreamSynchronize(st));
+      bool bad = false;
+      for (int j = 0; j < N; ++j) bad = bad || hf[j] != 0;
+      if (bad) {
+        result = BK_BREAKDOWN;
+        break;
+      }
+    }
     // Ybar = sum_j w_j Y_j; S = Q_t (T_t + nugget) Ybar + Q_{t+1} B_t E_t^T Ybar
     BK_CK(bk::launch_combine_shifts(n, m, N, Z, dw, Ybar, st));
     BK_CK(bk::launch_band_mult(n, m, lz.band, lz.ldb(), nugget, Ybar, m, M1, st));
@@ -574,5 +720,6 @@ extern "C" bk_status bk_sample(bk_ctx* c, const bk_operator* Kop, double nugget,
     info->rel_residual = change;
     info->ms_total = ms;
   }
+  prof.report(info);
   return result;
 }

@@ -12,6 +12,8 @@
 // 4 x 4 outputs each, accumulation in the element type of C (FP32 or FP64). A and B may
 // each be FP32 or FP64; the tile loader reads along whichever stride is unit so the
 // global loads coalesce.
+#include <algorithm>
+
 #include "bk_common.cuh"
 
 namespace bk {
@@ -22,7 +24,12 @@ constexpr int GBM = 64, GBN = 64, GBK = 16, GTH = 256;
 template <typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(GTH) k_gemm(int64_t M, int64_t N, int64_t K, TC alpha, const TA* __restrict__ A,
                                              int64_t sai, int64_t sak, const TB* __restrict__ B, int64_t sbk,
-                                             int64_t sbj, TC beta, TC* __restrict__ C, int64_t ldc) {
+                                             int64_t sbj, TC beta, TC* __restrict__ C, int64_t ldc,
+                                             int64_t kchunk, int64_t zstride) {
+  // split-K: CTA z covers k in [z kchunk, (z + 1) kchunk) and writes its own C + z zstride
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
+  C += (int64_t)blockIdx.z * zstride;
   __shared__ TC sA[GBK][GBM + 4];
   __shared__ TC sB[GBK][GBN + 4];
   const int tid = threadIdx.x;
@@ -35,7 +42,7 @@ __global__ void __launch_bounds__(GTH) k_gemm(int64_t M, int64_t N, int64_t K, T
     for (int b = 0; b < 4; ++b) acc[a][b] = (TC)0;
   const bool a_rows_fast = (sai == 1);  // consecutive i contiguous
   const bool b_rows_fast = (sbk == 1);  // consecutive k contiguous
-  for (int64_t k0 = 0; k0 < K; k0 += GBK) {
+  for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
     // A tile: GBM x GBK elements, 4 per thread
 #pragma unroll
     for (int e = 0; e < (GBM * GBK) / GTH; ++e) {
@@ -49,7 +56,7 @@ __global__ void __launch_bounds__(GTH) k_gemm(int64_t M, int64_t N, int64_t K, T
         ii = idx / GBK;
       }
       int64_t gi = i0 + ii, gk = k0 + kk;
-      sA[kk][ii] = (gi < M && gk < K) ? (TC)A[gi * sai + gk * sak] : (TC)0;
+      sA[kk][ii] = (gi < M && gk < kend) ? (TC)A[gi * sai + gk * sak] : (TC)0;
     }
 #pragma unroll
     for (int e = 0; e < (GBN * GBK) / GTH; ++e) {
@@ -63,7 +70,7 @@ __global__ void __launch_bounds__(GTH) k_gemm(int64_t M, int64_t N, int64_t K, T
         kk = idx / GBN;
       }
       int64_t gj = j0 + jj, gk = k0 + kk;
-      sB[kk][jj] = (gj < N && gk < K) ? (TC)B[gk * sbk + gj * sbj] : (TC)0;
+      sB[kk][jj] = (gj < N && gk < kend) ? (TC)B[gk * sbk + gj * sbj] : (TC)0;
     }
     __syncthreads();
 #pragma unroll
@@ -97,28 +104,91 @@ __global__ void __launch_bounds__(GTH) k_gemm(int64_t M, int64_t N, int64_t K, T
 
 }  // namespace
 
+namespace {
+
+cudaError_t gemm_grid(int is_f64, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int a_f64, int64_t sai,
+                      int64_t sak, const void* B, int64_t sbk, int64_t sbj, double beta, void* C, int64_t ldc,
+                      int64_t kchunk, int64_t zstride, int nz, cudaStream_t st) {
+  dim3 grid((unsigned)((M + GBM - 1) / GBM), (unsigned)((N + GBN - 1) / GBN), (unsigned)nz);
+  if (grid.y > 65535 || nz > 65535) return cudaErrorInvalidValue;
+  if (is_f64) {
+    if (a_f64 == 1)
+      k_gemm<double, double, double><<<grid, GTH, 0, st>>>(M, N, K, alpha, (const double*)A, sai, sak,
+                                                           (const double*)B, sbk, sbj, beta, (double*)C, ldc, kchunk,
+                                                           zstride);
+    else if (a_f64 == 0)
+      k_gemm<float, double, double><<<grid, GTH, 0, st>>>(M, N, K, alpha, (const float*)A, sai, sak,
+                                                          (const double*)B, sbk, sbj, beta, (double*)C, ldc, kchunk,
+                                                          zstride);
+    else  // a_f64 == 2: FP32 A and B, FP64 accumulation and output (exact products)
+      k_gemm<float, float, double><<<grid, GTH, 0, st>>>(M, N, K, alpha, (const float*)A, sai, sak,
+                                                         (const float*)B, sbk, sbj, beta, (double*)C, ldc, kchunk,
+                                                         zstride);
+  } else {
+    if (a_f64) return cudaErrorInvalidValue;
+    k_gemm<float, float, float><<<grid, GTH, 0, st>>>(M, N, K, (float)alpha, (const float*)A, sai, sak,
+                                                      (const float*)B, sbk, sbj, (float)beta, (float*)C, ldc, kchunk,
+                                                      zstride);
+  }
+  return cudaGetLastError();
+}
+
+// C (M x N, ldc) = sum_z Wz + beta C, Wz = W + z M N (M x N column-major, ld M); the
+// partials are added in z order in FP64.
+template <typename T>
+__global__ void k_gemm_reduce(int64_t M, int64_t N, int nz, const T* __restrict__ W, double beta, T* C, int64_t ldc) {
+  const int64_t total = M * N;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < nz; ++z) s += (double)W[(size_t)z * total + idx];
+    T* c = C + (idx % M) + (idx / M) * ldc;
+    *c = (T)(beta == 0.0 ? s : fma(beta, (double)*c, s));
+  }
+}
+
+}  // namespace
+
 cudaError_t launch_gemm(int is_f64, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int a_f64,
                         int64_t sai, int64_t sak, const void* B, int64_t sbk, int64_t sbj, double beta, void* C,
                         int64_t ldc, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((M + GBM - 1) / GBM), (unsigned)((N + GBN - 1) / GBN));
-  if (grid.y > 65535) return cudaErrorInvalidValue;
-  if (is_f64) {
-    if (a_f64 == 1)
-      k_gemm<double, double, double><<<grid, GTH, 0, st>>>(M, N, K, alpha, (const double*)A, sai, sak,
-                                                           (const double*)B, sbk, sbj, beta, (double*)C, ldc);
-    else if (a_f64 == 0)
-      k_gemm<float, double, double><<<grid, GTH, 0, st>>>(M, N, K, alpha, (const float*)A, sai, sak,
-                                                          (const double*)B, sbk, sbj, beta, (double*)C, ldc);
-    else  // a_f64 == 2: FP32 A and B, FP64 accumulation and output (exact products)
-      k_gemm<float, float, double><<<grid, GTH, 0, st>>>(M, N, K, alpha, (const float*)A, sai, sak,
-                                                         (const float*)B, sbk, sbj, beta, (double*)C, ldc);
-  } else {
-    if (a_f64) return cudaErrorInvalidValue;
-    k_gemm<float, float, float><<<grid, GTH, 0, st>>>(M, N, K, (float)alpha, (const float*)A, sai, sak,
-                                                      (const float*)B, sbk, sbj, (float)beta, (float*)C, ldc);
-  }
+  return gemm_grid(is_f64, M, N, K, alpha, A, a_f64, sai, sak, B, sbk, sbj, beta, C, ldc, K, 0, 1, st);
+}
+
+int gemm_split_count(int64_t M, int64_t N, int64_t K, int sms) {
+  const int64_t tiles = ((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN);
+  if (tiles >= sms || K < 8 * GBK * 4) return 1;
+  int64_t nz = (2LL * sms + tiles - 1) / tiles;
+  nz = std::min<int64_t>(nz, K / (8 * GBK));  // at least 8 slices of K per split
+  return (int)std::max<int64_t>(1, std::min<int64_t>(nz, 256));
+}
+
+cudaError_t launch_gemm_split(int is_f64, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int a_f64,
+                              int64_t sai, int64_t sak, const void* B, int64_t sbk, int64_t sbj, double beta, void* C,
+                              int64_t ldc, void* work, size_t work_bytes, int sms, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  const int nz = gemm_split_count(M, N, K, sms);
+  const size_t es = is_f64 ? 8 : 4;
+  if (nz <= 1 || !work || (size_t)nz * M * N * es > work_bytes)
+    return gemm_grid(is_f64, M, N, K, alpha, A, a_f64, sai, sak, B, sbk, sbj, beta, C, ldc, K, 0, 1, st);
+  int64_t kchunk = (K + nz - 1) / nz;
+  kchunk = (kchunk + GBK - 1) / GBK * GBK;
+  const int nzz = (int)((K + kchunk - 1) / kchunk);
+  cudaError_t e = gemm_grid(is_f64, M, N, K, alpha, A, a_f64, sai, sak, B, sbk, sbj, 0.0, work, M, kchunk, M * N,
+                            nzz, st);
+  if (e != cudaSuccess) return e;
+  const int rb = (int)std::min<int64_t>((M * N + 255) / 256, 4LL * sms);
+  if (is_f64)
+    k_gemm_reduce<double><<<rb, 256, 0, st>>>(M, N, nzz, (const double*)work, beta, (double*)C, ldc);
+  else
+    k_gemm_reduce<float><<<rb, 256, 0, st>>>(M, N, nzz, (const float*)work, beta, (float*)C, ldc);
   return cudaGetLastError();
+}
+
+size_t gemm_split_work_bytes(int is_f64, int64_t M, int64_t N, int64_t K, int sms) {
+  const int nz = gemm_split_count(M, N, K, sms);
+  return nz <= 1 ? 0 : (size_t)nz * M * N * (is_f64 ? 8 : 4);
 }
 
 }  // namespace bk

@@ -232,6 +232,43 @@ def ridge_workload(seed: int, n: int, d: int, noise_std: float, dtype=np.float32
     return Z, f, b
 
 
+def ridge_workload_torch(seed: int, n: int, d: int, noise_std: float, device, chunk: int = 1 << 14):
+    """ridge_workload's construction on a CUDA device, for sizes the host cannot build
+    quickly: Z = H_16 ... H_1 [diag(1/i) V^T; 0] with the same reflector vectors (with
+    noise_std = 0 it is ridge_workload's Z up to the FP32 rounding of the construction),
+    stored in FP32 row-major. The noise N(0, noise_std^2) and f ~ N(0, I_n) come from
+    torch's CUDA generator seeded with `seed` (the host Philox stream would take
+    minutes at 8e8 entries). b = Z^T f in FP64 from the stored Z.
+    Returns (Z, f, b) as device tensors."""
+    import torch
+    V = torch.eye(d, dtype=torch.float64, device=device)
+    for r in range(16):
+        v = torch.from_numpy(normals(seed, STREAM_FACTORS, d, offset=16 * n + r * d)).to(device)
+        v /= torch.linalg.norm(v)
+        V -= 2.0 * torch.outer(v, v @ V)
+    sig = 1.0 / torch.arange(1, d + 1, dtype=torch.float64, device=device)
+    Z = torch.zeros((n, d), dtype=torch.float32, device=device)
+    Z[:d] = (sig[:, None] * V.T).to(torch.float32)
+    del V
+    for r in range(16):
+        u = torch.from_numpy(normals(seed, STREAM_FACTORS, n, offset=r * n)).to(device)
+        u = (u / torch.linalg.norm(u)).to(torch.float32)
+        w = u @ Z
+        Z.addr_(u, w, alpha=-2.0)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    if noise_std > 0:
+        for s in range(0, n, chunk):
+            e = min(n, s + chunk)
+            Z[s:e] += noise_std * torch.randn((e - s, d), generator=g, device=device, dtype=torch.float32)
+    f = torch.randn(n, generator=g, device=device, dtype=torch.float64)
+    b = torch.zeros(d, dtype=torch.float64, device=device)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        b += Z[s:e].to(torch.float64).T @ f[s:e]
+    return Z, f, b
+
+
 # --------------------------------------------------------------------------------------
 # Gaussian sampling: RBF kernel on uniform points in [0, 1]^3.
 # --------------------------------------------------------------------------------------
@@ -249,6 +286,21 @@ def rbf_kernel(points: np.ndarray, lengthscale: float = 0.2, dtype=np.float64, c
         d2 = sq[s:e, None] + sq[None, :] - 2.0 * points[s:e] @ points.T
         np.maximum(d2, 0.0, out=d2)
         K[s:e] = np.exp(-d2 / (2.0 * lengthscale ** 2)).astype(dtype)
+    return K
+
+
+def rbf_kernel_torch(points: np.ndarray, device, lengthscale: float = 0.2, chunk: int = 4096):
+    """rbf_kernel on a CUDA device: FP64 arithmetic in row chunks, stored in FP32."""
+    import torch
+    x = torch.from_numpy(np.asarray(points, dtype=np.float64)).to(device)
+    n = x.shape[0]
+    K = torch.empty((n, n), dtype=torch.float32, device=device)
+    sq = (x * x).sum(1)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        d2 = sq[s:e, None] + sq[None, :] - 2.0 * (x[s:e] @ x.T)
+        d2.clamp_(min=0.0)
+        K[s:e] = torch.exp(-d2 / (2.0 * lengthscale ** 2)).to(torch.float32)
     return K
 
 

@@ -66,18 +66,49 @@ def test_ridge_dense_path(bk, ctx, inner):
     np.testing.assert_allclose(X, direct.ridge_path(aa, mus, b), rtol=0, atol=1e-4 * np.abs(X).max())
 
 
-@pytest.mark.parametrize("inner", ["fp64", "fp32"])
+@pytest.mark.parametrize("inner", ["fp64", "fp32", "f32x2"])
 def test_ridge_gram_path(bk, ctx, inner):
     """A = Z^T Z matrix-free (two products over Z per load), FP32 Z."""
     n, d, l = 3000, 256, 16
     Z, f, b = W.ridge_workload(W.BASE_SEED + 22, n, d, noise_std=1e-3)
     mus = np.logspace(-6, 0, 20)
-    tol = 1e-10 if inner == "fp64" else 1e-8
+    tol = 1e-8 if inner == "fp32" else 1e-10
     X = np.zeros((d, len(mus)), order="F")
     info = bk.ridge_path(ctx, bk.gram_operator(torch.from_numpy(Z).to(dev())), mus, b, X,
                          bk.default_opts(tol=tol, sketch=l, seed=6, inner=inner,
-                                         inner_tol=1e-6 if inner == "fp64" else 1e-5))
+                                         inner_tol=1e-5 if inner == "fp32" else 1e-6))
     op = operators.Gram(Z.astype(np.float64))
     res = shift_residuals(op, mus, X, b)
     assert res.max() <= tol, (res.max(), info.as_dict())
     assert info.loads <= 40 * info.refinements
+
+
+@pytest.mark.parametrize("d", [300, 257])
+def test_ridge_gram_tiles_and_ragged_edges(bk, ctx, d):
+    """Block width 65 (sketch 64) over ragged row and column tiles. d = 300 runs the
+    tall-skinny product kernels (FP32 loads, compensated FP64-accurate residuals) with a
+    partial last tile in both dimensions; d = 257 has rows that are not 16-byte aligned
+    and takes the general GEMM. Both must meet 1e-8 in the oracle's FP64 residual."""
+    n = 5003
+    Z, f, b = W.ridge_workload(W.BASE_SEED + 23, n, d, noise_std=1e-3)
+    mus = np.logspace(-6, 0, 20)
+    X = np.zeros((d, len(mus)), order="F")
+    info = bk.ridge_path(ctx, bk.gram_operator(torch.from_numpy(Z).to(dev())), mus, b, X,
+                         bk.default_opts(tol=1e-8, sketch=64, seed=7, inner="fp32", inner_tol=1e-5, check_every=2))
+    op = operators.Gram(Z.astype(np.float64))
+    res = shift_residuals(op, mus, X, b)
+    assert res.max() <= 1e-8, (res.max(), info.as_dict())
+    ref = direct.ridge_path(op.matrix(), mus, b)
+    np.testing.assert_allclose(X, ref, rtol=0, atol=1e-6 * np.abs(ref).max())
+
+
+def test_ridge_generator_matches_host_construction():
+    """The device generator of the full-size ridge inputs builds the same Z as the
+    host generator (noise off): same reflectors, same singular values."""
+    n, d = 3000, 96
+    Zh, _, _ = W.ridge_workload(W.BASE_SEED + 24, n, d, noise_std=0.0)
+    Zd, f, b = W.ridge_workload_torch(W.BASE_SEED + 24, n, d, 0.0, dev())
+    Zd = Zd.cpu().numpy()
+    assert np.max(np.abs(Zd - Zh)) <= 1e-6 * np.max(np.abs(Zh))
+    np.testing.assert_allclose(b.cpu().numpy(), Zd.astype(np.float64).T @ f.cpu().numpy(), rtol=1e-12,
+                               atol=1e-12 * np.abs(b.cpu().numpy()).max())

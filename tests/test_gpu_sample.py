@@ -57,3 +57,28 @@ def test_sample_converges_to_sqrt(bk, ctx, inner):
     lam = np.linalg.eigvalsh(K.astype(np.float64)) + nug
     tol = 1e-8 if inner == "fp64" else 20 * 2.0 ** -24 * np.sqrt(lam[-1] / lam[0])
     assert err <= tol, (err, tol, info.as_dict())
+
+
+@pytest.mark.parametrize("inner", ["fp64", "f32x2"])
+def test_sample_rbf_subset_validation(bk, ctx, inner):
+    """The sampling configuration's validation problem: the first 2000 of the seeded
+    uniform points, K stored in FP32 (lengthscale 0.2), nugget 1e-6 as the shift, 256
+    samples, 32 nodes; against the oracle's eigendecomposition of the stored K
+    promoted to FP64. At this size the FP32 rounding of K (norm 4e-7) stays below the
+    nugget, so K32 + 1e-6 I is positive definite (smallest eigenvalue 6.6e-7)."""
+    d, m = 2000, 256
+    pts = W.rbf_points(W.BASE_SEED + 4, 40000)[:d]
+    K = W.rbf_kernel(pts, dtype=np.float32)
+    B = W.sample_block(W.BASE_SEED + 4, 40000, m)[:d].copy(order="F")
+    S = np.zeros((d, m), order="F")
+    info = bk.sample(ctx, bk.dense_operator(torch.from_numpy(K).to("cuda:0")), 1e-6, B, S, 32,
+                     bk.default_opts(tol=1e-10, inner=inner, check_every=2, max_loads=64), check=False)
+    ref = direct.sqrtm_apply(K.astype(np.float64), B, shift=1e-6)
+    err = np.linalg.norm(S - ref) / np.linalg.norm(ref)
+    # K_t spans R^2000 after 8 loads, so only quadrature and rounding remain. An FP32
+    # basis cannot resolve this spectrum (u ||K|| = 1e-5 exceeds the nugget: the shifted
+    # projected systems become indefinite), hence FP64 blocks with FP64 or compensated
+    # FP32-pair products (about 2^-44 relative, 1e-11 absolute here).
+    assert info.status == bk.BK_OK, info.as_dict()
+    tol = 1e-8 if inner == "fp64" else 1e-7
+    assert err <= tol, (err, tol, info.as_dict())
