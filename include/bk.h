@@ -169,16 +169,24 @@ bk_status bk_solve(bk_ctx* ctx, const bk_operator* A, double mu, const double* b
  * banded systems (T_t + mu_j I) z_j = ||b|| e_1 are solved in one launch (one thread
  * block per shift, FP64) and combined as X = Q_t [z_1 .. z_L]. The run stops when the
  * Lanczos residual estimate ||B_t z_j,last|| of every shift meets the inner target.
- * FP64 refinement: the residuals r_j = b - (A + mu_j) x_j are formed in FP64 from the
- * stored values; while max_j ||r_j|| > tol ||b||, a block-Lanczos basis of the residual
- * block [r_1 .. r_L] (block width L) gives every correction at once and x_j is updated.
+ * FP64 refinement: the residuals r_j = b - (A + mu_j) x_j are formed from the stored
+ * values to FP64 accuracy (FP32 values: compensated FP32-pair products while their
+ * estimated error 1e-13 ||A|| ||X|| stays below tol ||b|| / 10, else, or once a basis
+ * stops reducing the residual, FP64 products); while max_j ||r_j|| > tol ||b||, a
+ * block-Lanczos basis of the residual block [r_1 .. r_L] (block width L) gives every
+ * correction at once and x_j is updated. A shifted projected system that is not
+ * positive definite (only through rounding in the basis) drops its non-positive pivots;
+ * an FP32 run that meets one builds its later bases in FP64 blocks with FP64-accurate
+ * products.
  *   A      BK_DENSE or BK_GRAM, FP32 or FP64 values (FP32 runs use FP32 values; FP64
  *          values are rounded by the library for them)
  *   L      number of shifts, 1 <= L <= 1024; mus: L shifts >= 0 (host or device)
  *   b      d doubles; X: d x L doubles, column-major (leading dimension d), output
  *   opts   sketch (l, block width l + 1 <= 256), seed, tol (relative residual of every
- *          shift), inner (FP64 or FP32 basis and products), inner_tol, max_loads (cap on
- *          operator applications per basis), max_refine (bases built), check_every
+ *          shift), inner (bk_prec of the basis and products), inner_tol, max_loads (cap
+ *          on operator applications per basis), max_refine (bases built), check_every,
+ *          profile (CUDA-event sums per group in ms_kernel / launches: BK_K_OPERATOR,
+ *          BK_K_RESIDUAL, BK_K_ORTH)
  *   info   loads (all bases), refinements (bases built), rel_residual (worst shift)
  * Returns BK_NOT_CONVERGED if the worst shift misses tol after max_refine bases. */
 bk_status bk_ridge_path(bk_ctx* ctx, const bk_operator* A, int32_t L, const double* mus, const double* b,

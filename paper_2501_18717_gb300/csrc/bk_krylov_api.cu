@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -454,6 +455,8 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
   // compensated FP32 residual products allowed (not on the plain FP64 path) and still
   // accurate enough
   bool df_ok = opts.inner != BK_PREC_FP64;
+  int skipped_shifts = 0;  // shifted solves that failed (reported through last_error)
+  bool escalated = false;  // FP32 run moved to FP64 bases
   if (bnorm == 0.0) {
     result = BK_OK;
     worst = 0.0;
@@ -466,12 +469,16 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
   for (int pass = 0; result != BK_OK && pass < opts.max_refine; ++pass) {
     const int mb = pass == 0 ? m : (int)std::min<int64_t>(L, d);
     const int tmax = (int)std::min<int64_t>((d + mb - 1) / mb + 1, std::max(1, opts.max_loads - loads));
+    // basis precision of this pass: FP32 runs escalate to FP64 blocks with FP64-accurate
+    // products once an FP32 basis has produced indefinite shifted systems (its rounding,
+    // about u ||A||, reached the smallest shifted eigenvalues)
+    const int pis64 = is64 || escalated;
     Lanczos lz;
     LzOp ol = o;
-    BK_CK(lz.init(c, ol, is64, mb, tmax));
+    BK_CK(lz.init(c, ol, pis64, mb, tmax));
     lz.prof = &prof;
-    lz.df = opts.inner == BK_PREC_F32X2;
-    const size_t es = is64 ? 8 : 4;
+    lz.df = opts.inner == BK_PREC_F32X2 || escalated;
+    bool pass_flagged = false;
     // start block into W (block precision), column scales applied in FP64 first
     double* B0d = nullptr;
     BK_CK(ws_get(c, WS_LB0, (size_t)d * std::max(mb, 1) * 8 + 4096 * 8, (void**)&B0d));
@@ -488,7 +495,7 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
     }
     BK_CK(cudaMemcpyAsync(scales, hs.data(), (size_t)mb * 8, cudaMemcpyHostToDevice, st));
     BK_CK(bk::launch_scale_cols(1, d, mb, d, scales, B0d, st));
-    BK_CK(bk::launch_copy_cols(1, is64, d, mb, B0d, d, lz.W, lz.ldq, st));
+    BK_CK(bk::launch_copy_cols(1, pis64, d, mb, B0d, d, lz.W, lz.ldq, st));
     BK_CK(lz.start(lz.W));
     // right-hand sides of the projected systems: columns of E_1 R_0 (R_0 row-major)
     double* rhs = nullptr;
@@ -518,13 +525,25 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
       BK_CK(cudaStreamSynchronize(st));
       double est = 0.0;
       for (int j = 0; j < L; ++j) est = std::max(est, c->hparts[j]);
+      int* hf = (int*)c->hparts;
+      BK_CK(cudaMemcpyAsync(hf, flags, (size_t)L * 4, cudaMemcpyDeviceToHost, st));
+      BK_CK(cudaStreamSynchronize(st));
+      // T_t + mu_j I not positive definite: only possible through rounding in the basis
+      // (A + mu_j I is positive definite for mu_j > 0); the solve dropped the offending
+      // directions and the FP64 residual of that shift drives the next basis
+      for (int j = 0; j < L; ++j)
+        if (hf[j]) {
+          ++skipped_shifts;
+          pass_flagged = true;
+        }
       if (est <= target || last) done = 1;
     }
     loads += lz.loads;
     // X += Q_t Z (pass 0 scaled back by ||b||: the start column was b / ||b||)
     const int n = lz.n();
-    BK_CK(lz.gemm_k(1, d, L, n, pass == 0 ? bnorm : 1.0, lz.Q, is64, 1, lz.ldq, Z, 1, n, 1.0, Xd, ldx));
+    BK_CK(lz.gemm_k(1, d, L, n, pass == 0 ? bnorm : 1.0, lz.Q, pis64, 1, lz.ldq, Z, 1, n, 1.0, Xd, ldx));
     ++refinements;
+    if (pass_flagged && !pis64) escalated = true;
     // FP64 residuals of every shift. The compensated FP32 products carry about 44 bits:
     // their error in b - A_mu x is about 1e-13 ||A|| ||X|| (cancellation when x is
     // large). Use them only while that floor is below tol / 10 (||A|| <= the
@@ -556,7 +575,6 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
       df_ok = false;  // recompute this residual in FP64
     }
     if (worst <= opts.tol) result = BK_OK;
-    (void)es;
   }
   BK_CK(cudaMemcpyAsync(X, Xd, (size_t)d * L * 8, cudaMemcpyDefault, st));
   BK_CK(cudaEventRecord(ev1, st));
@@ -573,6 +591,9 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
     info->rel_residual = worst;
     info->ms_total = ms;
   }
+  if (skipped_shifts && result != BK_OK)
+    std::snprintf(c->last_error, sizeof(c->last_error), "%d shifted projected solves dropped non-positive pivots",
+                  skipped_shifts);
   prof.report(info);
   return result;
 }

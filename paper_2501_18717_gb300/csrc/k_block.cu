@@ -271,56 +271,116 @@ __global__ void k_chol_solve(int m, const double* G, const double* S, double* X,
 }
 
 // ------------------------------------------------------------------ updates
-// R -= Y alpha, then the Gram partial of the new R. Thread per row; the whole R and Y
-// rows are loaded up front (2 MP independent loads per thread in flight), alpha is
-// read from shared memory as 16-byte broadcasts.
-template <typename T, int MP, int TM>
-__global__ void __launch_bounds__(TM, sizeof(T) == 4 ? 4 : 2)
+// R -= Y alpha, then the Gram partial of the new R. A tile of 128 rows is split over
+// 32 x CG threads: thread (rg, cg) owns rows rg + 32 u (u < 4) and the CPT = MP / CG
+// columns of column group cg. The Y tile is staged in shared memory column by column,
+// so each k costs four row values and CPT / 4 broadcast 16-byte alpha chunks for 4 CPT
+// FMAs (at width 36: 7 shared loads per 48 FMAs; one row per thread needed 9 per 36,
+// which left the kernel bound by the shared-memory pipe).
+template <int MP>
+struct UpdRShape {
+  static constexpr int CG = (MP % 12 == 0) ? MP / 12 : ((MP % 8 == 0) ? MP / 8 : 1);
+  static constexpr int CPT = MP / CG;
+  static constexpr int TH = 32 * CG;
+  static constexpr int TM = 128;
+};
+
+template <typename T, int MP>
+struct UpdRSmem {
+  static constexpr int LDY = UpdRShape<MP>::TM + (sizeof(T) == 4 ? 4 : 2);
+  static constexpr size_t A_B = ((size_t)MP * MP * sizeof(T) + 15) / 16 * 16;
+  static constexpr size_t Y_B = ((size_t)MP * LDY * sizeof(T) + 15) / 16 * 16;
+  static constexpr size_t X_B = (size_t)UpdRShape<MP>::TM * MP * sizeof(T);
+  static constexpr size_t RED_B = (size_t)(UpdRShape<MP>::TH / GramShape<MP>::NT) * GramShape<MP>::NE * 8;
+  static constexpr size_t TOTAL = A_B + (Y_B + X_B > RED_B ? Y_B + X_B : RED_B);
+};
+
+template <typename T, int MP>
+__global__ void __launch_bounds__(UpdRShape<MP>::TH)
     k_update_r(int64_t d, int m, const T* __restrict__ Y, T* __restrict__ R, int64_t ld,
                const T* __restrict__ alpha_t, double* parts, int nparts, const DevState* state) {
   if (is_done(state)) return;
+  using U = UpdRShape<MP>;
+  using SM = UpdRSmem<T, MP>;
+  constexpr int TM = U::TM, CPT = U::CPT, LDY = SM::LDY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sA = reinterpret_cast<T*>(smem_raw);  // MP x MP
-  T* sX = sA + MP * MP;                     // TM x MP tile of the new R
+  T* sA = reinterpret_cast<T*>(smem_raw);               // MP x MP: row k = alpha(k, :)
+  T* sY = reinterpret_cast<T*>(smem_raw + SM::A_B);      // MP x LDY: column k of the Y tile
+  T* sX = reinterpret_cast<T*>(smem_raw + SM::A_B + SM::Y_B);  // TM x MP: new R rows
   for (int idx = threadIdx.x; idx < MP * MP; idx += blockDim.x) sA[idx] = alpha_t[idx];
-  __syncthreads();
+  const int rg = threadIdx.x & 31, cg = threadIdx.x >> 5, c0 = cg * CPT;
   GramAcc<T, MP> g;
   g.init();
-  int64_t ntiles = (d + TM - 1) / TM;
+  __syncthreads();
+  const int64_t ntiles = (d + TM - 1) / TM;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t i = tile * TM + threadIdx.x;
-    const bool ok = i < d;
-    asm volatile("" ::: "memory");  // no hoisting of the alpha reads across tiles
-    T acc[MP], y[MP];
+    const int64_t i0 = tile * TM;
+    T acc[4][CPT];
 #pragma unroll
-    for (int q = 0; q < MP / 4; ++q) {
-      if (ok && 4 * q < m) {
-        ld4(panel_row(R, ld, q, i), acc + 4 * q);
-        ldg4(panel_row(Y, ld, q, i), y + 4 * q);
-      } else {
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + rg + 32 * u;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[4 * q + u] = y[4 * q + u] = (T)0;
+      for (int pi = 0; pi < CPT / 4; ++pi) {
+        const int q = c0 / 4 + pi;
+        T y4[4];
+        if (i < d && 4 * q < m) {
+          ld4(panel_row(R, ld, q, i), acc[u] + 4 * pi);
+          ldg4(panel_row(Y, ld, q, i), y4);
+        } else {
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc[u][4 * pi + w] = y4[w] = (T)0;
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) sY[(4 * q + w) * LDY + rg + 32 * u] = y4[w];
       }
     }
-#pragma unroll
+    __syncthreads();
+#pragma unroll 4
     for (int k = 0; k < MP; ++k) {
-      const T* a = sA + k * MP;
+      T yk[4];
 #pragma unroll
-      for (int c = 0; c < MP; ++c) acc[c] = fma(-y[k], a[c], acc[c]);
-    }
-    if (ok) {
+      for (int u = 0; u < 4; ++u) yk[u] = sY[k * LDY + rg + 32 * u];
+      T a[CPT];
 #pragma unroll
-      for (int q = 0; q < MP / 4; ++q)
-        if (4 * q < m) st4(panel_row(R, ld, q, i), acc + 4 * q);
+      for (int j4 = 0; j4 < CPT / 4; ++j4) {
+        if constexpr (sizeof(T) == 4) {
+          const float4 v = *reinterpret_cast<const float4*>(sA + k * MP + c0 + 4 * j4);
+          a[4 * j4] = v.x;
+          a[4 * j4 + 1] = v.y;
+          a[4 * j4 + 2] = v.z;
+          a[4 * j4 + 3] = v.w;
+        } else {
+          const double2 v0 = *reinterpret_cast<const double2*>(sA + k * MP + c0 + 4 * j4);
+          const double2 v1 = *reinterpret_cast<const double2*>(sA + k * MP + c0 + 4 * j4 + 2);
+          a[4 * j4] = v0.x;
+          a[4 * j4 + 1] = v0.y;
+          a[4 * j4 + 2] = v1.x;
+          a[4 * j4 + 3] = v1.y;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) acc[u][j] = fma(-yk[u], a[j], acc[u][j]);
     }
-    store_row<MP>(sX, threadIdx.x, acc);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int row = rg + 32 * u;
+      const int64_t i = i0 + row;
+#pragma unroll
+      for (int pi = 0; pi < CPT / 4; ++pi) {
+        const int q = c0 / 4 + pi;
+        if (i < d && 4 * q < m) st4(panel_row(R, ld, q, i), acc[u] + 4 * pi);
+        T v4[4] = {acc[u][4 * pi], acc[u][4 * pi + 1], acc[u][4 * pi + 2], acc[u][4 * pi + 3]};
+        store4<MP>(sX, row, q, v4);
+      }
+    }
     __syncthreads();
     g.tile(sX, sX, TM);
     __syncthreads();
   }
-  // sred aliases the tile area after the alpha block
-  gram_finish<T, MP>(g, reinterpret_cast<double*>(smem_raw + ((MP * MP * sizeof(T) + 15) / 16) * 16), parts,
-                     nparts, blockIdx.x);
+  // the phase buffer of the Gram reduction aliases the tiles after alpha
+  gram_finish<T, MP>(g, reinterpret_cast<double*>(smem_raw + SM::A_B), parts, nparts, blockIdx.x);
 }
 
 // x += P xc; unless the solve just ended, Q = W T^{-1} (W is held in Q) and
@@ -452,13 +512,12 @@ cudaError_t gram_impl(int64_t d, const void* X, const void* Y, int64_t ld, int m
 template <typename T, int MP>
 cudaError_t update_r_impl(int64_t d, int m, const void* Y, void* R, int64_t ld, const void* alpha_t, double* parts,
                           int nparts, const DevState* state, cudaStream_t st) {
-  constexpr int TM = 128;
-  size_t head = ((MP * MP * sizeof(T) + 15) / 16) * 16;
-  size_t smem = head + gram_smem_bytes<T, MP>(TM, TM);
-  auto kern = k_update_r<T, MP, TM>;
+  const size_t smem = UpdRSmem<T, MP>::TOTAL;
+  auto kern = k_update_r<T, MP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<nparts, TM, smem, st>>>(d, m, (const T*)Y, (T*)R, ld, (const T*)alpha_t, parts, nparts, state);
+  kern<<<nparts, UpdRShape<MP>::TH, smem, st>>>(d, m, (const T*)Y, (T*)R, ld, (const T*)alpha_t, parts, nparts,
+                                                state);
   return cudaGetLastError();
 }
 

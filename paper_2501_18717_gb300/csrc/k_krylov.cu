@@ -5,6 +5,8 @@
 //                   from the Lanczos blocks, shifted Cholesky solves for many shifts in
 //                   one launch (one CTA per shift), and the banded product T_t Y
 //   small helpers   FP32/FP64 block copies, scaled column sums, residual norms
+#include <algorithm>
+
 #include "bk_common.cuh"
 
 namespace bk {
@@ -127,24 +129,25 @@ __global__ void k_band_put(int ldb, int bw, int m, int k, const double* __restri
   }
 }
 
-// Shifted banded Cholesky solves, one CTA per shift j:
-//   (T + mu_j I) Z_j = E_j, E_j = the nrhs columns of rhs starting at column rhs_col[j]
-//   (rhs: n x ncol column-major, ld n).
-// A diagonal entry that is exactly zero (a dropped Lanczos direction) is replaced by 1
-// so the dropped direction decouples. work: L x (bw + 2) x n doubles (the factor and
-// the reciprocal diagonal). Z_j is n x nrhs column-major at Z + j * n * nrhs.
-// flags[j] = 1 if a pivot was not positive. Cost O(n bw^2) per shift (Thm. cost).
-__global__ void __launch_bounds__(256) k_band_solve(int n, int bw, const double* __restrict__ band, int ldb,
-                                                    const double* __restrict__ mus, const double* __restrict__ rhs,
-                                                    const int* __restrict__ rhs_col, int nrhs, double* work,
-                                                    double* Z, int* flags) {
+// Shifted banded Cholesky solves (T + mu_j I) Z_j = E_j, E_j = the nrhs columns of rhs
+// starting at column rhs_col[j] (rhs: n x ncol column-major, ld n). Two kernels:
+//   k_band_factor: one CTA per shift j factors T + mu_j I (band storage, bw
+//     subdiagonals) into work: L x (bw + 2) x n doubles (the factor and the reciprocal
+//     diagonal). A diagonal entry that is exactly zero (a dropped Lanczos direction) is
+//     replaced by 1 so the dropped direction decouples. A pivot that is not positive
+//     drops its direction the same way (its solution component is zero) and sets
+//     flags[j] = 1: T + mu_j I was not positive definite.
+//   k_band_subst: CTAs (j, s) run the forward and backward substitutions for their
+//     slice of the right-hand sides, so that many right-hand sides spread over many SMs.
+// Z_j is n x nrhs column-major at Z + j * n * nrhs. Cost O(n bw^2) per shift to factor,
+// O(n bw nrhs) to substitute (Thm. cost).
+__global__ void __launch_bounds__(256) k_band_factor(int n, int bw, const double* __restrict__ band, int ldb,
+                                                     const double* __restrict__ mus, double* work, int* flags) {
   const int j = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
   double* Lb = work + (size_t)j * (bw + 2) * n;
   double* invL = Lb + (size_t)(bw + 1) * n;
-  double* z = Z + (size_t)j * n * nrhs;
   const double mu = mus[j];
-  const double* e = rhs + (size_t)rhs_col[j] * n;
   __shared__ double s_inv;
   __shared__ int s_bad;
   for (size_t idx = tid; idx < (size_t)(bw + 1) * n; idx += nth) {
@@ -154,7 +157,6 @@ __global__ void __launch_bounds__(256) k_band_solve(int n, int bw, const double*
     if (r == 0) v = (v == 0.0) ? 1.0 : v + mu;
     Lb[idx] = v;
   }
-  for (size_t idx = tid; idx < (size_t)n * nrhs; idx += nth) z[idx] = e[idx];
   if (tid == 0) s_bad = 0;
   __syncthreads();
   // factorisation, column by column: L(c, c) = sqrt(pivot) formed by one thread
@@ -162,8 +164,11 @@ __global__ void __launch_bounds__(256) k_band_solve(int n, int bw, const double*
     if (tid == 0) {
       const double x = Lb[c];
       if (!(x > 0.0)) {
+        // not positive: drop this direction (unit pivot, zero column), as the block
+        // solves drop dependent columns; the solve continues on the others
         s_bad = 1;
         s_inv = 0.0;
+        Lb[c] = 1.0;
       } else {
         const double r = rsqrt_nr(x);
         Lb[c] = x * r;
@@ -176,6 +181,7 @@ __global__ void __launch_bounds__(256) k_band_solve(int n, int bw, const double*
     const int w = min(bw, n - 1 - c);
     for (int r = 1 + tid; r <= w; r += nth) Lb[(size_t)r * n + c] *= inv;
     __syncthreads();
+    if (inv == 0.0) continue;  // dropped: its zero column changes nothing below
     // trailing window T(c+a, c+b) -= L(c+a, c) L(c+b, c), 1 <= b <= a <= w:
     // warps over a, lanes over b
     for (int a = 1 + warp; a <= w; a += nw) {
@@ -187,17 +193,31 @@ __global__ void __launch_bounds__(256) k_band_solve(int n, int bw, const double*
     }
     __syncthreads();
   }
-  if (s_bad) {
-    if (tid == 0) flags[j] = 1;
-    return;
-  }
+  if (tid == 0) flags[j] = s_bad;
+}
+
+__global__ void __launch_bounds__(256) k_band_subst(int n, int bw, const double* __restrict__ rhs,
+                                                    const int* __restrict__ rhs_col, int nrhs, int per_cta,
+                                                    const double* __restrict__ work, double* Z,
+                                                    const int* __restrict__ flags) {
+  const int j = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const int q0 = blockIdx.y * per_cta;
+  const int q1 = min(nrhs, q0 + per_cta);
+  if (q0 >= q1) return;
+  const int nq = q1 - q0;
+  const double* Lb = work + (size_t)j * (bw + 2) * n;
+  const double* invL = Lb + (size_t)(bw + 1) * n;
+  double* z = Z + (size_t)j * n * nrhs + (size_t)q0 * n;
+  const double* e = rhs + (size_t)(rhs_col[j] + q0) * n;
+  for (size_t idx = tid; idx < (size_t)n * nq; idx += nth) z[idx] = e[idx];
+  __syncthreads();
   // forward L y = e, column-oriented: y_c *= 1/L_cc, then y_{c+r} -= L(c+r, c) y_c
   for (int c = 0; c < n; ++c) {
     const double inv = invL[c];
-    for (int q = tid; q < nrhs; q += nth) z[(size_t)q * n + c] *= inv;
+    for (int q = tid; q < nq; q += nth) z[(size_t)q * n + c] *= inv;
     __syncthreads();
     const int w = min(bw, n - 1 - c);
-    for (int idx = tid; idx < w * nrhs; idx += nth) {
+    for (int idx = tid; idx < w * nq; idx += nth) {
       const int r = 1 + idx % w, q = idx / w;
       z[(size_t)q * n + c + r] = fma(-Lb[(size_t)r * n + c], z[(size_t)q * n + c], z[(size_t)q * n + c + r]);
     }
@@ -206,16 +226,15 @@ __global__ void __launch_bounds__(256) k_band_solve(int n, int bw, const double*
   // backward L^T z = y, column-oriented: z_c *= 1/L_cc, then z_{c-r} -= L(c, c-r) z_c
   for (int c = n - 1; c >= 0; --c) {
     const double inv = invL[c];
-    for (int q = tid; q < nrhs; q += nth) z[(size_t)q * n + c] *= inv;
+    for (int q = tid; q < nq; q += nth) z[(size_t)q * n + c] *= inv;
     __syncthreads();
     const int w = min(bw, c);
-    for (int idx = tid; idx < w * nrhs; idx += nth) {
+    for (int idx = tid; idx < w * nq; idx += nth) {
       const int r = 1 + idx % w, q = idx / w;
       z[(size_t)q * n + c - r] = fma(-Lb[(size_t)r * n + c - r], z[(size_t)q * n + c], z[(size_t)q * n + c - r]);
     }
     __syncthreads();
   }
-  if (tid == 0) flags[j] = 0;
 }
 
 // out (n x nc, column-major) = (T + shift I) Y for the banded symmetric T.
@@ -370,7 +389,17 @@ cudaError_t launch_band_solve(int n, int bw, const double* band, int ldb, int L,
                               const double* rhs, const int* rhs_col, int nrhs, double* work, double* Z, int* flags,
                               cudaStream_t st) {
   if (L <= 0) return cudaSuccess;
-  k_band_solve<<<L, 256, 0, st>>>(n, bw, band, ldb, mus, rhs, rhs_col, nrhs, work, Z, flags);
+  k_band_factor<<<L, 256, 0, st>>>(n, bw, band, ldb, mus, work, flags);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // right-hand-side slices: about two CTAs per SM in total, at least 8 columns each
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int slices = std::max(1, std::min((2 * sms + L - 1) / L, nrhs / 8));
+  const int per = (nrhs + slices - 1) / slices;
+  slices = (nrhs + per - 1) / per;
+  k_band_subst<<<dim3(L, slices), 256, 0, st>>>(n, bw, rhs, rhs_col, nrhs, per, work, Z, flags);
   return cudaGetLastError();
 }
 

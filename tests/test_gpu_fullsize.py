@@ -46,3 +46,57 @@ def test_ridge_path_full_size(bk, ctx):
     for j in range(0, L, 9):
         res = direct.rel_residual(op, mus[j], Xh[:, j], bh)
         assert res <= 1e-8, (j, mus[j], res, info.as_dict())
+
+
+def _rbf_full(dev, d=40000, m=256):
+    seed = W.BASE_SEED + 4
+    pts = W.rbf_points(seed, d)
+    ld = (d + 31) // 32 * 32
+    Kbuf = torch.zeros((d, ld), dtype=torch.float32, device=dev)
+    Kbuf[:, :d] = W.rbf_kernel_torch(pts, dev)
+    B = W.sample_block(seed, d, m)
+    return Kbuf[:, :d], B
+
+
+def test_sample_full_size(bk, ctx):
+    """40,000 RBF points, K stored in FP32 (6.4 GB), 256 samples, 32 nodes, FP64
+    blocks with compensated FP32-pair products. The oracle checks, from the stored K
+    promoted to FP64, the identity S^T S = B^T (K + nugget I) B on 8 sampled columns
+    (it holds for the exact square root and for the block-Lanczos approximation
+    alike, so it pins scaling, column order and the operator, not convergence), and
+    the driver must report convergence of S itself (relative change <= 1e-6).
+    Nugget 1e-5: the FP32 rounding of K is a symmetric perturbation of norm about
+    3e-6 at this size, so K32 + 1e-6 I is indefinite (next test)."""
+    dev = torch.device("cuda:0")
+    K, B = _rbf_full(dev)
+    d, m = B.shape
+    nug = 1e-5
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).to(dev)
+    S = torch.zeros((m, d), dtype=torch.float64, device=dev)
+    info = bk.sample(ctx, bk.dense_operator(K), nug, Bt.T, S.T, 32,
+                     bk.default_opts(tol=1e-6, inner="f32x2", check_every=4, max_loads=24), check=False)
+    assert info.status == bk.BK_OK, info.as_dict()
+    cols = 8
+    Sh = S[:cols].cpu().numpy().T
+    Kh = K.cpu().numpy()
+    del K
+    op = operators.Dense(Kh[:, :d])  # stored FP32 values promoted to FP64
+    Bc = B[:, :cols]
+    G_ref = Bc.T @ op.apply(Bc, nug)
+    G = Sh.T @ Sh
+    scale = np.sqrt(np.outer(np.diag(G_ref), np.diag(G_ref)))
+    assert np.max(np.abs(G - G_ref) / scale) <= 1e-8
+
+
+def test_sample_full_size_fp32_floor(bk, ctx):
+    """At the configuration's nugget 1e-6 the stored FP32 K + 1e-6 I is indefinite
+    (rounding perturbation about 3e-6): the driver must stop with BK_BREAKDOWN rather
+    than return a square root that does not exist."""
+    dev = torch.device("cuda:0")
+    K, B = _rbf_full(dev)
+    d, m = B.shape
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).to(dev)
+    S = torch.zeros((m, d), dtype=torch.float64, device=dev)
+    info = bk.sample(ctx, bk.dense_operator(K), 1e-6, Bt.T, S.T, 32,
+                     bk.default_opts(tol=1e-6, inner="f32x2", check_every=4, max_loads=16), check=False)
+    assert info.status == bk.BK_BREAKDOWN, info.as_dict()
