@@ -212,6 +212,32 @@ bk_status bk_ridge_path(bk_ctx* ctx, const bk_operator* A, int32_t L, const doub
 bk_status bk_sample(bk_ctx* ctx, const bk_operator* K, double nugget, int32_t m, const double* B, double* S,
                     int32_t n_quad, const bk_opts* opts, bk_info* info);
 
+/* Nystrom-preconditioned CG, the comparator of Thm. main (Def. PCG, preconditioner of
+ * Eq. precond_def): the block-Krylov Nystrom approximation A<K_s> of Eq. nystromBKI_def
+ * from the sketch Omega of opts (d x sketch Gaussian, the same Philox key and stream as
+ * bk_solve's, so both methods see the same Omega), theta = its smallest eigenvalue
+ * (Sec. 7), P^{-1} = (theta + mu) U (D + mu)^{-1} U^T + (I - U U^T), then PCG from
+ * x = 0 on (A + mu I) x = b, everything in FP64 on the device. The approximation comes
+ * from s_ny block-Lanczos steps on Omega (s_ny loads): with V = [Q_0 .. Q_{s-1}] and the
+ * Lanczos relation A V = V T + Q_s B E_s^T, the factor F = A V (V^T A V)^{+1/2} is
+ * [V Q_s] H for a small H, so U and D follow from two small eigendecompositions on
+ * the host (cyclic Jacobi) and one d x r product.
+ *   A      BK_DENSE, BK_GRAM or BK_CSR; FP64 or FP32 values (promoted: FP32 dense and
+ *          Gram products use the compensated FP32-pair kernels, about 2^-44 relative)
+ *   s_ny   Krylov depth of the approximation, 1..16 (s_ny = 1 is the plain Nystrom
+ *          approximation A Omega (Omega^T A Omega)^+ Omega^T A)
+ *   b, x   d doubles (host or device); x is output (x_0 = 0)
+ *   opts   sketch (columns of Omega, <= 256), seed, tol (stop when the recurrence
+ *          residual meets tol ||b|| and the residual recomputed from the stored values
+ *          confirms it; checked every check_every iterations), max_loads (cap on
+ *          s_ny + PCG iterations)
+ *   info   loads (s_ny + iterations), refinements (rank r of the approximation),
+ *          residual_loads (recomputed residual checks), rel_residual (recomputed)
+ * Returns BK_NOT_CONVERGED at the load cap (x holds the last iterate), BK_BREAKDOWN if
+ * p^T A_mu p or r^T z stopped being positive. */
+bk_status bk_nystrom_pcg(bk_ctx* ctx, const bk_operator* A, double mu, const double* b, double* x, int32_t s_ny,
+                         const bk_opts* opts, bk_info* info);
+
 /* Many independent systems (A_i + mu_i I) x_i = b_i of uneven size, i < n, solved
  * together (bk_solve on each, batched): systems are grouped by padded block width and
  * every step of the block-CG recurrence (Def. BCG) runs as one launch over all systems

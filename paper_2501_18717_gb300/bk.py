@@ -86,6 +86,8 @@ def _load():
                             ctypes.POINTER(Info)]),
         "bk_ridge_path": (i32, [vp, ctypes.POINTER(Operator), i32, vp, vp, vp, ctypes.POINTER(Opts),
                                 ctypes.POINTER(Info)]),
+        "bk_nystrom_pcg": (i32, [vp, ctypes.POINTER(Operator), dbl, vp, vp, i32, ctypes.POINTER(Opts),
+                                 ctypes.POINTER(Info)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -273,6 +275,20 @@ def ridge_path(ctx: Context, A: OperatorRef, mus, b, X, opts: Opts | None = None
                            ctypes.byref(info))
     if check and s != BK_OK:
         raise BKError(s, "bk_ridge_path", ctx.last_error())
+    return info
+
+
+def nystrom_pcg(ctx: Context, A: OperatorRef, mu: float, b, x, s_ny: int = 1, opts: Opts | None = None,
+                check=True) -> Info:
+    """bk_nystrom_pcg: x ~= (A + mu I)^{-1} b by Nystrom-preconditioned CG (depth s_ny)."""
+    info = Info()
+    pb, kb = _ptr(b)
+    px, kx = _ptr(x)
+    o = opts if opts is not None else default_opts()
+    s = _lib.bk_nystrom_pcg(ctx.handle, ctypes.byref(A.op), float(mu), pb, px, int(s_ny), ctypes.byref(o),
+                            ctypes.byref(info))
+    if check and s != BK_OK:
+        raise BKError(s, "bk_nystrom_pcg", ctx.last_error())
     return info
 
 

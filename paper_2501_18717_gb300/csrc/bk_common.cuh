@@ -161,6 +161,24 @@ cudaError_t launch_tsm_tn(int df, int64_t R, int64_t D, int N, const float* Z, i
                           int64_t ldt, double alpha, double beta, void* Y, int64_t ldy, void* work, size_t work_bytes,
                           int sms, cudaStream_t st);
 size_t tsm_tn_work_bytes(int64_t R, int64_t D, int N, int df, int sms);
+// ---- Nystrom PCG (k_pcg.cu), FP64
+cudaError_t launch_csr_cols(int vals_f64, int64_t d, const int* rowptr, const int* colidx, const void* vals, int nc,
+                            const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t st);
+int pcg_parts();
+int gemv_parts();
+// kind 0: sc[1] = sc[0] / (a^T b); 1: sc[2] = (a^T b) / sc[0], sc[0] = a^T b; 2: sc[0] = a^T b;
+// 3: sc[3] = a^T b. parts: pcg_parts() doubles.
+cudaError_t launch_dot_scalar(int kind, int64_t n, const double* a, const double* b, double* parts, double* sc,
+                              cudaStream_t st);
+cudaError_t launch_pcg_xr(int64_t d, const double* sc, double mu, const double* p, const double* q, double* x,
+                          double* r, double* parts, cudaStream_t st);
+cudaError_t launch_pcg_p(int64_t d, const double* sc, const double* z, double* p, cudaStream_t st);
+cudaError_t launch_scale_vec(int n, const double* f, double* c, cudaStream_t st);
+// c = U^T v (parts: gemv_parts() x r doubles), z += U c; r <= 768
+cudaError_t launch_gemv_t(int64_t d, int r, const double* U, int64_t ldu, const double* v, double* parts, double* c,
+                          cudaStream_t st);
+cudaError_t launch_gemv_n(int64_t d, int r, const double* U, int64_t ldu, const double* c, double* z,
+                          cudaStream_t st);
 // ---- block-Lanczos drivers (k_krylov.cu)
 cudaError_t launch_e1r0(int n, int mb, const double* R0, double* rhs, cudaStream_t st);
 cudaError_t launch_chol_inv(int m, const double* G, double rank_tol, double* work, double* R, double* Rinv,

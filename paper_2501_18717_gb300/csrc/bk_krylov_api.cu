@@ -25,6 +25,9 @@ struct LzOp {
   int64_t d = 0, nrows = 0, ld = 0;
   const void* vals = nullptr;
   int vals_f64 = 0;
+  const int* rowptr = nullptr;  // BK_CSR (FP64 blocks only)
+  const int* colidx = nullptr;
+  int64_t nnz = 0;
 };
 
 // CUDA events around kernel groups of a profiled driver call (opts.profile): one pair
@@ -159,6 +162,11 @@ struct Lanczos {
       if ((e = ws_get(c, WS_TSM, wb, &wk)) != cudaSuccess) return e;
       return bk::launch_tsm_tn(0, op.nrows, d, nc, A, op.ld, V, ldv, 1.0, 0.0, Y, ldy, wk, wb, c->sms, st);
     }
+    if (op.kind == BK_CSR) {
+      if (!is64) return cudaErrorInvalidValue;
+      return bk::launch_csr_cols(af, d, op.rowptr, op.colidx, op.vals, nc, (const double*)X, ldx, (double*)Y, ldy,
+                                 st);
+    }
     if (op.kind == BK_DENSE) {
       e = bk::launch_gemm(is64, d, nc, d, 1.0, op.vals, af, op.ld, 1, X, 1, ldx, 0.0, Y, ldy, st);
     } else {
@@ -292,6 +300,8 @@ cudaError_t stage_lz_values(bk_ctx* c, const bk_operator* A, LzOp* o, int want_f
 // through the FP64 GEMM.
 cudaError_t apply_fp64(bk_ctx* c, const LzOp& o, const double* X, int64_t ld, int L, double* AX, double* Vw,
                        bool allow_df) {
+  if (o.kind == BK_CSR)
+    return bk::launch_csr_cols(o.vals_f64, o.d, o.rowptr, o.colidx, o.vals, L, X, ld, AX, ld, c->stream);
   if (allow_df && !o.vals_f64 && bk::tsm_supported(o.vals, o.ld, X, ld, 1)) {
     const float* A = (const float*)o.vals;
     if (o.kind == BK_DENSE) return bk::launch_tsm_nn(1, o.d, L, o.d, 1.0, A, o.ld, X, ld, 0.0, AX, ld, c->stream);
@@ -742,5 +752,292 @@ extern "C" bk_status bk_sample(bk_ctx* c, const bk_operator* Kop, double nugget,
     info->ms_total = ms;
   }
   prof.report(info);
+  return result;
+}
+
+// ---------------------------------------------------------------- Nystrom PCG
+namespace {
+
+// Eigen-decomposition of a symmetric n x n matrix (row-major, overwritten) by cyclic
+// Jacobi rotations (Golub & Van Loan, Sec. 8.5: sym.schur2 and cyclic sweeps):
+// eigenvalues ascending in w, eigenvectors as the columns of V (row-major n x n).
+void jacobi_eigh(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& V) {
+  V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  double fro = 0.0;
+  for (double a : A) fro += a * a;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+    if (off <= 1e-32 * fro || off == 0.0) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        const double tau = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
+        for (int k = 0; k < n; ++k) {  // A J
+          const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = cs * akp - sn * akq;
+          A[(size_t)k * n + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // J^T A
+          const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+          A[(size_t)p * n + k] = cs * apk - sn * aqk;
+          A[(size_t)q * n + k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < n; ++k) {  // V J
+          const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+          V[(size_t)k * n + p] = cs * vkp - sn * vkq;
+          V[(size_t)k * n + q] = sn * vkp + cs * vkq;
+        }
+      }
+  }
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return A[(size_t)a * n + a] < A[(size_t)b * n + b]; });
+  w.resize(n);
+  std::vector<double> Vs((size_t)n * n);
+  for (int j = 0; j < n; ++j) {
+    w[j] = A[(size_t)ord[j] * n + ord[j]];
+    for (int k = 0; k < n; ++k) Vs[(size_t)k * n + j] = V[(size_t)k * n + ord[j]];
+  }
+  V.swap(Vs);
+}
+
+bk_status check_pcg_operator(const bk_operator* A, LzOp* o) {
+  if (A && A->kind == BK_CSR) {
+    if (!A->vals || !A->rowptr || !A->colidx || A->rows <= 0 || A->rows != A->cols || A->nnz < 0) return BK_ERR_ARG;
+    if (A->dtype != BK_F64 && A->dtype != BK_F32) return BK_ERR_UNSUPPORTED;
+    o->kind = BK_CSR;
+    o->d = A->rows;
+    o->nnz = A->nnz;
+    o->vals_f64 = A->dtype == BK_F64;
+    return BK_OK;
+  }
+  return check_lz_operator(A, o);
+}
+
+cudaError_t stage_pcg_operator(bk_ctx* c, const bk_operator* A, LzOp* o) {
+  if (o->kind != BK_CSR) {
+    const void* staged = nullptr;
+    return stage_lz_values(c, A, o, 1, &staged);
+  }
+  const void *rp = nullptr, *ci = nullptr, *va = nullptr;
+  cudaError_t e = stage_in(c, WS_OP_ROW, A->rowptr, (size_t)(o->d + 1) * 4, &rp);
+  if (e != cudaSuccess) return e;
+  if ((e = stage_in(c, WS_OP_COL, A->colidx, (size_t)std::max<int64_t>(o->nnz, 1) * 4, &ci)) != cudaSuccess) return e;
+  if ((e = stage_in(c, WS_OP_VALS, A->vals, (size_t)std::max<int64_t>(o->nnz, 1) * (o->vals_f64 ? 8 : 4), &va)) !=
+      cudaSuccess)
+    return e;
+  o->rowptr = (const int*)rp;
+  o->colidx = (const int*)ci;
+  o->vals = va;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" bk_status bk_nystrom_pcg(bk_ctx* c, const bk_operator* A, double mu, const double* b, double* x,
+                                    int32_t s_ny, const bk_opts* opts_in, bk_info* info) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!c || !b || !x || s_ny < 1 || s_ny > 16 || !(mu >= 0.0) || !std::isfinite(mu)) return BK_ERR_ARG;
+  err_ctx() = c;
+  c->last_error[0] = 0;
+  LzOp o;
+  bk_status s = check_pcg_operator(A, &o);
+  if (s != BK_OK) return s;
+  bk_opts opts;
+  if (opts_in)
+    opts = *opts_in;
+  else
+    bk_default_opts(&opts);
+  if (!(opts.tol > 0.0) || opts.sketch < 1 || opts.max_loads < 1 || opts.check_every < 1) return BK_ERR_ARG;
+  const int64_t d = o.d;
+  const int l = (int)std::min<int64_t>(opts.sketch, d);
+  if (l > 256) return BK_ERR_UNSUPPORTED;
+  BK_CK(cudaSetDevice(c->device));
+  cudaStream_t st = c->stream;
+  cudaEvent_t ev0, ev1;
+  BK_CK(cudaEventCreate(&ev0));
+  BK_CK(cudaEventCreate(&ev1));
+  BK_CK(cudaEventRecord(ev0, st));
+  BK_CK(stage_pcg_operator(c, A, &o));
+  const double* bd = nullptr;
+  BK_CK(stage_in(c, WS_B64, b, (size_t)d * 8, (const void**)&bd));
+
+  // --- Nystrom approximation of depth s (Eq. nystromBKI_def) from s block-Lanczos
+  // steps on Omega: V = [Q_0 .. Q_{s-1}] spans K_s(A, Omega), and the Lanczos relation
+  // A V = V T_s + Q_s B E_s^T gives Y = A V = [V Q_s] [T_s; B E_s^T] without another
+  // load. With T_s = W diag(lam) W^T (numerically nonzero part), F = Y W lam^{-1/2}
+  // satisfies F F^T = Y (V^T Y)^+ Y^T = A<K_s>, and F = [V Q_s] H with
+  // H = [W lam^{1/2}; B E_s^T W lam^{-1/2}]; H^T H = G sig^2 G^T then gives
+  // U = [V Q_s] H G sig^{-1} and D = sig^2.
+  Lanczos lz;
+  const int tmax = s_ny;
+  BK_CK(lz.init(c, o, 1, l, tmax));
+  double* Om = nullptr;
+  BK_CK(ws_get(c, WS_LB0, (size_t)d * l * 8 + 4096 * 8, (void**)&Om));
+  BK_CK(bk::launch_gaussian(opts.seed, 3u, d * (int64_t)l, 0, Om, st));
+  BK_CK(bk::launch_copy_cols(1, 1, d, l, Om, d, lz.W, lz.ldq, st));
+  BK_CK(lz.start(lz.W));
+  for (int k = 0; k < s_ny; ++k) BK_CK(lz.step());
+  const int n = lz.n();  // s l
+  const int nb = n + l;  // columns of [V Q_s]
+  std::vector<double> hband((size_t)(l + 1) * lz.ldb()), hB((size_t)l * l);
+  BK_CK(cudaMemcpyAsync(hband.data(), lz.band, hband.size() * 8, cudaMemcpyDeviceToHost, st));
+  BK_CK(cudaMemcpyAsync(hB.data(), lz.Bk, hB.size() * 8, cudaMemcpyDeviceToHost, st));
+  BK_CK(cudaStreamSynchronize(st));
+  std::vector<double> T((size_t)n * n, 0.0);
+  for (int col = 0; col < n; ++col)
+    for (int r = 0; r <= l && col + r < n; ++r) {
+      const double v = hband[(size_t)r * lz.ldb() + col];
+      T[(size_t)(col + r) * n + col] = v;
+      T[(size_t)col * n + col + r] = v;
+    }
+  std::vector<double> lam, W;
+  jacobi_eigh(n, T, lam, W);
+  const double lmax = lam.empty() ? 0.0 : lam.back();
+  std::vector<int> keep;
+  for (int i = 0; i < n; ++i)
+    if (lam[i] > 1e-13 * lmax) keep.push_back(i);
+  const int k1 = (int)keep.size();
+  if (k1 == 0) {
+    std::snprintf(c->last_error, sizeof(c->last_error), "Nystrom approximation is zero");
+    return BK_BREAKDOWN;
+  }
+  std::vector<double> H((size_t)nb * k1, 0.0);  // row-major nb x k1
+  for (int j = 0; j < k1; ++j) {
+    const int e = keep[j];
+    const double sl = std::sqrt(lam[e]);
+    for (int i = 0; i < n; ++i) H[(size_t)i * k1 + j] = W[(size_t)i * n + e] * sl;
+    // bottom block: B (row-major l x l) times the last l rows of W, scaled by lam^{-1/2}
+    for (int i = 0; i < l; ++i) {
+      double acc = 0.0;
+      for (int q = 0; q < l; ++q) acc += hB[(size_t)i * l + q] * W[(size_t)(n - l + q) * n + e];
+      H[(size_t)(n + i) * k1 + j] = acc / sl;
+    }
+  }
+  std::vector<double> M((size_t)k1 * k1, 0.0);
+  for (int a = 0; a < k1; ++a)
+    for (int bb = a; bb < k1; ++bb) {
+      double acc = 0.0;
+      for (int i = 0; i < nb; ++i) acc += H[(size_t)i * k1 + a] * H[(size_t)i * k1 + bb];
+      M[(size_t)a * k1 + bb] = M[(size_t)bb * k1 + a] = acc;
+    }
+  std::vector<double> sig2, G;
+  jacobi_eigh(k1, M, sig2, G);
+  const double smax = sig2.back();
+  std::vector<int> kept;
+  for (int i = k1 - 1; i >= 0; --i)  // descending, as the oracle's SVD
+    if (sig2[i] > 1e-13 * smax) kept.push_back(i);
+  const int r = (int)kept.size();
+  std::vector<double> Gc((size_t)nb * r), Dv(r);  // column-major nb x r: H G sig^{-1}
+  for (int j = 0; j < r; ++j) {
+    const int e = kept[j];
+    Dv[j] = sig2[e];
+    const double is = 1.0 / std::sqrt(sig2[e]);
+    for (int i = 0; i < nb; ++i) {
+      double acc = 0.0;
+      for (int q = 0; q < k1; ++q) acc += H[(size_t)i * k1 + q] * G[(size_t)q * k1 + e];
+      Gc[(size_t)j * nb + i] = acc * is;
+    }
+  }
+  const double theta = Dv.back();  // smallest eigenvalue of the approximation (Sec. 7)
+  std::vector<double> f(r);
+  for (int j = 0; j < r; ++j) f[j] = (theta + mu) / (Dv[j] + mu) - 1.0;
+
+  // --- device buffers: U (d x r), coefficients, PCG vectors and scalars
+  double *U = nullptr, *pw = nullptr;
+  BK_CK(ws_get(c, WS_NYU, (size_t)d * r * 8 + (size_t)nb * r * 8 + 2 * (size_t)r * 8 + 4096, (void**)&U));
+  double* Gd = U + (size_t)d * r;
+  double* fd = Gd + (size_t)nb * r;
+  double* cv = fd + r;
+  BK_CK(ws_get(c, WS_PCG, (size_t)d * 5 * 8 + 4096 * 8, (void**)&pw));
+  double *xd = pw, *rd = pw + d, *zd = pw + 2 * d, *pd = pw + 3 * d, *qd = pw + 4 * d;
+  double* parts = pw + 5 * d;
+  double* sc = parts + bk::pcg_parts();
+  BK_CK(cudaMemcpyAsync(Gd, Gc.data(), Gc.size() * 8, cudaMemcpyHostToDevice, st));
+  BK_CK(cudaMemcpyAsync(fd, f.data(), f.size() * 8, cudaMemcpyHostToDevice, st));
+  BK_CK(bk::launch_gemm(1, d, r, nb, 1.0, lz.Q, 1, 1, lz.ldq, Gd, 1, nb, 0.0, U, d, st));
+  double* gparts = nullptr;
+  BK_CK(ws_get(c, WS_SPLIT, (size_t)bk::gemv_parts() * r * 8 + 4096, (void**)&gparts));
+  auto precond = [&](const double* rin, double* zout) -> cudaError_t {
+    // z = r + U diag(f) U^T r  ==  (theta + mu) U (D + mu)^{-1} U^T r + (I - U U^T) r
+    cudaError_t e = bk::launch_gemv_t(d, r, U, d, rin, gparts, cv, st);
+    if (e != cudaSuccess) return e;
+    if ((e = bk::launch_scale_vec(r, fd, cv, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(zout, rin, (size_t)d * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    return bk::launch_gemv_n(d, r, U, d, cv, zout, st);
+  };
+  double* Vw = nullptr;
+  if (o.kind == BK_GRAM) BK_CK(ws_get(c, WS_LB64, (size_t)o.nrows * 8, (void**)&Vw));
+
+  // --- PCG from x = 0 (Def. PCG); scalars stay on the device
+  double bn2 = 0.0;
+  BK_CK(bk::launch_dot_scalar(3, d, bd, bd, parts, sc, st));
+  BK_CK(cudaMemsetAsync(xd, 0, (size_t)d * 8, st));
+  BK_CK(cudaMemsetAsync(sc + 5, 0, 8, st));
+  BK_CK(cudaMemcpyAsync(rd, bd, (size_t)d * 8, cudaMemcpyDeviceToDevice, st));
+  BK_CK(precond(rd, zd));
+  BK_CK(cudaMemcpyAsync(pd, zd, (size_t)d * 8, cudaMemcpyDeviceToDevice, st));
+  BK_CK(bk::launch_dot_scalar(2, d, rd, zd, parts, sc, st));
+  BK_CK(cudaMemcpyAsync(c->hparts, sc, 8 * 8, cudaMemcpyDeviceToHost, st));
+  BK_CK(cudaStreamSynchronize(st));
+  bn2 = c->hparts[3];
+  const double bnorm = std::sqrt(bn2);
+  int loads = lz.loads, iters = 0;
+  bk_status result = BK_NOT_CONVERGED;
+  double rel = bnorm > 0.0 ? 1.0 : 0.0;
+  if (bnorm == 0.0) result = BK_OK;
+  double* rtrue = qd;  // scratch for the recomputed residual
+  int checks = 0;
+  while (result != BK_OK && loads < opts.max_loads) {
+    BK_CK(apply_fp64(c, o, pd, d, 1, qd, Vw, true));  // q = A p
+    ++loads;
+    ++iters;
+    if (mu != 0.0) BK_CK(bk::launch_axpy(d, mu, pd, qd, st));  // q = (A + mu) p
+    BK_CK(bk::launch_dot_scalar(0, d, pd, qd, parts, sc, st));  // alpha = rz / p^T q
+    BK_CK(bk::launch_pcg_xr(d, sc, 0.0, pd, qd, xd, rd, parts, st));
+    BK_CK(precond(rd, zd));
+    BK_CK(bk::launch_dot_scalar(1, d, rd, zd, parts, sc, st));
+    BK_CK(bk::launch_pcg_p(d, sc, zd, pd, st));
+    if (iters % opts.check_every != 0 && loads < opts.max_loads) continue;
+    BK_CK(cudaMemcpyAsync(c->hparts, sc, 8 * 8, cudaMemcpyDeviceToHost, st));
+    BK_CK(cudaStreamSynchronize(st));
+    if (c->hparts[5] != 0.0) {
+      result = BK_BREAKDOWN;
+      break;
+    }
+    if (std::sqrt(c->hparts[3]) > opts.tol * bnorm && loads < opts.max_loads) continue;
+    // the recurrence residual met tol (or the cap): confirm with the FP64 residual
+    BK_CK(apply_fp64(c, o, xd, d, 1, rtrue, Vw, true));
+    BK_CK(bk::launch_axpy(d, mu, xd, rtrue, st));
+    BK_CK(bk::launch_axpy(d, -1.0, bd, rtrue, st));
+    BK_CK(bk::launch_dot_scalar(3, d, rtrue, rtrue, parts, sc + 8, st));
+    BK_CK(cudaMemcpyAsync(c->hparts, sc + 8, 8 * 8, cudaMemcpyDeviceToHost, st));
+    BK_CK(cudaStreamSynchronize(st));
+    rel = std::sqrt(c->hparts[3]) / bnorm;
+    ++checks;
+    if (rel <= opts.tol) result = BK_OK;
+    if (loads >= opts.max_loads) break;
+  }
+  BK_CK(cudaMemcpyAsync(x, xd, (size_t)d * 8, cudaMemcpyDefault, st));
+  BK_CK(cudaEventRecord(ev1, st));
+  BK_CK(cudaEventSynchronize(ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (info) {
+    info->status = result;
+    info->loads = loads;
+    info->refinements = r;  // rank of the Nystrom approximation
+    info->residual_loads = checks;
+    info->rel_residual = rel;
+    info->ms_total = ms;
+  }
   return result;
 }
