@@ -212,6 +212,14 @@ bk_status bk_ridge_path(bk_ctx* ctx, const bk_operator* A, int32_t L, const doub
 bk_status bk_sample(bk_ctx* ctx, const bk_operator* K, double nugget, int32_t m, const double* B, double* S,
                     int32_t n_quad, const bk_opts* opts, bk_info* info);
 
+/* Inverse square root S ~= (K + nugget I)^{-1/2} B (Sec. 5, the whitening counterpart of
+ * bk_sample): the same block-Lanczos basis, shifts and weights as bk_sample, since
+ * (2/pi) int_0^inf (A + z^2 I)^{-1} dz = A^{-1/2}; S = Q_t Ybar with
+ * Ybar = sum_j w_j (T_t + (nugget + z_j^2) I)^{-1} E_1 R_0. Arguments, stopping rule and
+ * status as bk_sample. */
+bk_status bk_sample_isqrt(bk_ctx* ctx, const bk_operator* K, double nugget, int32_t m, const double* B, double* S,
+                          int32_t n_quad, const bk_opts* opts, bk_info* info);
+
 /* Nystrom-preconditioned CG, the comparator of Thm. main (Def. PCG, preconditioner of
  * Eq. precond_def): the block-Krylov Nystrom approximation A<K_s> of Eq. nystromBKI_def
  * from the sketch Omega of opts (d x sketch Gaussian, the same Philox key and stream as

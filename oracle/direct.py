@@ -4,6 +4,8 @@
 * ridge_path: x(mu_j) = (A + mu_j I)^{-1} b for every shift via one
               eigendecomposition of A (Sec. 1, ridge regression).
 * sqrtm_apply: A^{1/2} B via the eigendecomposition (Sec. 1, sampling Gaussians).
+* isqrtm_apply: A^{-1/2} B via the eigendecomposition (the inverse square root that
+              Sec. 5 computes with the same basis and shifts, other weights).
 
 Pinned by tests against closed forms (diagonal matrices, known eigenpairs) and
 residuals.
@@ -33,6 +35,12 @@ def sqrtm_apply(a, b, shift=0.0):
     """(A + shift I)^{1/2} B from the eigendecomposition of A."""
     lam, v = np.linalg.eigh(np.asarray(a, dtype=np.float64))
     return v @ (np.sqrt(lam + shift)[:, None] * (v.T @ np.asarray(b, dtype=np.float64)))
+
+
+def isqrtm_apply(a, b, shift=0.0):
+    """(A + shift I)^{-1/2} B from the eigendecomposition of A."""
+    lam, v = np.linalg.eigh(np.asarray(a, dtype=np.float64))
+    return v @ ((1.0 / np.sqrt(lam + shift))[:, None] * (v.T @ np.asarray(b, dtype=np.float64)))
 
 
 def rel_residual(op, mu, x, b):

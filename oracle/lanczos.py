@@ -18,8 +18,12 @@ Orthogonalisation: each new block is orthogonalised against all previous blocks
 twice (classical Gram-Schmidt, twice) and factorised by an SVD-based QR that drops
 directions below rtol, so the block width may shrink once K_t fills R^d.
 
+The inverse square root on the same basis is Q_t T_t^{-1/2} E_1 R_0: the integral of
+bcg_t(z^2) itself, without the factor A.
+
 Pinned by: shift invariance against separate direct solves, brute-force Galerkin
-iterates, finite termination, and closed-form A^{1/2} on known spectra.
+iterates, finite termination, closed-form A^{1/2} and A^{-1/2} on known spectra, and
+adaptive quadrature of both integrals on a partial basis.
 """
 from __future__ import annotations
 
@@ -98,6 +102,19 @@ def shifted_iterates(lz, mus, col=0):
     rhs[:lz["R0"].shape[0]] = lz["R0"][:, col]
     Z = np.stack([np.linalg.solve(T + mu * np.eye(n), rhs) for mu in mus], axis=1)
     return Q @ Z
+
+
+def isqrt_iterate(lz):
+    """The inverse square root on the basis: (2/pi) int_0^inf bcg_t(z^2) dz for every
+    column of B, which is exactly Q_t T_t^{-1/2} E_1 R_0 (Sec. 5: the same shifted
+    iterates as bsq_t without the factor A, so no Lanczos-relation term)."""
+    Q = basis(lz)
+    T = tridiag(lz)
+    n = T.shape[0]
+    lam, V = np.linalg.eigh(T)
+    E1R0 = np.zeros((n, lz["R0"].shape[1]))
+    E1R0[:lz["R0"].shape[0]] = lz["R0"]
+    return Q @ (V @ ((1.0 / np.sqrt(lam))[:, None] * (V.T @ E1R0)))
 
 
 def sqrt_iterate(lz):

@@ -88,6 +88,8 @@ def _load():
                                 ctypes.POINTER(Info)]),
         "bk_nystrom_pcg": (i32, [vp, ctypes.POINTER(Operator), dbl, vp, vp, i32, ctypes.POINTER(Opts),
                                  ctypes.POINTER(Info)]),
+        "bk_sample_isqrt": (i32, [vp, ctypes.POINTER(Operator), dbl, i32, vp, vp, i32, ctypes.POINTER(Opts),
+                                  ctypes.POINTER(Info)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -275,6 +277,21 @@ def ridge_path(ctx: Context, A: OperatorRef, mus, b, X, opts: Opts | None = None
                            ctypes.byref(info))
     if check and s != BK_OK:
         raise BKError(s, "bk_ridge_path", ctx.last_error())
+    return info
+
+
+def sample_isqrt(ctx: Context, K: OperatorRef, nugget: float, B, S, n_quad: int = 32, opts: Opts | None = None,
+                 check=True) -> Info:
+    """bk_sample_isqrt: S ~= (K + nugget I)^{-1/2} B (B, S d x m column-major)."""
+    info = Info()
+    pb, kb = _ptr(B)
+    ps, ks = _ptr(S)
+    m = B.shape[1]
+    o = opts if opts is not None else default_opts()
+    st = _lib.bk_sample_isqrt(ctx.handle, ctypes.byref(K.op), float(nugget), int(m), pb, ps, int(n_quad),
+                              ctypes.byref(o), ctypes.byref(info))
+    if check and st != BK_OK:
+        raise BKError(st, "bk_sample_isqrt", ctx.last_error())
     return info
 
 

@@ -608,8 +608,15 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
   return result;
 }
 
-extern "C" bk_status bk_sample(bk_ctx* c, const bk_operator* Kop, double nugget, int32_t m, const double* B,
-                               double* S, int32_t n_quad, const bk_opts* opts_in, bk_info* info) {
+namespace {
+
+// bk_sample (inverse = false: (K + nugget I)^{1/2} B) and bk_sample_isqrt (inverse =
+// true: (K + nugget I)^{-1/2} B) share the basis, the shifts and the weights: with
+// Ybar = sum_j w_j (T_t + (nugget + z_j^2) I)^{-1} E_1 R_0, the square root is
+// Q_t (T_t + nugget) Ybar + Q_{t+1} B_t E_t^T Ybar (Def. blansq) and the inverse square
+// root Q_t Ybar (the integrand without the factor A).
+bk_status sample_driver(bk_ctx* c, const bk_operator* Kop, double nugget, int32_t m, const double* B, double* S,
+                        int32_t n_quad, const bk_opts* opts_in, bk_info* info, bool inverse) {
   if (info) std::memset(info, 0, sizeof(*info));
   if (!c || !B || !S || m < 1 || m > 256 || n_quad < 1 || n_quad > 1024 || !(nugget >= 0.0) ||
       !std::isfinite(nugget))
@@ -709,14 +716,14 @@ extern "C" bk_status bk_sample(bk_ctx* c, const bk_operator* Kop, double nugget,
     }
     // Ybar = sum_j w_j Y_j; S = Q_t (T_t + nugget) Ybar + Q_{t+1} B_t E_t^T Ybar
     BK_CK(bk::launch_combine_shifts(n, m, N, Z, dw, Ybar, st));
-    BK_CK(bk::launch_band_mult(n, m, lz.band, lz.ldb(), nugget, Ybar, m, M1, st));
-    BK_CK(bk::launch_gemm(1, d, m, n, 1.0, lz.Q, is64, 1, lz.ldq, M1, 1, n, 0.0, Sd, d, st));
-    // small = B_t (rows n-m.. of Ybar): B_t row-major m x m, Ybar rows n-m..n-1 (ld n)
-    BK_CK(bk::launch_gemm(1, m, m, m, 1.0, lz.Bk, 1, m, 1, Ybar + (n - m), 1, n, 0.0, small, m, st));
-    if (is64) {
-      BK_CK(bk::launch_gemm(1, d, m, m, 1.0, lz.qblock(lz.t), 1, 1, lz.ldq, small, 1, m, 1.0, Sd, d, st));
+    if (inverse) {
+      BK_CK(bk::launch_gemm(1, d, m, n, 1.0, lz.Q, is64, 1, lz.ldq, Ybar, 1, n, 0.0, Sd, d, st));
     } else {
-      BK_CK(bk::launch_gemm(1, d, m, m, 1.0, lz.qblock(lz.t), 0, 1, lz.ldq, small, 1, m, 1.0, Sd, d, st));
+      BK_CK(bk::launch_band_mult(n, m, lz.band, lz.ldb(), nugget, Ybar, m, M1, st));
+      BK_CK(bk::launch_gemm(1, d, m, n, 1.0, lz.Q, is64, 1, lz.ldq, M1, 1, n, 0.0, Sd, d, st));
+      // small = B_t (rows n-m.. of Ybar): B_t row-major m x m, Ybar rows n-m..n-1 (ld n)
+      BK_CK(bk::launch_gemm(1, m, m, m, 1.0, lz.Bk, 1, m, 1, Ybar + (n - m), 1, n, 0.0, small, m, st));
+      BK_CK(bk::launch_gemm(1, d, m, m, 1.0, lz.qblock(lz.t), is64, 1, lz.ldq, small, 1, m, 1.0, Sd, d, st));
     }
     // relative change against the previous check (a-posteriori stopping, Sec. 4 remark)
     int np = bk::residual_parts(d * m);
@@ -753,6 +760,18 @@ extern "C" bk_status bk_sample(bk_ctx* c, const bk_operator* Kop, double nugget,
   }
   prof.report(info);
   return result;
+}
+
+}  // namespace
+
+extern "C" bk_status bk_sample(bk_ctx* c, const bk_operator* Kop, double nugget, int32_t m, const double* B,
+                               double* S, int32_t n_quad, const bk_opts* opts_in, bk_info* info) {
+  return sample_driver(c, Kop, nugget, m, B, S, n_quad, opts_in, info, false);
+}
+
+extern "C" bk_status bk_sample_isqrt(bk_ctx* c, const bk_operator* Kop, double nugget, int32_t m, const double* B,
+                                     double* S, int32_t n_quad, const bk_opts* opts_in, bk_info* info) {
+  return sample_driver(c, Kop, nugget, m, B, S, n_quad, opts_in, info, true);
 }
 
 // ---------------------------------------------------------------- Nystrom PCG

@@ -82,3 +82,44 @@ def test_sample_rbf_subset_validation(bk, ctx, inner):
     assert info.status == bk.BK_OK, info.as_dict()
     tol = 1e-8 if inner == "fp64" else 1e-7
     assert err <= tol, (err, tol, info.as_dict())
+
+
+def test_isqrt_matches_exact_integral_on_same_basis(bk, ctx):
+    """The inverse square root at a fixed number of loads equals the oracle's exact
+    integral on the same basis, Q_t T_t^{-1/2} E_1 R_0, up to the quadrature error."""
+    d, m = 300, 12
+    pts = W.rbf_points(W.BASE_SEED + 32, d)
+    K = W.rbf_kernel(pts)
+    nug = 1e-2
+    B = W.sample_block(W.BASE_SEED + 32, d, m)
+    for t in [2, 4]:
+        S = np.zeros((d, m), order="F")
+        bk.sample_isqrt(ctx, bk.dense_operator(K), nug, B, S, 32,
+                        bk.default_opts(tol=1e-14, max_loads=t, check_every=100), check=False)
+        lz = lanczos.block_lanczos(K + nug * np.eye(d), B, t)
+        ref = lanczos.isqrt_iterate(lz)
+        assert np.linalg.norm(S - ref) / np.linalg.norm(ref) < 1e-9, t
+
+
+@pytest.mark.parametrize("d, m, nug, inner, tol", [(600, 32, 1e-3, "fp64", 1e-8), (2000, 256, 1e-6, "fp64", 1e-7),
+                                                  (2000, 256, 1e-6, "f32x2", None)])
+def test_isqrt_converges(bk, ctx, d, m, nug, inner, tol):
+    """(K + nugget I)^{-1/2} B against the oracle's eigendecomposition of the stored K;
+    the 2000-point case is the sampling configuration's validation problem (K in FP32).
+    Compensated FP32-pair products carry about 1e-13 ||K|| absolute error; the inverse
+    square root amplifies a perturbation of A by up to 1 / lambda_min relative, so the
+    bound is 1e-13 ||K|| / lambda_min(K + nugget) (2.6e-5 here)."""
+    pts = W.rbf_points(W.BASE_SEED + 4 if d == 2000 else W.BASE_SEED + 33, 40000 if d == 2000 else d)[:d]
+    K = W.rbf_kernel(pts, dtype=np.float32 if d == 2000 else np.float64)
+    B = (W.sample_block(W.BASE_SEED + 4, 40000, m)[:d].copy(order="F") if d == 2000
+         else W.sample_block(W.BASE_SEED + 33, d, m))
+    S = np.zeros((d, m), order="F")
+    info = bk.sample_isqrt(ctx, bk.dense_operator(torch.from_numpy(K).to("cuda:0")), nug, B, S, 32,
+                           bk.default_opts(tol=1e-10, inner=inner, check_every=2, max_loads=64), check=False)
+    assert info.status == bk.BK_OK, info.as_dict()
+    ref = direct.isqrtm_apply(K.astype(np.float64), B, shift=nug)
+    err = np.linalg.norm(S - ref) / np.linalg.norm(ref)
+    if tol is None:
+        lam = np.linalg.eigvalsh(K.astype(np.float64)) + nug
+        tol = 1e-13 * lam[-1] / lam[0]
+    assert err <= tol, (err, tol, info.as_dict())

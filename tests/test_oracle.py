@@ -204,6 +204,31 @@ def test_sqrt_iterate_closed_forms():
         assert abs(2 / np.pi * val - bsq[i]) <= 1e-8 * np.linalg.norm(bsq)
 
 
+def test_isqrt_closed_forms():
+    """A^{-1/2}: diagonal closed form; SciPy's matrix square root, inverted; the Lanczos
+    iterate is exact once K_t = R^d and equals the integral of bcg_t(z^2) over z for a
+    partial basis (adaptive quadrature)."""
+    import scipy.linalg as sla
+    lam = np.logspace(-1, 2, 24)
+    b = W.normals(11, 2, 24)
+    np.testing.assert_allclose(direct.isqrtm_apply(np.diag(lam), b[:, None], shift=0.5)[:, 0],
+                               b / np.sqrt(lam + 0.5), rtol=1e-14)
+    a = spd(24, lam, 12)
+    B = np.column_stack([b, W.omega(11, 24, 3)])
+    ref = np.linalg.solve(np.real(sla.sqrtm(a + 0.1 * np.eye(24))), B)
+    np.testing.assert_allclose(direct.isqrtm_apply(a, B, shift=0.1), ref, rtol=1e-9, atol=1e-12)
+    lz = lanczos.block_lanczos(a, B, 6)
+    np.testing.assert_allclose(lanczos.isqrt_iterate(lz), direct.isqrtm_apply(a, B), rtol=1e-9, atol=1e-10)
+    lzp = lanczos.block_lanczos(a, B, 2)
+    v = lanczos.isqrt_iterate(lzp)[:, 0]
+
+    def integrand(z, i):
+        return lanczos.shifted_iterates(lzp, [z * z])[i, 0]
+    for i in [0, 7, 19]:
+        val, _ = si.quad(integrand, 0, np.inf, args=(i,), epsabs=1e-12, epsrel=1e-11, limit=400)
+        assert abs(2 / np.pi * val - v[i]) <= 1e-8 * np.linalg.norm(v)
+
+
 def test_elliptic_identity():
     """Eq. ellipticK_eval: int_0^inf dz / sqrt((l1+z^2)(ld+z^2)) = K(1 - l1/ld)/sqrt(ld)
     (K with parameter m, ld < l1), and it equals pi / (2 AGM(sqrt l1, sqrt ld))."""
