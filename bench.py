@@ -630,6 +630,15 @@ def run_sample(args, world, rank, local, dev):
         torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1) / args.steps
     pinfo = call(opts(profile=1))
+    # the inverse square root on the same basis, shifts and weights (one timed call)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        iinfo = bk.sample_isqrt(ctx, op, args.sample_nugget, Bt.T, S.T, SAMPLE_NQUAD, opts(), check=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    isqrt = {"value": m / (e0.elapsed_time(e1) / 1e3), "unit": "samples/s", "ms": e0.elapsed_time(e1),
+             "loads": iinfo.loads, "last_change": iinfo.rel_residual, "status": iinfo.status}
     names = bk.KERNEL_CLASSES
     groups = {}
     for k in ("operator", "orth"):
@@ -666,7 +675,7 @@ def run_sample(args, world, rank, local, dev):
                          "hbm_equiv": {"achieved_gbs": 4.0 * d * d / (groups['operator']['avg_ms'] / 1e3) / 1e9
                                        if groups["operator"]["calls"] else None, "peak": peak_hbm,
                                        "peak_source": peak_src}},
-            "clocks": clocks, "cpu_baseline": None,
+            "isqrt": isqrt, "clocks": clocks, "cpu_baseline": None,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
