@@ -76,7 +76,7 @@ struct TsCfg {
 // Shared memory per stage: sA[BM][TS_LDK] floats, then sB (FP32: [NT][TS_LDK]; DF: head
 // and tail, 2 x [NT][TS_LDK]).
 template <int NPT, bool DF>
-__global__ void __launch_bounds__(TS_TH) k_tsm_nn(int64_t M, int N, int64_t K, double alpha, const float* __restrict__ A,
+__global__ void __launch_bounds__(TS_TH, 3) k_tsm_nn(int64_t M, int N, int64_t K, double alpha, const float* __restrict__ A,
                                                   int64_t lda, const void* __restrict__ Bv, int64_t ldb, double beta,
                                                   void* Cv, int64_t ldc) {
   using Cfg = TsCfg<DF>;
@@ -90,27 +90,40 @@ __global__ void __launch_bounds__(TS_TH) k_tsm_nn(int64_t M, int N, int64_t K, d
   const int j0 = blockIdx.x * NT;
   const int nst = (int)((K + TS_BK - 1) / TS_BK);
 
+  // Staging geometry is fixed per thread: chunk column c4 = tid % 8 (16 bytes of a
+  // 32-deep slice) and rows (or columns of B) r0 + 16 e; only the slice offset moves.
+  const int c4 = tid & 7, r0 = tid >> 3;
+  constexpr int EA = BM / 16, EB = (NT * 8 + TS_TH - 1) / TS_TH;
+  const float* a_row = A + (i0 + r0) * lda + c4 * 4;
+  const int64_t a_step = 16 * lda;
+  unsigned a_ok = 0, b_ok = 0;
+#pragma unroll
+  for (int e = 0; e < EA; ++e)
+    if (i0 + r0 + 16 * e < M) a_ok |= 1u << e;
+#pragma unroll
+  for (int e = 0; e < EB; ++e)
+    if (r0 + 16 * e < NT && j0 + r0 + 16 * e < N) b_ok |= 1u << e;
   auto issue_a = [&](int s, int buf) {
-    float* sA = smem + buf * ST_FL;
-    const int64_t k0 = (int64_t)s * TS_BK;
-    for (int q = tid; q < BM * (TS_BK / 4); q += TS_TH) {
-      const int row = q >> 3, c4 = q & 7;
-      const int64_t gi = i0 + row, gk = k0 + c4 * 4;
-      const int bytes = gi < M ? clamp16((K - gk) * 4) : 0;
-      const float* src = bytes ? A + gi * lda + gk : A;
-      cp16(sA + row * TS_LDK + c4 * 4, src, bytes);
+    float* sA = smem + buf * ST_FL + r0 * TS_LDK + c4 * 4;
+    const int64_t k = (int64_t)s * TS_BK + c4 * 4;
+    const int bytes = clamp16((K - k) * 4);
+    const float* src = a_row + (int64_t)s * TS_BK;
+#pragma unroll 1
+    for (int e = 0; e < EA; ++e, src += a_step) {
+      const bool ok = (a_ok >> e & 1u) && bytes;
+      cp16(sA + 16 * e * TS_LDK, ok ? src : A, ok ? bytes : 0);
     }
   };
   auto issue_b32 = [&](int s, int buf) {
-    float* sB = smem + buf * ST_FL + A_FL;
+    float* sB = smem + buf * ST_FL + A_FL + r0 * TS_LDK + c4 * 4;
     const float* B = (const float*)Bv;
-    const int64_t k0 = (int64_t)s * TS_BK;
-    for (int q = tid; q < NT * (TS_BK / 4); q += TS_TH) {
-      const int j = q >> 3, c4 = q & 7;
-      const int64_t gk = k0 + c4 * 4;
-      const int bytes = (j0 + j) < N ? clamp16((K - gk) * 4) : 0;
-      const float* src = bytes ? B + (int64_t)(j0 + j) * ldb + gk : B;
-      cp16(sB + j * TS_LDK + c4 * 4, src, bytes);
+    const int64_t k = (int64_t)s * TS_BK + c4 * 4;
+    const int bytes = clamp16((K - k) * 4);
+#pragma unroll 1
+    for (int e = 0; e < EB; ++e) {
+      if (r0 + 16 * e >= NT) break;
+      const bool ok = (b_ok >> e & 1u) && bytes;
+      cp16(sB + 16 * e * TS_LDK, ok ? B + (int64_t)(j0 + r0 + 16 * e) * ldb + k : B, ok ? bytes : 0);
     }
   };
   auto load_b64 = [&](int s, int buf) {  // DF: synchronous load, split into head / tail
@@ -237,7 +250,7 @@ __global__ void __launch_bounds__(TS_TH) k_tsm_nn(int64_t M, int N, int64_t K, d
 // tc + 8 v. Shared memory per stage: sZ[TS_BK][BD + 4], sT (FP32: [NT][TS_LDK]; DF:
 // head and tail).
 template <int NPT, bool DF>
-__global__ void __launch_bounds__(TS_TH) k_tsm_tn(int64_t R, int64_t D, int N, int64_t rows_per_chunk,
+__global__ void __launch_bounds__(TS_TH, 3) k_tsm_tn(int64_t R, int64_t D, int N, int64_t rows_per_chunk,
                                                   const float* __restrict__ Z, int64_t ldz, const void* __restrict__ Tv,
                                                   int64_t ldt, void* Wv, int64_t ldw) {
   using Cfg = TsCfg<DF>;
@@ -251,27 +264,34 @@ __global__ void __launch_bounds__(TS_TH) k_tsm_tn(int64_t R, int64_t D, int N, i
   const int j0 = blockIdx.z * NT;
   const int nst = r1 > r0 ? (int)((r1 - r0 + TS_BK - 1) / TS_BK) : 0;
 
+  // fixed staging geometry: Z chunks (column c4z = tid % (BD/4), rows rz + (128 / (BD/4)) e),
+  // T chunks (column c4 = tid % 8 of the slice, T columns rt + 16 e)
+  constexpr int ZC = BD / 4, ZR = TS_TH / ZC, EZ = TS_BK / ZR, ET = (NT * 8 + TS_TH - 1) / TS_TH;
+  const int c4z = tid % ZC, rz = tid / ZC, c4 = tid & 7, rt = tid >> 3;
+  const int64_t gkz = d0 + c4z * 4;
+  const int zbytes = clamp16((D - gkz) * 4);
+  const float* z_col = Z + gkz;
   auto issue_z = [&](int s, int buf) {
-    float* sZ = smem + buf * ST_FL;
-    const int64_t i0 = r0 + (int64_t)s * TS_BK;
-    for (int q = tid; q < TS_BK * (BD / 4); q += TS_TH) {
-      const int row = q / (BD / 4), c4 = q % (BD / 4);
-      const int64_t gi = i0 + row, gk = d0 + c4 * 4;
-      const int bytes = gi < r1 ? clamp16((D - gk) * 4) : 0;
-      const float* src = bytes ? Z + gi * ldz + gk : Z;
-      cp16(sZ + row * LDZ + c4 * 4, src, bytes);
+    float* sZ = smem + buf * ST_FL + rz * LDZ + c4z * 4;
+    const int64_t i0 = r0 + (int64_t)s * TS_BK + rz;
+#pragma unroll
+    for (int e = 0; e < EZ; ++e) {
+      const int64_t gi = i0 + ZR * e;
+      const bool ok = gi < r1 && zbytes;
+      cp16(sZ + ZR * e * LDZ, ok ? z_col + gi * ldz : Z, ok ? zbytes : 0);
     }
   };
   auto issue_t32 = [&](int s, int buf) {
-    float* sT = smem + buf * ST_FL + Z_FL;
+    float* sT = smem + buf * ST_FL + Z_FL + rt * TS_LDK + c4 * 4;
     const float* T = (const float*)Tv;
-    const int64_t i0 = r0 + (int64_t)s * TS_BK;
-    for (int q = tid; q < NT * (TS_BK / 4); q += TS_TH) {
-      const int j = q >> 3, c4 = q & 7;
-      const int64_t gi = i0 + c4 * 4;
-      const int bytes = (j0 + j) < N ? clamp16((r1 - gi) * 4) : 0;
-      const float* src = bytes ? T + (int64_t)(j0 + j) * ldt + gi : T;
-      cp16(sT + j * TS_LDK + c4 * 4, src, bytes);
+    const int64_t gi = r0 + (int64_t)s * TS_BK + c4 * 4;
+    const int bytes = clamp16((r1 - gi) * 4);
+#pragma unroll
+    for (int e = 0; e < ET; ++e) {
+      const int j = rt + 16 * e;
+      if (j >= NT) break;
+      const bool ok = (j0 + j) < N && bytes;
+      cp16(sT + 16 * e * TS_LDK, ok ? T + (int64_t)(j0 + j) * ldt + gi : T, ok ? bytes : 0);
     }
   };
   auto load_t64 = [&](int s, int buf) {
