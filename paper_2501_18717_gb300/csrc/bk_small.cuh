@@ -92,9 +92,10 @@ __device__ int block_cholesky_skip(SmallShared& sh, int m, double rank_tol) {
   // square roots (L[k][k] and 1 / L[k][k]) and the scaling of the columns follow in
   // one parallel pass at the end. The pivot thread (lane 0 of the last warp) updates
   // the next diagonal entry and forms its reciprocal; the other pairs (i, j),
-  // k < j <= i, of the trailing triangle are spread evenly over the other threads, so
-  // the pivot chain does not wait on a warp that also carries update work.
+  // k < j <= i, of the trailing triangle are spread over the other threads, so the
+  // pivot chain does not wait on a warp that also carries update work.
   constexpr int PW = NTH - 32;
+  static_assert(PW % 8 == 0 && PW >= 8, "update threads form a TI x 8 grid");
   auto pivot = [&](int k) {  // keep column k if its pivot is above rank_tol
     const double x = W[k * kLds + k];
     const bool keep = x > rank_tol;
@@ -110,14 +111,14 @@ __device__ int block_cholesky_skip(SmallShared& sh, int m, double rank_tol) {
     if (n > 0) {
       if (tid < PW) {
         if (rx != 0.0) {
-          const int npairs = n * (n + 1) / 2 - 1;  // all but the diagonal (k+1, k+1)
-          for (int p = tid; p < npairs; p += PW) {
-            const int q = p + 1;  // index in the triangle, row-major: (r, c), c <= r
-            int r = (int)((sqrtf(8.f * q + 1.f) - 1.f) * 0.5f);
-            while ((r + 1) * (r + 2) / 2 <= q) ++r;
-            while (r * (r + 1) / 2 > q) --r;
-            const int i = k + 1 + r, j = k + 1 + (q - r * (r + 1) / 2);
-            W[i * kLds + j] = fma(-W[i * kLds + k] * rx, W[j * kLds + k], W[i * kLds + j]);
+          // the trailing triangle k < j <= i < m over a fixed TI x 8 thread grid: rows
+          // k + 1 + ti + TI a, columns k + 1 + tj + 8 b (no index decoding per entry)
+          constexpr int TJ = 8, TI = PW / TJ;
+          const int ti = tid / TJ, tj = tid % TJ;
+          for (int i = k + 1 + ti; i < m; i += TI) {
+            const double lik = -W[i * kLds + k] * rx;
+            for (int j = k + 1 + tj; j <= i; j += TJ)
+              if (j != i || i != k + 1) W[i * kLds + j] = fma(lik, W[j * kLds + k], W[i * kLds + j]);
           }
         }
       } else if (tid == PW) {
