@@ -315,6 +315,31 @@ def run_batched(args, world, rank, local, dev):
                 "rel_residual_max": max(i.rel_residual for i in pinfo),
                 "loads_mean": float(np.mean([i.loads for i in pinfo])),
                 "note": "FP64 blocks on every (n/subset)-th system by size; solves/s scaled by sum d^2"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the FP64 oracle's refined block-CG on a size-stratified subset, scaled by sum d^2
+        from oracle import bcg
+        order = np.argsort(ds)
+        sub, spent, t_all = [], 0.0, 0.0
+        # systems at the size quantiles 0, 1/5, ..., 1 (smallest first), while time lasts
+        for q in np.linspace(0.0, 1.0, 6):
+            i = int(order[min(n - 1, int(round(q * (n - 1))))])
+            if spent > args.cpu_seconds:
+                break
+            A_, b_ = W.batch_system(BATCH_SEED, i, ds[i])
+            sk = table.get(int(np.floor(np.log2(ds[i]))), 16)
+            om = W.omega(OMEGA_SEED + i, ds[i], sk)
+            t0 = time.perf_counter()
+            bcg.refined_solve(A_.astype(np.float64), 0.0, b_, om, tol=TOL, inner_tol=1e-6, max_loads=5000)
+            dt = time.perf_counter() - t0
+            spent += dt
+            t_all += dt
+            sub.append(i)
+        frac = sum(ds[i] ** 2 for i in sub) / sum(d * d for d in ds)
+        cpu = {"value": n / (t_all / frac), "unit": "solves/s", "cores": threads_used(), "kind": "oracle",
+               "sample": f"FP64 oracle refined block-CG (NumPy) on {len(sub)} systems at the size quantiles "
+                         f"0, 0.2, ..., 1 (d = {[ds[i] for i in sub]}), stopping once {args.cpu_seconds:.0f} s "
+                         f"were spent; solves/s scaled by their share of sum d^2 ({frac:.4f})"}
     if rank == 0:
         line = {
             "metric": "solves/s at rel. residual 1e-8, batched uneven dense systems, mixed vs FP64 plain",
@@ -329,7 +354,7 @@ def run_batched(args, world, rank, local, dev):
             "loads_max": int(max(loads)),
             "roofline": {"bound": "hbm", "kernel": "whole solve (A streamed once per load)", "achieved": gbs,
                          "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None, "peak_source": peak_src},
-            "fp64_plain": fp64, "clocks": clk.summary(), "cpu_baseline": None,
+            "fp64_plain": fp64, "clocks": clk.summary(), "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -653,12 +678,37 @@ def run_sample(args, world, rank, local, dev):
     # compensated FP32-pair products issue about 11 FP32 instructions per multiply-add
     issue = (11.0 if args.sample_inner == "f32x2" else 1.0)
     peak_hbm, peak_src = measured_peaks()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the FP64 oracle's block-Lanczos (full reorthogonalisation) on the stored K
+        # promoted to FP64, timed for a bounded number of steps
+        from oracle import lanczos, operators
+        Kh = K.cpu().numpy()
+        op64 = operators.Dense(Kh)
+        del Kh
+        Bh = B.cpu().numpy()
+        t0 = time.perf_counter()
+        lanczos.block_lanczos(op64, Bh, 1)
+        t1 = time.perf_counter() - t0
+        nsteps = int(max(1, min(4, args.cpu_seconds / max(t1, 1e-3))))
+        t0 = time.perf_counter()
+        lanczos.block_lanczos(op64, Bh, nsteps)
+        sps = (time.perf_counter() - t0) / nsteps
+        del op64
+        loads = infos[-1].loads
+        cpu = {"value": m / (sps * loads), "unit": "samples/s", "cores": threads_used(), "kind": "oracle",
+               "sample": f"{nsteps} block-Lanczos steps of the FP64 oracle (NumPy, full reorthogonalisation, "
+                         f"K promoted to FP64, block width {m}) on the full workload, {sps:.2f} s/step; "
+                         f"samples/s = {m} / (s per step x {loads} loads, the loads of this run's GPU call; "
+                         "the quadrature solves are not counted)"}
     if rank == 0:
         line = {
             "metric": "samples/s, (K + nugget I)^{1/2} B by block-Lanczos quadrature (32 shifts)",
             "value": world * m / (ms / 1e3), "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 products + f64 Gram/band solves", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": "f64 blocks, " + ("compensated f32-pair" if args.sample_inner == "f32x2" else args.sample_inner)
+                     + " products of the f32-stored K, f64 Gram/band solves", "data": "synthetic",
             "config": {"workload": f"rbf_sample_d{d}_m{m}_ls0.2_nugget{args.sample_nugget:g}_fp32_nquad32",
                        "stop": "relative change of S <= 1e-4 between checks every 4 loads, or the load cap",
                        "inner": args.sample_inner,
@@ -675,7 +725,7 @@ def run_sample(args, world, rank, local, dev):
                          "hbm_equiv": {"achieved_gbs": 4.0 * d * d / (groups['operator']['avg_ms'] / 1e3) / 1e9
                                        if groups["operator"]["calls"] else None, "peak": peak_hbm,
                                        "peak_source": peak_src}},
-            "isqrt": isqrt, "clocks": clocks, "cpu_baseline": None,
+            "isqrt": isqrt, "clocks": clocks, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
