@@ -185,6 +185,9 @@ cudaError_t launch_chol_inv(int m, const double* G, double rank_tol, double* wor
                             int* keep, int* rank, cudaStream_t st);
 cudaError_t launch_band_put(int ldb, int bw, int m, int k, const double* A, const double* B, double* band,
                             cudaStream_t st);
+// M = [B^T; A] (2m x m column-major, block precision) for the three-term recurrence
+cudaError_t launch_three_term(int is_f64, int m, int first, const double* A, const double* B, void* M,
+                              cudaStream_t st);
 cudaError_t launch_band_solve(int n, int bw, const double* band, int ldb, int L, const double* mus,
                               const double* rhs, const int* rhs_col, int nrhs, double* work, double* Z, int* flags,
                               cudaStream_t st);

@@ -83,7 +83,7 @@ struct Lanczos {
   LzOp op;
   int m = 0, tmax = 0;
   int64_t d = 0, ldq = 0, ncol_max = 0, ldv = 0;
-  void *Q = nullptr, *W = nullptr, *V = nullptr, *C = nullptr, *Rt = nullptr;
+  void *Q = nullptr, *W = nullptr, *V = nullptr, *C = nullptr, *Rt = nullptr, *M3 = nullptr;
   double *G = nullptr, *R1 = nullptr, *R2 = nullptr, *Ri1 = nullptr, *Ri2 = nullptr, *work = nullptr;
   double *Ak = nullptr, *Bk = nullptr, *R0 = nullptr, *band = nullptr;
   int *keep = nullptr, *rank = nullptr;
@@ -116,6 +116,7 @@ struct Lanczos {
     if (op.kind == BK_GRAM)
       if ((e = ws_get(c, WS_LV, (size_t)ldv * m * es, &V)) != cudaSuccess) return e;
     if ((e = ws_get(c, WS_LC, (size_t)ncol_max * m * es, &C)) != cudaSuccess) return e;
+    if ((e = ws_get(c, WS_LQ2, (size_t)2 * m * m * es, &M3)) != cudaSuccess) return e;
     double* sm = nullptr;
     const size_t mm = (size_t)m * m;
     if ((e = ws_get(c, WS_LSMALL, (11 * mm + 2 * m + 64) * 8, (void**)&sm)) != cudaSuccess) return e;
@@ -233,14 +234,20 @@ struct Lanczos {
     // A_k = Q_k^T (A Q_k) with FP64 accumulation
     const int gaf = is64 ? 1 : 2;
     if ((e = gemm_k(1, m, m, d, 1.0, Qk, gaf, ldq, 1, W, 1, ldq, 0.0, Ak, m)) != cudaSuccess) return e;
-    // full reorthogonalisation against Q_0..Q_k, twice
+    // three-term recurrence W -= Q_{k-1} B_{k-1}^T + Q_k A_k (Bk still holds B_{k-1}),
+    // then one classical Gram-Schmidt pass against Q_0..Q_k for what rounding left along
+    // the older blocks (full reorthogonalisation; the first pass of a CGS2 against all
+    // blocks would remove the same two terms, so the result equals it up to rounding)
+    if ((e = bk::launch_three_term(is64, m, k == 0, Ak, Bk, M3, st)) != cudaSuccess) return e;
+    if (k == 0)
+      e = bk::launch_gemm(is64, d, m, m, -1.0, Qk, is64, 1, ldq, (const char*)M3 + (size_t)m * es, 1, 2 * m, 1.0, W,
+                          ldq, st);
+    else
+      e = bk::launch_gemm(is64, d, m, 2 * m, -1.0, qblock(k - 1), is64, 1, ldq, M3, 1, 2 * m, 1.0, W, ldq, st);
+    if (e != cudaSuccess) return e;
     const int64_t nk = (int64_t)(k + 1) * m;
-    for (int pass = 0; pass < 2; ++pass) {
-      if ((e = gemm_k(is64, nk, m, d, 1.0, Q, is64, ldq, 1, W, 1, ldq, 0.0, C, nk)) != cudaSuccess)
-        return e;
-      if ((e = gemm_k(is64, d, m, nk, -1.0, Q, is64, 1, ldq, C, 1, nk, 1.0, W, ldq)) != cudaSuccess)
-        return e;
-    }
+    if ((e = gemm_k(is64, nk, m, d, 1.0, Q, is64, ldq, 1, W, 1, ldq, 0.0, C, nk)) != cudaSuccess) return e;
+    if ((e = gemm_k(is64, d, m, nk, -1.0, Q, is64, 1, ldq, C, 1, nk, 1.0, W, ldq)) != cudaSuccess) return e;
     if ((e = qr(W, qblock(k + 1), Bk)) != cudaSuccess) return e;
     if (prof) prof->end(BK_K_ORTH);
     if ((e = bk::launch_band_put(ldb(), m, m, k, Ak, Bk, band, st)) != cudaSuccess) return e;

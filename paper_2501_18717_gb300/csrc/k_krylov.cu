@@ -129,6 +129,22 @@ __global__ void k_band_put(int ldb, int bw, int m, int k, const double* __restri
   }
 }
 
+// M (2m x m, column-major, block precision) = [B_{k-1}^T; A_k] for the three-term
+// recurrence W -= [Q_{k-1} Q_k] M; B (upper triangular) and A row-major m x m FP64.
+// first: the top half is zero (no Q_{k-1}).
+template <typename T>
+__global__ void k_three_term(int m, int first, const double* __restrict__ A, const double* __restrict__ B, T* M) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * m * m; idx += gridDim.x * blockDim.x) {
+    const int j = idx / (2 * m), r = idx - j * 2 * m;
+    double v;
+    if (r < m)
+      v = first ? 0.0 : B[j * m + r];  // (B^T)(r, j) = B(j, r)
+    else
+      v = A[(r - m) * m + j];
+    M[idx] = (T)v;
+  }
+}
+
 // Shifted banded Cholesky solves (T + mu_j I) Z_j = E_j, E_j = the nrhs columns of rhs
 // starting at column rhs_col[j] (rhs: n x ncol column-major, ld n). Two kernels:
 //   k_band_factor: one CTA per shift j factors T + mu_j I (band storage, bw
@@ -376,6 +392,16 @@ cudaError_t launch_chol_inv(int m, const double* G, double rank_tol, double* wor
                             int* keep, int* rank, cudaStream_t st) {
   if (m < 1 || m > 256) return cudaErrorInvalidValue;
   k_chol_inv<<<1, kCholThreads, 0, st>>>(m, G, rank_tol, work, R, Rinv, keep, rank);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_three_term(int is_f64, int m, int first, const double* A, const double* B, void* M,
+                              cudaStream_t st) {
+  const int g = (2 * m * m + 255) / 256;
+  if (is_f64)
+    k_three_term<double><<<g, 256, 0, st>>>(m, first, A, B, (double*)M);
+  else
+    k_three_term<float><<<g, 256, 0, st>>>(m, first, A, B, (float*)M);
   return cudaGetLastError();
 }
 
