@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--sample-m", type=int, default=256)
     ap.add_argument("--sample-loads", type=int, default=16)
     ap.add_argument("--sample-inner", default="f32x2", choices=["f32x2", "fp32", "fp64"])
-    ap.add_argument("--sample-nugget", type=float, default=SAMPLE_NUGGET)
+    ap.add_argument("--sample-nugget", type=float, default=None)
+    ap.add_argument("--sample-operator", default="stored", choices=["stored", "rbf"])
     ap.add_argument("--dense-d", type=int, default=16384)
     ap.add_argument("--dense-m", type=int, default=33)
     ap.add_argument("--batch", type=int, default=512)
@@ -618,12 +619,20 @@ def run_sample(args, world, rank, local, dev):
     from paper_2501_18717_gb300 import bk
 
     d, m = args.sample_d, args.sample_m
+    onfly = args.sample_operator == "rbf"
+    if args.sample_nugget is None:
+        # the literal nugget is well posed for the exactly formed kernel only (R14)
+        args.sample_nugget = 1e-6 if onfly else SAMPLE_NUGGET
     t0 = time.perf_counter()
     pts = W.rbf_points(SAMPLE_SEED, d)
-    ld = (d + 31) // 32 * 32
-    Kbuf = torch.zeros((d, ld), dtype=torch.float32, device=dev)
-    Kbuf[:, :d] = W.rbf_kernel_torch(pts, dev)
-    K = Kbuf[:, :d]
+    if onfly:
+        K = None
+        pts_d = torch.from_numpy(np.ascontiguousarray(pts)).to(dev)
+    else:
+        ld = (d + 31) // 32 * 32
+        Kbuf = torch.zeros((d, ld), dtype=torch.float32, device=dev)
+        Kbuf[:, :d] = W.rbf_kernel_torch(pts, dev)
+        K = Kbuf[:, :d]
     B = torch.from_numpy(W.sample_block(SAMPLE_SEED, d, m)).to(dev)  # column-major d x m
     Bt = B.T.contiguous()  # (m, d) row-major = d x m column-major
     S = torch.zeros((m, d), dtype=torch.float64, device=dev)
@@ -632,7 +641,7 @@ def run_sample(args, world, rank, local, dev):
     ctx = bk.Context(local)
     stream = torch.cuda.Stream(dev)
     ctx.set_stream(stream.cuda_stream)
-    op = bk.dense_operator(K)
+    op = bk.rbf_operator(pts_d, 0.2) if onfly else bk.dense_operator(K)
 
     def opts(profile=0):
         return bk.default_opts(tol=1e-4, inner=args.sample_inner, check_every=4, max_loads=args.sample_loads,
@@ -676,14 +685,15 @@ def run_sample(args, world, rank, local, dev):
     peak_tf = fp32_peak_tflops(sm_mhz)
     op_tf = 2.0 * d * d * m / (groups["operator"]["avg_ms"] / 1e3) / 1e12 if groups["operator"]["calls"] else None
     # compensated FP32-pair products issue about 11 FP32 instructions per multiply-add
-    issue = (11.0 if args.sample_inner == "f32x2" else 1.0)
+    # (12 with both operands split, on the fly)
+    issue = 12.0 if onfly else (11.0 if args.sample_inner == "f32x2" else 1.0)
     peak_hbm, peak_src = measured_peaks()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the FP64 oracle's block-Lanczos (full reorthogonalisation) on the stored K
-        # promoted to FP64, timed for a bounded number of steps
+        # promoted to FP64 (or the FP64 kernel matrix), timed for a bounded number of steps
         from oracle import lanczos, operators
-        Kh = K.cpu().numpy()
+        Kh = W.rbf_kernel(pts) if onfly else K.cpu().numpy()
         op64 = operators.Dense(Kh)
         del Kh
         Bh = B.cpu().numpy()
@@ -707,16 +717,21 @@ def run_sample(args, world, rank, local, dev):
             "value": world * m / (ms / 1e3), "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64 blocks, " + ("compensated f32-pair" if args.sample_inner == "f32x2" else args.sample_inner)
-                     + " products of the f32-stored K, f64 Gram/band solves", "data": "synthetic",
-            "config": {"workload": f"rbf_sample_d{d}_m{m}_ls0.2_nugget{args.sample_nugget:g}_fp32_nquad32",
+            "dtype": "f64 blocks, " + ("compensated f32-pair" if args.sample_inner == "f32x2" or onfly
+                                       else args.sample_inner)
+                     + (" products of K formed on the fly in f64" if onfly else " products of the f32-stored K")
+                     + ", f64 Gram/band solves", "data": "synthetic",
+            "config": {"workload": f"rbf_sample_d{d}_m{m}_ls0.2_nugget{args.sample_nugget:g}_"
+                                   + ("onthefly_fp64entries" if onfly else "fp32") + "_nquad32",
                        "stop": "relative change of S <= 1e-4 between checks every 4 loads, or the load cap",
                        "inner": args.sample_inner,
                        "max_loads": args.sample_loads, "generator_s": gen_s,
-                       "l2": f"K {4.0 * d * d / 1e9:.1f} GB, larger than L2; no flush"},
+                       "l2": ("K formed on the fly (points 1 MB, block 82 MB); no flush" if onfly
+                              else f"K {4.0 * d * d / 1e9:.1f} GB, larger than L2; no flush")},
             "loads": [i.loads for i in infos], "last_change": [i.rel_residual for i in infos],
             "status": [i.status for i in infos], "groups": groups,
-            "roofline": {"bound": "alu", "kernel": f"dense load K P (k_tsm nn, {args.sample_inner})",
+            "roofline": {"bound": "alu", "kernel": ("on-the-fly kernel load K P (k_rbf, f32 pairs)" if onfly
+                                                    else f"dense load K P (k_tsm nn, {args.sample_inner})"),
                          "achieved": op_tf, "peak": peak_tf / issue, "unit": "TFLOP/s",
                          "frac": (op_tf * issue / peak_tf) if op_tf else None,
                          "traffic": None,

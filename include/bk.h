@@ -54,7 +54,7 @@ typedef enum {
   BK_ERR_TOO_LARGE = 9     /* the call needs more than the fixed static scratch holds */
 } bk_status;
 
-typedef enum { BK_DENSE = 0, BK_CSR = 1, BK_GRAM = 2 } bk_op_kind;
+typedef enum { BK_DENSE = 0, BK_CSR = 1, BK_GRAM = 2, BK_RBF = 3 } bk_op_kind;
 typedef enum { BK_F64 = 0, BK_F32 = 1 } bk_dtype;
 
 /* Precision of the inner block-CG iteration (block vectors, block products,
@@ -72,6 +72,12 @@ typedef enum { BK_PREC_FP64 = 0, BK_PREC_FP32 = 1, BK_PREC_F32X2 = 2 } bk_prec;
  *   BK_GRAM:  A = Z^T Z applied matrix-free as Z^T (Z P) (ridge regression, Sec. 1);
  *             vals is Z, rows x cols row-major with leading dimension ld; d = cols.
  *             Accepted by bk_ridge_path and bk_sample.
+ *   BK_RBF:   K_ij = exp(-||x_i - x_j||^2 / (2 param^2)) formed on the fly, never stored
+ *             (the matrix-free access mode of Sec. 1): vals is d points of 3 FP64
+ *             coordinates, row stride ld >= 3, rows = cols = d, dtype BK_F64, param > 0
+ *             the lengthscale. Entries in FP64 (library exp), products in compensated
+ *             FP32 pairs (about 2^-44). Accepted by bk_sample and bk_sample_isqrt with
+ *             FP64 blocks (inner BK_PREC_FP64 or BK_PREC_F32X2).
  *   dtype gives the element type of vals. A must be symmetric positive definite
  *   (or positive semi-definite with mu > 0); the library does not check symmetry. */
 typedef struct {
@@ -82,6 +88,7 @@ typedef struct {
   const int32_t* rowptr;
   const int32_t* colidx;
   int64_t nnz;
+  double param;           /* BK_RBF: the lengthscale; ignored by the other kinds */
 } bk_operator;
 
 typedef struct {

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libbk.so")
 
 BK_OK, BK_ERR_ARG, BK_ERR_CUDA, BK_ERR_OOM, BK_NOT_CONVERGED, BK_BREAKDOWN, BK_STAGNATED, BK_TIMEOUT, \
     BK_ERR_UNSUPPORTED, BK_ERR_TOO_LARGE = range(10)
-BK_DENSE, BK_CSR, BK_GRAM = 0, 1, 2
+BK_DENSE, BK_CSR, BK_GRAM, BK_RBF = 0, 1, 2, 3
 BK_F64, BK_F32 = 0, 1
 BK_PREC_FP64, BK_PREC_FP32, BK_PREC_F32X2 = 0, 1, 2
 
@@ -35,7 +35,8 @@ EXPORTS = ("bk_default_opts", "bk_create", "bk_destroy", "bk_set_stream", "bk_st
 class Operator(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("dtype", ctypes.c_int32), ("rows", ctypes.c_int64),
                 ("cols", ctypes.c_int64), ("ld", ctypes.c_int64), ("vals", ctypes.c_void_p),
-                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("nnz", ctypes.c_int64)]
+                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("nnz", ctypes.c_int64),
+                ("param", ctypes.c_double)]
 
 
 class Opts(ctypes.Structure):
@@ -211,6 +212,16 @@ def csr_operator(rowptr, colidx, vals) -> OperatorRef:
     pv, kv = _ptr(vals)
     op = Operator(BK_CSR, _dtype_code(vals), d, d, 0, pv, pr, pc, vals.shape[0])
     return OperatorRef(op, [kr, kc, kv])
+
+
+def rbf_operator(points, lengthscale: float) -> OperatorRef:
+    """K_ij = exp(-||x_i - x_j||^2 / (2 lengthscale^2)) formed on the fly from d points
+    (d x 3 float64, row-major); never stored."""
+    d = points.shape[0]
+    ld = points.stride(0) if hasattr(points, "stride") and callable(points.stride) else points.strides[0] // points.itemsize
+    p, k = _ptr(points)
+    op = Operator(BK_RBF, _dtype_code(points), d, d, ld, p, None, None, 0, float(lengthscale))
+    return OperatorRef(op, [k])
 
 
 def gram_operator(Z) -> OperatorRef:

@@ -179,6 +179,10 @@ cudaError_t launch_gemv_t(int64_t d, int r, const double* U, int64_t ldu, const 
                           cudaStream_t st);
 cudaError_t launch_gemv_n(int64_t d, int r, const double* U, int64_t ldu, const double* c, double* z,
                           cudaStream_t st);
+// ---- on-the-fly RBF kernel (k_rbf.cu): Y = K X, K_ij = exp(-|x_i - x_j|^2 / (2 l^2))
+// in FP64 entries and compensated FP32-pair products; X, Y d x N column-major FP64.
+cudaError_t launch_rbf_apply(int64_t d, int N, const double* pts, int64_t ldp, double lengthscale, const double* X,
+                             int64_t ldx, double* Y, int64_t ldy, cudaStream_t st);
 // ---- block-Lanczos drivers (k_krylov.cu)
 cudaError_t launch_e1r0(int n, int mb, const double* R0, double* rhs, cudaStream_t st);
 cudaError_t launch_chol_inv(int m, const double* G, double rank_tol, double* work, double* R, double* Rinv,

@@ -25,6 +25,7 @@ struct LzOp {
   int64_t d = 0, nrows = 0, ld = 0;
   const void* vals = nullptr;
   int vals_f64 = 0;
+  double param = 0.0;           // BK_RBF: lengthscale (FP64 blocks only)
   const int* rowptr = nullptr;  // BK_CSR (FP64 blocks only)
   const int* colidx = nullptr;
   int64_t nnz = 0;
@@ -163,6 +164,11 @@ struct Lanczos {
       if ((e = ws_get(c, WS_TSM, wb, &wk)) != cudaSuccess) return e;
       return bk::launch_tsm_tn(0, op.nrows, d, nc, A, op.ld, V, ldv, 1.0, 0.0, Y, ldy, wk, wb, c->sms, st);
     }
+    if (op.kind == BK_RBF) {
+      if (!is64) return cudaErrorInvalidValue;
+      return bk::launch_rbf_apply(d, nc, (const double*)op.vals, op.ld, op.param, (const double*)X, ldx, (double*)Y,
+                                  ldy, st);
+    }
     if (op.kind == BK_CSR) {
       if (!is64) return cudaErrorInvalidValue;
       return bk::launch_csr_cols(af, d, op.rowptr, op.colidx, op.vals, nc, (const double*)X, ldx, (double*)Y, ldy,
@@ -268,6 +274,16 @@ bk_status check_lz_operator(const bk_operator* A, LzOp* o) {
     o->nrows = 0;
     return BK_OK;
   }
+  if (A->kind == BK_RBF) {
+    if (A->rows <= 0 || A->rows != A->cols || A->ld < 3 || !(A->param > 0.0)) return BK_ERR_ARG;
+    if (A->dtype != BK_F64) return BK_ERR_UNSUPPORTED;
+    o->kind = BK_RBF;
+    o->d = A->rows;
+    o->ld = A->ld;
+    o->nrows = 0;
+    o->param = A->param;
+    return BK_OK;
+  }
   if (A->kind == BK_GRAM) {
     if (A->rows <= 0 || A->cols <= 0 || A->ld < A->cols) return BK_ERR_ARG;
     o->kind = BK_GRAM;
@@ -283,6 +299,13 @@ bk_status check_lz_operator(const bk_operator* A, LzOp* o) {
 cudaError_t stage_lz_values(bk_ctx* c, const bk_operator* A, LzOp* o, int want_f64, const void** staged) {
   const size_t es = A->dtype == BK_F64 ? 8 : 4;
   const int64_t rows = A->rows;
+  if (A->kind == BK_RBF) {  // the points (FP64, d x 3 with row stride ld)
+    const void* dv = nullptr;
+    cudaError_t e = stage_in(c, WS_OP_VALS, A->vals, ((size_t)(rows - 1) * A->ld + 3) * 8, &dv);
+    o->vals = dv;
+    *staged = dv;
+    return e;
+  }
   const size_t bytes = ((size_t)(rows - 1) * A->ld + A->cols) * es;
   const void* dv = nullptr;
   cudaError_t e = stage_in(c, WS_OP_VALS, A->vals, bytes, &dv);
@@ -309,6 +332,7 @@ cudaError_t apply_fp64(bk_ctx* c, const LzOp& o, const double* X, int64_t ld, in
                        bool allow_df) {
   if (o.kind == BK_CSR)
     return bk::launch_csr_cols(o.vals_f64, o.d, o.rowptr, o.colidx, o.vals, L, X, ld, AX, ld, c->stream);
+  if (o.kind == BK_RBF) return bk::launch_rbf_apply(o.d, L, (const double*)o.vals, o.ld, o.param, X, ld, AX, ld, c->stream);
   if (allow_df && !o.vals_f64 && bk::tsm_supported(o.vals, o.ld, X, ld, 1)) {
     const float* A = (const float*)o.vals;
     if (o.kind == BK_DENSE) return bk::launch_tsm_nn(1, o.d, L, o.d, 1.0, A, o.ld, X, ld, 0.0, AX, ld, c->stream);
@@ -417,6 +441,7 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
   if (!(opts.tol > 0.0) || opts.sketch < 0 || opts.max_loads < 1 || opts.max_refine < 1) return BK_ERR_ARG;
   if (opts.inner != BK_PREC_FP64 && opts.inner != BK_PREC_FP32 && opts.inner != BK_PREC_F32X2)
     return BK_ERR_UNSUPPORTED;
+  if (o.kind == BK_RBF && opts.inner == BK_PREC_FP32) return BK_ERR_UNSUPPORTED;
   std::vector<double> hmu(L);
   BK_CK(cudaSetDevice(c->device));
   cudaStream_t st = c->stream;
@@ -644,6 +669,7 @@ bk_status sample_driver(bk_ctx* c, const bk_operator* Kop, double nugget, int32_
   const int is64 = opts.inner != BK_PREC_FP32;
   const int64_t d = o.d;
   if (m > d) return BK_ERR_ARG;
+  if (o.kind == BK_RBF && !is64) return BK_ERR_UNSUPPORTED;
   BK_CK(cudaSetDevice(c->device));
   cudaStream_t st = c->stream;
   cudaEvent_t ev0, ev1;

@@ -1,0 +1,149 @@
+// Matrix-free RBF kernel operator (the access mode of Sec. 1 where only products with
+// A are available): Y = K X with K_ij = exp(-||x_i - x_j||^2 / (2 l^2)) formed on the
+// fly, never stored, for the sampling driver (Sec. 5, Def. blansq).
+//
+// Each K entry is computed in FP64 (the library exp) and split into an FP32 head and
+// tail; X (FP64) is split the same way; the products use compensated FP32-pair
+// arithmetic (the head-head product made exact by FMA, the two cross terms added to its
+// error, TwoSum accumulation), about 2^-44 relative to sum |K_ik x_k|. The entries are
+// therefore accurate to FP64 rounding, far below the nugget, unlike an FP32-stored K
+// whose rounding is a perturbation of norm ~3e-6 at 40,000 points.
+//
+// Tile: 384 threads as 12 row groups x 32 column groups; 48 rows x 256 columns per CTA
+// (4 rows x 8 columns per thread), so each exp serves all columns of a block of up to
+// 256. The K slice (48 rows x 16 points) is generated into shared memory per stage; the
+// X slice (16 rows x 256 columns) is split into head and tail in shared memory.
+#include <algorithm>
+
+#include "bk_common.cuh"
+
+namespace bk {
+namespace {
+
+constexpr int RB_TH = 384, RB_RG = 12, RB_BM = 4 * RB_RG, RB_BN = 256, RB_BK = 16, RB_NPT = 8;
+constexpr int RB_LDK = RB_BM + 4, RB_LDX = RB_BN + 4;
+static_assert((RB_BM * RB_BK) % RB_TH == 0, "whole K-slice entries per thread");
+
+__device__ __forceinline__ void dd_mac(float& s, float& c, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ void split_d(double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+
+// X: d x N column-major (ldx) FP64; Y likewise (ldy); pts: d points of 3 coordinates,
+// row stride ldp (FP64). h = 1 / (2 l^2).
+__global__ void __launch_bounds__(RB_TH, 1) k_rbf_apply(int64_t d, int N, const double* __restrict__ pts,
+                                                        int64_t ldp, double h, const double* __restrict__ X,
+                                                        int64_t ldx, double* __restrict__ Y, int64_t ldy) {
+  extern __shared__ __align__(16) float sm[];
+  float* sKh = sm;                              // [RB_BK][RB_LDK]
+  float* sKl = sKh + RB_BK * RB_LDK;
+  float* sXh = sKl + RB_BK * RB_LDK;            // [RB_BK][RB_LDX]
+  float* sXl = sXh + RB_BK * RB_LDX;
+  double* sP = reinterpret_cast<double*>(sXl + RB_BK * RB_LDX);  // this CTA's row points
+  const int tid = threadIdx.x, rg = tid >> 5, cg = tid & 31;  // rg < RB_RG
+  const int64_t i0 = (int64_t)blockIdx.x * RB_BM;
+  const int j0 = blockIdx.y * RB_BN;
+  for (int q = tid; q < RB_BM * 3; q += RB_TH) {
+    const int r = q / 3, c = q % 3;
+    sP[q] = (i0 + r < d) ? pts[(i0 + r) * ldp + c] : 0.0;
+  }
+  float s[4][RB_NPT], cc[4][RB_NPT];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < RB_NPT; ++v) s[u][v] = cc[u][v] = 0.f;
+  __syncthreads();
+  for (int64_t k0 = 0; k0 < d; k0 += RB_BK) {
+    // K slice: 48 rows x 16 points, 2 entries per thread
+#pragma unroll
+    for (int e = 0; e < (RB_BM * RB_BK) / RB_TH; ++e) {
+      const int q = tid + e * RB_TH;
+      const int r = q % RB_BM, kk = q / RB_BM;
+      const int64_t gk = k0 + kk;
+      double kv = 0.0;
+      if (i0 + r < d && gk < d) {
+        const double dx = sP[r * 3] - pts[gk * ldp];
+        const double dy = sP[r * 3 + 1] - pts[gk * ldp + 1];
+        const double dz = sP[r * 3 + 2] - pts[gk * ldp + 2];
+        kv = exp(-h * fma(dx, dx, fma(dy, dy, dz * dz)));
+      }
+      float kh, kl;
+      split_d(kv, kh, kl);
+      sKh[kk * RB_LDK + r] = kh;
+      sKl[kk * RB_LDK + r] = kl;
+    }
+    // X slice: 16 rows x 256 columns
+    for (int q = tid; q < RB_BK * RB_BN; q += RB_TH) {
+      const int kk = q & (RB_BK - 1), j = q >> 4;
+      const int64_t gk = k0 + kk;
+      const double xv = (gk < d && j0 + j < N) ? X[(int64_t)(j0 + j) * ldx + gk] : 0.0;
+      float xh, xl;
+      split_d(xv, xh, xl);
+      sXh[kk * RB_LDX + j] = xh;
+      sXl[kk * RB_LDX + j] = xl;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int kk = 0; kk < RB_BK; ++kk) {
+      float ah[4], al[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ah[u] = sKh[kk * RB_LDK + rg + RB_RG * u];
+        al[u] = sKl[kk * RB_LDK + rg + RB_RG * u];
+      }
+#pragma unroll
+      for (int v = 0; v < RB_NPT; ++v) {
+        const float bh = sXh[kk * RB_LDX + cg + 32 * v];
+        const float bl = sXl[kk * RB_LDX + cg + 32 * v];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dd_mac(s[u][v], cc[u][v], ah[u], al[u], bh, bl);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t i = i0 + rg + RB_RG * u;
+    if (i >= d) continue;
+#pragma unroll
+    for (int v = 0; v < RB_NPT; ++v) {
+      const int j = j0 + cg + 32 * v;
+      if (j < N) Y[(int64_t)j * ldy + i] = (double)s[u][v] + (double)cc[u][v];
+    }
+  }
+}
+
+constexpr size_t rbf_smem() {
+  return (size_t)2 * RB_BK * RB_LDK * 4 + (size_t)2 * RB_BK * RB_LDX * 4 + (size_t)RB_BM * 3 * 8;
+}
+
+}  // namespace
+
+cudaError_t launch_rbf_apply(int64_t d, int N, const double* pts, int64_t ldp, double lengthscale, const double* X,
+                             int64_t ldx, double* Y, int64_t ldy, cudaStream_t st) {
+  if (d <= 0 || N <= 0) return cudaSuccess;
+  if (!(lengthscale > 0.0) || ldp < 3) return cudaErrorInvalidValue;
+  const size_t smem = rbf_smem();
+  cudaError_t e = cudaFuncSetAttribute(k_rbf_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t mt = (d + RB_BM - 1) / RB_BM;
+  const int nt = (N + RB_BN - 1) / RB_BN;
+  if (mt > 0x7fffffff || nt > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)mt, (unsigned)nt);
+  k_rbf_apply<<<grid, RB_TH, smem, st>>>(d, N, pts, ldp, 1.0 / (2.0 * lengthscale * lengthscale), X, ldx, Y, ldy);
+  return cudaGetLastError();
+}
+
+}  // namespace bk

@@ -123,3 +123,45 @@ def test_isqrt_converges(bk, ctx, d, m, nug, inner, tol):
         lam = np.linalg.eigvalsh(K.astype(np.float64)) + nug
         tol = 1e-13 * lam[-1] / lam[0]
     assert err <= tol, (err, tol, info.as_dict())
+
+
+def test_rbf_operator_exact_integral_on_same_basis(bk, ctx):
+    """The on-the-fly RBF operator (K never stored, entries in FP64): at a fixed number
+    of loads the sample equals the oracle's exact integral on the basis built from the
+    FP64 kernel matrix, so the operator matches K to the pair arithmetic's accuracy."""
+    d, m = 333, 12
+    pts = W.rbf_points(W.BASE_SEED + 34, d)
+    K = W.rbf_kernel(pts)
+    nug = 1e-2
+    B = W.sample_block(W.BASE_SEED + 34, d, m)
+    op = bk.rbf_operator(torch.from_numpy(pts).to("cuda:0"), 0.2)
+    for t in [2, 4]:
+        S = np.zeros((d, m), order="F")
+        bk.sample(ctx, op, nug, B, S, 32, bk.default_opts(tol=1e-14, inner="f32x2", max_loads=t, check_every=100),
+                  check=False)
+        ref = lanczos.sqrt_iterate(lanczos.block_lanczos(K + nug * np.eye(d), B, t))
+        assert np.linalg.norm(S - ref) / np.linalg.norm(ref) < 1e-9, t
+
+
+@pytest.mark.parametrize("fn", ["sqrt", "isqrt"])
+def test_rbf_operator_subset_literal_nugget(bk, ctx, fn):
+    """The sampling validation problem with the kernel formed on the fly instead of
+    stored in FP32: the first 2000 points, 256 samples, the configuration's nugget 1e-6,
+    against the oracle's eigendecomposition of the FP64 kernel. Pair-arithmetic error
+    about 1e-13 ||K||, amplified by at most sqrt(kappa) (square root) or kappa (inverse
+    square root) relative."""
+    d, m, nug = 2000, 256, 1e-6
+    pts = W.rbf_points(W.BASE_SEED + 4, 40000)[:d].copy()
+    K = W.rbf_kernel(pts)
+    B = W.sample_block(W.BASE_SEED + 4, 40000, m)[:d].copy(order="F")
+    S = np.zeros((d, m), order="F")
+    call = bk.sample if fn == "sqrt" else bk.sample_isqrt
+    info = call(ctx, bk.rbf_operator(torch.from_numpy(pts).to("cuda:0"), 0.2), nug, B, S, 32,
+                bk.default_opts(tol=1e-10, inner="f32x2", check_every=2, max_loads=64), check=False)
+    assert info.status == bk.BK_OK, info.as_dict()
+    ref = (direct.sqrtm_apply if fn == "sqrt" else direct.isqrtm_apply)(K, B, shift=nug)
+    lam = np.linalg.eigvalsh(K) + nug
+    kap = lam[-1] / lam[0]
+    tol = 1e-13 * (np.sqrt(kap) if fn == "sqrt" else kap)
+    err = np.linalg.norm(S - ref) / np.linalg.norm(ref)
+    assert err <= max(tol, 1e-9), (err, tol, info.as_dict())
