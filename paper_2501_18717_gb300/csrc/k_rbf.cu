@@ -42,16 +42,16 @@ __device__ __forceinline__ void split_d(double v, float& h, float& l) {
 }
 
 // X: d x N column-major (ldx) FP64; Y likewise (ldy); pts: d points of 3 coordinates,
-// row stride ldp (FP64). h = 1 / (2 l^2).
+// row stride ldp (FP64). h = 1 / (2 l^2). The slices are double buffered: each thread
+// builds its part of slice s + 1 (FP64 exp, FP64 splits) and then runs its products on
+// slice s, with one barrier per slice, so the FP64 work of some warps overlaps the FP32
+// multiply-adds of others.
 __global__ void __launch_bounds__(RB_TH, 1) k_rbf_apply(int64_t d, int N, const double* __restrict__ pts,
                                                         int64_t ldp, double h, const double* __restrict__ X,
                                                         int64_t ldx, double* __restrict__ Y, int64_t ldy) {
   extern __shared__ __align__(16) float sm[];
-  float* sKh = sm;                              // [RB_BK][RB_LDK]
-  float* sKl = sKh + RB_BK * RB_LDK;
-  float* sXh = sKl + RB_BK * RB_LDK;            // [RB_BK][RB_LDX]
-  float* sXl = sXh + RB_BK * RB_LDX;
-  double* sP = reinterpret_cast<double*>(sXl + RB_BK * RB_LDX);  // this CTA's row points
+  constexpr int KS = RB_BK * RB_LDK, XS = RB_BK * RB_LDX, STAGE = 2 * KS + 2 * XS;
+  double* sP = reinterpret_cast<double*>(sm + 2 * STAGE);  // this CTA's row points
   const int tid = threadIdx.x, rg = tid >> 5, cg = tid & 31;  // rg < RB_RG
   const int64_t i0 = (int64_t)blockIdx.x * RB_BM;
   const int j0 = blockIdx.y * RB_BN;
@@ -65,7 +65,12 @@ __global__ void __launch_bounds__(RB_TH, 1) k_rbf_apply(int64_t d, int N, const 
 #pragma unroll
     for (int v = 0; v < RB_NPT; ++v) s[u][v] = cc[u][v] = 0.f;
   __syncthreads();
-  for (int64_t k0 = 0; k0 < d; k0 += RB_BK) {
+
+  auto build = [&](int64_t k0, int buf) {
+    float* sKh = sm + buf * STAGE;
+    float* sKl = sKh + KS;
+    float* sXh = sKl + KS;
+    float* sXl = sXh + XS;
     // K slice: 48 rows x 16 points, 2 entries per thread
 #pragma unroll
     for (int e = 0; e < (RB_BM * RB_BK) / RB_TH; ++e) {
@@ -94,7 +99,18 @@ __global__ void __launch_bounds__(RB_TH, 1) k_rbf_apply(int64_t d, int N, const 
       sXh[kk * RB_LDX + j] = xh;
       sXl[kk * RB_LDX + j] = xl;
     }
-    __syncthreads();
+  };
+
+  const int64_t nst = (d + RB_BK - 1) / RB_BK;
+  build(0, 0);
+  __syncthreads();
+  for (int64_t st = 0; st < nst; ++st) {
+    const int buf = (int)(st & 1);
+    if (st + 1 < nst) build((st + 1) * RB_BK, buf ^ 1);
+    const float* sKh = sm + buf * STAGE;
+    const float* sKl = sKh + KS;
+    const float* sXh = sKl + KS;
+    const float* sXl = sXh + XS;
 #pragma unroll 2
     for (int kk = 0; kk < RB_BK; ++kk) {
       float ah[4], al[4];
@@ -111,7 +127,7 @@ __global__ void __launch_bounds__(RB_TH, 1) k_rbf_apply(int64_t d, int N, const 
         for (int u = 0; u < 4; ++u) dd_mac(s[u][v], cc[u][v], ah[u], al[u], bh, bl);
       }
     }
-    __syncthreads();
+    __syncthreads();  // slice st + 1 complete; slice st free for st + 2
   }
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -126,7 +142,7 @@ __global__ void __launch_bounds__(RB_TH, 1) k_rbf_apply(int64_t d, int N, const 
 }
 
 constexpr size_t rbf_smem() {
-  return (size_t)2 * RB_BK * RB_LDK * 4 + (size_t)2 * RB_BK * RB_LDX * 4 + (size_t)RB_BM * 3 * 8;
+  return (size_t)2 * (2 * RB_BK * RB_LDK + 2 * RB_BK * RB_LDX) * 4 + (size_t)RB_BM * 3 * 8;
 }
 
 }  // namespace
