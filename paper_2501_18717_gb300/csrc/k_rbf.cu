@@ -2,8 +2,12 @@
 // A are available): Y = K X with K_ij = exp(-||x_i - x_j||^2 / (2 l^2)) formed on the
 // fly, never stored, for the sampling driver (Sec. 5, Def. blansq).
 //
-// Each K entry is computed in FP64 (the library exp) and split into an FP32 head and
-// tail; X (FP64) is split the same way; the products use compensated FP32-pair
+// Each K entry exp(t), t = -||x_i - x_j||^2 / (2 l^2) formed in FP64, is evaluated in
+// double-float arithmetic (pairs of FP32): Cody-Waite reduction t = k ln2 + r in FP64,
+// |r| <= ln2 / 2, then the Taylor polynomial of exp(r) to degree 14 by Horner's rule in
+// pair arithmetic (Dekker's product and Knuth's sum, error-free by FMA), scaled by 2^k;
+// relative error about 2^-46, and the entry comes out as the head and tail the products
+// need. X (FP64) is split into head and tail; the products use compensated FP32-pair
 // arithmetic (the head-head product made exact by FMA, the two cross terms added to its
 // error, TwoSum accumulation), about 2^-44 relative to sum |K_ik x_k|. The entries are
 // therefore accurate to FP64 rounding, far below the nugget, unlike an FP32-stored K
@@ -34,6 +38,71 @@ __device__ __forceinline__ void dd_mac(float& s, float& c, float ah, float al, f
   const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
   s = t;
   c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// ---- double-float (FP32 pair) arithmetic; the _rn intrinsics keep the compiler from
+// contracting the error-free transformations into FMAs
+__device__ __forceinline__ void df_fast_two_sum(float a, float b, float& s, float& e) {  // |a| >= |b|
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  df_fast_two_sum(p, e, ph, pl);
+}
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  const float s = __fadd_rn(ah, bh);
+  const float bb = __fsub_rn(s, ah);
+  float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  df_fast_two_sum(s, e, sh, sl);
+}
+
+// Taylor coefficients 1 / k!, k = 0..14, as FP32 head and tail
+struct ExpCoef {
+  float h[15], l[15];
+};
+constexpr ExpCoef make_exp_coef() {
+  ExpCoef c{};
+  double f = 1.0;
+  for (int k = 0; k < 15; ++k) {
+    if (k > 0) f /= (double)k;
+    c.h[k] = (float)f;
+    c.l[k] = (float)(f - (double)c.h[k]);
+  }
+  return c;
+}
+__constant__ ExpCoef kExpCoef = make_exp_coef();
+
+// exp(t) for t <= 0 as a pair (h, l) of FP32 (0 below exp(-100)).
+__device__ __forceinline__ void exp_df(double t, float& h, float& l) {
+  if (t < -100.0) {
+    h = l = 0.f;
+    return;
+  }
+  // ln 2 split into a head of 32 significant bits (k * head is exact for |k| < 2^21)
+  // and the rest of its double value; the double's own rounding (1e-16 relative) moves
+  // r by at most |k| 1e-16, below the pair arithmetic's 2^-46
+  constexpr double kLn2 = 0.69314718055994530942;
+  constexpr double kLn2Hi = (double)(long long)(kLn2 * 4294967296.0) / 4294967296.0;
+  constexpr double kLn2Lo = kLn2 - kLn2Hi;
+  const double kd = rint(t * (1.0 / kLn2));
+  double r = fma(-kd, kLn2Hi, t);
+  r = fma(-kd, kLn2Lo, r);
+  const float rh = (float)r, rl = (float)(r - (double)rh);
+  float ph = kExpCoef.h[14], pl = kExpCoef.l[14];
+#pragma unroll
+  for (int k = 13; k >= 0; --k) {
+    float mh, ml;
+    df_mul(ph, pl, rh, rl, mh, ml);
+    df_add(mh, ml, kExpCoef.h[k], kExpCoef.l[k], ph, pl);
+  }
+  const int ki = (int)kd;
+  h = ldexpf(ph, ki);
+  l = ldexpf(pl, ki);
 }
 
 __device__ __forceinline__ void split_d(double v, float& h, float& l) {
@@ -77,15 +146,13 @@ __global__ void __launch_bounds__(RB_TH, 1) k_rbf_apply(int64_t d, int N, const 
       const int q = tid + e * RB_TH;
       const int r = q % RB_BM, kk = q / RB_BM;
       const int64_t gk = k0 + kk;
-      double kv = 0.0;
+      float kh = 0.f, kl = 0.f;
       if (i0 + r < d && gk < d) {
         const double dx = sP[r * 3] - pts[gk * ldp];
         const double dy = sP[r * 3 + 1] - pts[gk * ldp + 1];
         const double dz = sP[r * 3 + 2] - pts[gk * ldp + 2];
-        kv = exp(-h * fma(dx, dx, fma(dy, dy, dz * dz)));
+        exp_df(-h * fma(dx, dx, fma(dy, dy, dz * dz)), kh, kl);
       }
-      float kh, kl;
-      split_d(kv, kh, kl);
       sKh[kk * RB_LDK + r] = kh;
       sKl[kk * RB_LDK + r] = kl;
     }
