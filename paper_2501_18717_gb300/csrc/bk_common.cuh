@@ -151,15 +151,20 @@ cudaError_t launch_gemm_split(int is_f64, int64_t M, int64_t N, int64_t K, doubl
                               int64_t ldc, void* work, size_t work_bytes, int sms, cudaStream_t st);
 size_t gemm_split_work_bytes(int is_f64, int64_t M, int64_t N, int64_t K, int sms);
 // ---- tall-skinny products of the Lanczos drivers (k_tsm.cu)
-// df = 0: FP32 B / T and output; df = 1: FP64 B / T and output with compensated FP32
-// arithmetic (FP64-accurate for FP32 A / Z). A and Z must be 16-byte aligned with
-// leading dimensions a multiple of 4 floats (FP32 B / T likewise); tsm_supported checks.
-bool tsm_supported(const void* A, int64_t lda, const void* B, int64_t ldb, int b_f64);
+// df = 0: FP32 B / T (the *lo arguments unused) and FP32 output; df = 1: B / T is an
+// FP64 operand given as its FP32 head and tail (launch_split_f64, same leading
+// dimension), FP64 output with compensated FP32 arithmetic (FP64-accurate for FP32 A /
+// Z). Every FP32 array must be 16-byte aligned with a leading dimension that is a
+// multiple of 4 floats; tsm_supported checks one.
+bool tsm_supported(const void* A, int64_t lda);
+cudaError_t launch_split_f64(int64_t rows, int cols, const double* src, int64_t lds, float* hi, float* lo, int64_t ldd,
+                             cudaStream_t st);
 cudaError_t launch_tsm_nn(int df, int64_t M, int N, int64_t K, double alpha, const float* A, int64_t lda,
-                          const void* B, int64_t ldb, double beta, void* C, int64_t ldc, cudaStream_t st);
-cudaError_t launch_tsm_tn(int df, int64_t R, int64_t D, int N, const float* Z, int64_t ldz, const void* T,
-                          int64_t ldt, double alpha, double beta, void* Y, int64_t ldy, void* work, size_t work_bytes,
-                          int sms, cudaStream_t st);
+                          const float* B, const float* Blo, int64_t ldb, double beta, void* C, int64_t ldc,
+                          cudaStream_t st);
+cudaError_t launch_tsm_tn(int df, int64_t R, int64_t D, int N, const float* Z, int64_t ldz, const float* T,
+                          const float* Tlo, int64_t ldt, double alpha, double beta, void* Y, int64_t ldy, void* work,
+                          size_t work_bytes, int sms, cudaStream_t st);
 size_t tsm_tn_work_bytes(int64_t R, int64_t D, int N, int df, int sms);
 // ---- Nystrom PCG (k_pcg.cu), FP64
 cudaError_t launch_csr_cols(int vals_f64, int64_t d, const int* rowptr, const int* colidx, const void* vals, int nc,
@@ -180,9 +185,10 @@ cudaError_t launch_gemv_t(int64_t d, int r, const double* U, int64_t ldu, const 
 cudaError_t launch_gemv_n(int64_t d, int r, const double* U, int64_t ldu, const double* c, double* z,
                           cudaStream_t st);
 // ---- on-the-fly RBF kernel (k_rbf.cu): Y = K X, K_ij = exp(-|x_i - x_j|^2 / (2 l^2))
-// in FP64 entries and compensated FP32-pair products; X, Y d x N column-major FP64.
-cudaError_t launch_rbf_apply(int64_t d, int N, const double* pts, int64_t ldp, double lengthscale, const double* X,
-                             int64_t ldx, double* Y, int64_t ldy, cudaStream_t st);
+// accurate to about 2^-46, compensated FP32-pair products; X is given as the FP32 head
+// and tail of an FP64 block (launch_split_f64, ldx a multiple of 4), Y d x N FP64.
+cudaError_t launch_rbf_apply(int64_t d, int N, const double* pts, int64_t ldp, double lengthscale, const float* Xh,
+                             const float* Xl, int64_t ldx, double* Y, int64_t ldy, cudaStream_t st);
 // ---- block-Lanczos drivers (k_krylov.cu)
 cudaError_t launch_e1r0(int n, int mb, const double* R0, double* rhs, cudaStream_t st);
 cudaError_t launch_chol_inv(int m, const double* G, double rank_tol, double* work, double* R, double* Rinv,

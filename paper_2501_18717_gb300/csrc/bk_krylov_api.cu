@@ -72,6 +72,45 @@ struct Prof {
   }
 };
 
+// FP64-accurate products of FP32-stored values through the compensated tall-skinny
+// kernels: Y (d x nc, FP64) = A X (BK_DENSE) or Z^T (Z X) (BK_GRAM; V is an nrows x nc
+// FP64 scratch). Each FP64 operand is split once into FP32 head and tail arrays.
+cudaError_t df_apply(bk_ctx* c, const LzOp& o, const double* X, int64_t ldx, int nc, double* Y, int64_t ldy, double* V,
+                     int64_t ldv, cudaStream_t st) {
+  const int64_t lds = (o.d + 3) & ~int64_t(3);
+  const int64_t ldr = (o.nrows + 3) & ~int64_t(3);
+  const size_t need = (size_t)2 * lds * nc * 4 + (o.kind == BK_GRAM ? (size_t)2 * ldr * nc * 4 : 0) + 64;
+  void* wsv = nullptr;
+  cudaError_t e = ws_get(c, WS_SPLITB, need, &wsv);
+  if (e != cudaSuccess) return e;
+  float* Xh = (float*)wsv;
+  float* Xl = Xh + (size_t)lds * nc;
+  if ((e = bk::launch_split_f64(o.d, nc, X, ldx, Xh, Xl, lds, st)) != cudaSuccess) return e;
+  const float* A = (const float*)o.vals;
+  if (o.kind == BK_DENSE) return bk::launch_tsm_nn(1, o.d, nc, o.d, 1.0, A, o.ld, Xh, Xl, lds, 0.0, Y, ldy, st);
+  if ((e = bk::launch_tsm_nn(1, o.nrows, nc, o.d, 1.0, A, o.ld, Xh, Xl, lds, 0.0, V, ldv, st)) != cudaSuccess) return e;
+  float* Vh = Xl + (size_t)lds * nc;
+  float* Vl = Vh + (size_t)ldr * nc;
+  if ((e = bk::launch_split_f64(o.nrows, nc, V, ldv, Vh, Vl, ldr, st)) != cudaSuccess) return e;
+  void* wk = nullptr;
+  const size_t wb = bk::tsm_tn_work_bytes(o.nrows, o.d, nc, 1, c->sms);
+  if ((e = ws_get(c, WS_TSM, wb, &wk)) != cudaSuccess) return e;
+  return bk::launch_tsm_tn(1, o.nrows, o.d, nc, A, o.ld, Vh, Vl, ldr, 1.0, 0.0, Y, ldy, wk, wb, c->sms, st);
+}
+
+// Y (d x nc, FP64) = K X for the on-the-fly RBF operator (X split into FP32 head and tail).
+cudaError_t rbf_apply(bk_ctx* c, const LzOp& o, const double* X, int64_t ldx, int nc, double* Y, int64_t ldy,
+                      cudaStream_t st) {
+  const int64_t lds = (o.d + 3) & ~int64_t(3);
+  void* wsv = nullptr;
+  cudaError_t e = ws_get(c, WS_SPLITB, (size_t)2 * lds * nc * 4 + 64, &wsv);
+  if (e != cudaSuccess) return e;
+  float* Xh = (float*)wsv;
+  float* Xl = Xh + (size_t)lds * nc;
+  if ((e = bk::launch_split_f64(o.d, nc, X, ldx, Xh, Xl, lds, st)) != cudaSuccess) return e;
+  return bk::launch_rbf_apply(o.d, nc, (const double*)o.vals, o.ld, o.param, Xh, Xl, lds, Y, ldy, st);
+}
+
 // Block-Lanczos with full reorthogonalisation (classical Gram-Schmidt twice against
 // every previous block) and CholQR2 for the block QR (Sec. 3.2, Thm. cost). Blocks are
 // column-major with leading dimension ldq, in the precision of the run (FP32 or FP64);
@@ -146,28 +185,24 @@ struct Lanczos {
     cudaError_t e;
     const int af = op.vals_f64;  // 1: FP64 values, 0: FP32 values
     if (!is64 && af) return cudaErrorInvalidValue;  // FP32 runs use FP32 values
-    if (is64 && df && !af && bk::tsm_supported(op.vals, op.ld, X, ldx, 1)) {
+    if (is64 && df && !af && (op.kind == BK_DENSE || op.kind == BK_GRAM) && bk::tsm_supported(op.vals, op.ld))
+      return df_apply(c, op, (const double*)X, ldx, nc, (double*)Y, ldy, (double*)V, ldv, st);
+    if (!is64 && (op.kind == BK_DENSE || op.kind == BK_GRAM) && bk::tsm_supported(op.vals, op.ld) &&
+        bk::tsm_supported(X, ldx)) {
       const float* A = (const float*)op.vals;
-      if (op.kind == BK_DENSE) return bk::launch_tsm_nn(1, d, nc, d, 1.0, A, op.ld, X, ldx, 0.0, Y, ldy, st);
-      if ((e = bk::launch_tsm_nn(1, op.nrows, nc, d, 1.0, A, op.ld, X, ldx, 0.0, V, ldv, st)) != cudaSuccess) return e;
-      void* wk = nullptr;
-      const size_t wb = bk::tsm_tn_work_bytes(op.nrows, d, nc, 1, c->sms);
-      if ((e = ws_get(c, WS_TSM, wb, &wk)) != cudaSuccess) return e;
-      return bk::launch_tsm_tn(1, op.nrows, d, nc, A, op.ld, V, ldv, 1.0, 0.0, Y, ldy, wk, wb, c->sms, st);
-    }
-    if (!is64 && bk::tsm_supported(op.vals, op.ld, X, ldx, 0)) {
-      const float* A = (const float*)op.vals;
-      if (op.kind == BK_DENSE) return bk::launch_tsm_nn(0, d, nc, d, 1.0, A, op.ld, X, ldx, 0.0, Y, ldy, st);
-      if ((e = bk::launch_tsm_nn(0, op.nrows, nc, d, 1.0, A, op.ld, X, ldx, 0.0, V, ldv, st)) != cudaSuccess) return e;
+      const float* Xf = (const float*)X;
+      if (op.kind == BK_DENSE) return bk::launch_tsm_nn(0, d, nc, d, 1.0, A, op.ld, Xf, nullptr, ldx, 0.0, Y, ldy, st);
+      if ((e = bk::launch_tsm_nn(0, op.nrows, nc, d, 1.0, A, op.ld, Xf, nullptr, ldx, 0.0, V, ldv, st)) != cudaSuccess)
+        return e;
       void* wk = nullptr;
       const size_t wb = bk::tsm_tn_work_bytes(op.nrows, d, nc, 0, c->sms);
       if ((e = ws_get(c, WS_TSM, wb, &wk)) != cudaSuccess) return e;
-      return bk::launch_tsm_tn(0, op.nrows, d, nc, A, op.ld, V, ldv, 1.0, 0.0, Y, ldy, wk, wb, c->sms, st);
+      return bk::launch_tsm_tn(0, op.nrows, d, nc, A, op.ld, (const float*)V, nullptr, ldv, 1.0, 0.0, Y, ldy, wk, wb,
+                               c->sms, st);
     }
     if (op.kind == BK_RBF) {
       if (!is64) return cudaErrorInvalidValue;
-      return bk::launch_rbf_apply(d, nc, (const double*)op.vals, op.ld, op.param, (const double*)X, ldx, (double*)Y,
-                                  ldy, st);
+      return rbf_apply(c, op, (const double*)X, ldx, nc, (double*)Y, ldy, st);
     }
     if (op.kind == BK_CSR) {
       if (!is64) return cudaErrorInvalidValue;
@@ -332,17 +367,9 @@ cudaError_t apply_fp64(bk_ctx* c, const LzOp& o, const double* X, int64_t ld, in
                        bool allow_df) {
   if (o.kind == BK_CSR)
     return bk::launch_csr_cols(o.vals_f64, o.d, o.rowptr, o.colidx, o.vals, L, X, ld, AX, ld, c->stream);
-  if (o.kind == BK_RBF) return bk::launch_rbf_apply(o.d, L, (const double*)o.vals, o.ld, o.param, X, ld, AX, ld, c->stream);
-  if (allow_df && !o.vals_f64 && bk::tsm_supported(o.vals, o.ld, X, ld, 1)) {
-    const float* A = (const float*)o.vals;
-    if (o.kind == BK_DENSE) return bk::launch_tsm_nn(1, o.d, L, o.d, 1.0, A, o.ld, X, ld, 0.0, AX, ld, c->stream);
-    cudaError_t e = bk::launch_tsm_nn(1, o.nrows, L, o.d, 1.0, A, o.ld, X, ld, 0.0, Vw, o.nrows, c->stream);
-    if (e != cudaSuccess) return e;
-    void* wk = nullptr;
-    const size_t wb = bk::tsm_tn_work_bytes(o.nrows, o.d, L, 1, c->sms);
-    if ((e = ws_get(c, WS_TSM, wb, &wk)) != cudaSuccess) return e;
-    return bk::launch_tsm_tn(1, o.nrows, o.d, L, A, o.ld, Vw, o.nrows, 1.0, 0.0, AX, ld, wk, wb, c->sms, c->stream);
-  }
+  if (o.kind == BK_RBF) return rbf_apply(c, o, X, ld, L, AX, ld, c->stream);
+  if (allow_df && !o.vals_f64 && (o.kind == BK_DENSE || o.kind == BK_GRAM) && bk::tsm_supported(o.vals, o.ld))
+    return df_apply(c, o, X, ld, L, AX, ld, Vw, o.nrows, c->stream);
   if (o.kind == BK_DENSE) return bk::launch_gemm(1, o.d, L, o.d, 1.0, o.vals, o.vals_f64, o.ld, 1, X, 1, ld, 0.0, AX,
                                                  ld, c->stream);
   cudaError_t e =

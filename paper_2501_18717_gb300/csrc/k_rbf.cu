@@ -105,19 +105,17 @@ __device__ __forceinline__ void exp_df(double t, float& h, float& l) {
   l = ldexpf(pl, ki);
 }
 
-__device__ __forceinline__ void split_d(double v, float& h, float& l) {
-  h = (float)v;
-  l = (float)(v - (double)h);
-}
 
-// X: d x N column-major (ldx) FP64; Y likewise (ldy); pts: d points of 3 coordinates,
-// row stride ldp (FP64). h = 1 / (2 l^2). The slices are double buffered: each thread
+// X: the FP32 head and tail (d x N column-major, ldx a multiple of 4, rows d..ldx-1
+// zero) of the FP64 block; Y: d x N column-major (ldy) FP64; pts: d points of 3
+// coordinates, row stride ldp (FP64). h = 1 / (2 l^2). The slices are double buffered: each thread
 // builds its part of slice s + 1 (FP64 exp, FP64 splits) and then runs its products on
 // slice s, with one barrier per slice, so the FP64 work of some warps overlaps the FP32
 // multiply-adds of others.
 __global__ void __launch_bounds__(RB_TH, 1) k_rbf_apply(int64_t d, int N, const double* __restrict__ pts,
-                                                        int64_t ldp, double h, const double* __restrict__ X,
-                                                        int64_t ldx, double* __restrict__ Y, int64_t ldy) {
+                                                        int64_t ldp, double h, const float* __restrict__ Xh,
+                                                        const float* __restrict__ Xl, int64_t ldx,
+                                                        double* __restrict__ Y, int64_t ldy) {
   extern __shared__ __align__(16) float sm[];
   constexpr int KS = RB_BK * RB_LDK, XS = RB_BK * RB_LDX, STAGE = 2 * KS + 2 * XS;
   double* sP = reinterpret_cast<double*>(sm + 2 * STAGE);  // this CTA's row points
@@ -156,15 +154,24 @@ __global__ void __launch_bounds__(RB_TH, 1) k_rbf_apply(int64_t d, int N, const 
       sKh[kk * RB_LDK + r] = kh;
       sKl[kk * RB_LDK + r] = kl;
     }
-    // X slice: 16 rows x 256 columns
-    for (int q = tid; q < RB_BK * RB_BN; q += RB_TH) {
-      const int kk = q & (RB_BK - 1), j = q >> 4;
-      const int64_t gk = k0 + kk;
-      const double xv = (gk < d && j0 + j < N) ? X[(int64_t)(j0 + j) * ldx + gk] : 0.0;
-      float xh, xl;
-      split_d(xv, xh, xl);
-      sXh[kk * RB_LDX + j] = xh;
-      sXl[kk * RB_LDX + j] = xl;
+    // X slice: 16 rows x 256 columns, 16-byte loads of 4 consecutive rows of a column
+    for (int q = tid; q < (RB_BK / 4) * RB_BN; q += RB_TH) {
+      const int c4 = q & 3, j = q >> 2;
+      const int64_t gk = k0 + 4 * c4;
+      float4 h4 = make_float4(0.f, 0.f, 0.f, 0.f), l4 = h4;
+      if (gk < ldx && j0 + j < N) {
+        h4 = *reinterpret_cast<const float4*>(Xh + (int64_t)(j0 + j) * ldx + gk);
+        l4 = *reinterpret_cast<const float4*>(Xl + (int64_t)(j0 + j) * ldx + gk);
+      }
+      const int kk = 4 * c4;
+      sXh[(kk + 0) * RB_LDX + j] = h4.x;
+      sXh[(kk + 1) * RB_LDX + j] = h4.y;
+      sXh[(kk + 2) * RB_LDX + j] = h4.z;
+      sXh[(kk + 3) * RB_LDX + j] = h4.w;
+      sXl[(kk + 0) * RB_LDX + j] = l4.x;
+      sXl[(kk + 1) * RB_LDX + j] = l4.y;
+      sXl[(kk + 2) * RB_LDX + j] = l4.z;
+      sXl[(kk + 3) * RB_LDX + j] = l4.w;
     }
   };
 
@@ -214,10 +221,11 @@ constexpr size_t rbf_smem() {
 
 }  // namespace
 
-cudaError_t launch_rbf_apply(int64_t d, int N, const double* pts, int64_t ldp, double lengthscale, const double* X,
-                             int64_t ldx, double* Y, int64_t ldy, cudaStream_t st) {
+cudaError_t launch_rbf_apply(int64_t d, int N, const double* pts, int64_t ldp, double lengthscale, const float* Xh,
+                             const float* Xl, int64_t ldx, double* Y, int64_t ldy, cudaStream_t st) {
   if (d <= 0 || N <= 0) return cudaSuccess;
-  if (!(lengthscale > 0.0) || ldp < 3) return cudaErrorInvalidValue;
+  if (!(lengthscale > 0.0) || ldp < 3 || (ldx & 3) || ldx < d || ((uintptr_t)Xh & 15) || ((uintptr_t)Xl & 15))
+    return cudaErrorInvalidValue;
   const size_t smem = rbf_smem();
   cudaError_t e = cudaFuncSetAttribute(k_rbf_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -225,7 +233,8 @@ cudaError_t launch_rbf_apply(int64_t d, int N, const double* pts, int64_t ldp, d
   const int nt = (N + RB_BN - 1) / RB_BN;
   if (mt > 0x7fffffff || nt > 65535) return cudaErrorInvalidValue;
   dim3 grid((unsigned)mt, (unsigned)nt);
-  k_rbf_apply<<<grid, RB_TH, smem, st>>>(d, N, pts, ldp, 1.0 / (2.0 * lengthscale * lengthscale), X, ldx, Y, ldy);
+  k_rbf_apply<<<grid, RB_TH, smem, st>>>(d, N, pts, ldp, 1.0 / (2.0 * lengthscale * lengthscale), Xh, Xl, ldx, Y,
+                                         ldy);
   return cudaGetLastError();
 }
 

@@ -12,7 +12,9 @@
 //
 // Two arithmetic modes share the tiles:
 //   FP32  B / T in FP32, FFMA accumulation, FP32 output (the Lanczos basis products).
-//   DF    B / T in FP64, split into FP32 head + tail; every product of the FP32 matrix
+//   DF    B / T in FP64, split once per product into FP32 head and tail arrays
+//         (launch_split_f64) that the kernels stage like FP32 operands; every product of
+//         the FP32 matrix
 //         entry with the head is made exact with an FMA (its rounding error is
 //         representable) and added to a compensated FP32 pair (Knuth's TwoSum), so the
 //         sums carry about 44 significant bits. This is the FP64-accurate operator of
@@ -77,8 +79,8 @@ struct TsCfg {
 // and tail, 2 x [NT][TS_LDK]).
 template <int NPT, bool DF>
 __global__ void __launch_bounds__(TS_TH, 3) k_tsm_nn(int64_t M, int N, int64_t K, double alpha, const float* __restrict__ A,
-                                                  int64_t lda, const void* __restrict__ Bv, int64_t ldb, double beta,
-                                                  void* Cv, int64_t ldc) {
+                                                  int64_t lda, const float* __restrict__ Bh, const float* __restrict__ Bl,
+                                                  int64_t ldb, double beta, void* Cv, int64_t ldc) {
   using Cfg = TsCfg<DF>;
   constexpr int RPT = Cfg::RPT, BM = Cfg::BM, NT = 8 * NPT;
   constexpr int A_FL = BM * TS_LDK, B_FL = (DF ? 2 : 1) * NT * TS_LDK, ST_FL = A_FL + B_FL;
@@ -114,31 +116,18 @@ __global__ void __launch_bounds__(TS_TH, 3) k_tsm_nn(int64_t M, int N, int64_t K
       cp16(sA + 16 * e * TS_LDK, ok ? src : A, ok ? bytes : 0);
     }
   };
+  // B (FP32), or the FP32 head and tail of an FP64 B (DF), into the stage's B area
   auto issue_b32 = [&](int s, int buf) {
     float* sB = smem + buf * ST_FL + A_FL + r0 * TS_LDK + c4 * 4;
-    const float* B = (const float*)Bv;
     const int64_t k = (int64_t)s * TS_BK + c4 * 4;
     const int bytes = clamp16((K - k) * 4);
 #pragma unroll 1
     for (int e = 0; e < EB; ++e) {
       if (r0 + 16 * e >= NT) break;
       const bool ok = (b_ok >> e & 1u) && bytes;
-      cp16(sB + 16 * e * TS_LDK, ok ? B + (int64_t)(j0 + r0 + 16 * e) * ldb + k : B, ok ? bytes : 0);
-    }
-  };
-  auto load_b64 = [&](int s, int buf) {  // DF: synchronous load, split into head / tail
-    float* sBh = smem + buf * ST_FL + A_FL;
-    float* sBl = sBh + NT * TS_LDK;
-    const double* B = (const double*)Bv;
-    const int64_t k0 = (int64_t)s * TS_BK;
-    for (int q = tid; q < NT * TS_BK; q += TS_TH) {
-      const int j = q >> 5, kk = q & 31;
-      const int64_t gk = k0 + kk;
-      const double v = ((j0 + j) < N && gk < K) ? B[(int64_t)(j0 + j) * ldb + gk] : 0.0;
-      float h, l;
-      split_f64(v, h, l);
-      sBh[j * TS_LDK + kk] = h;
-      sBl[j * TS_LDK + kk] = l;
+      const int64_t off = (int64_t)(j0 + r0 + 16 * e) * ldb + k;
+      cp16(sB + 16 * e * TS_LDK, ok ? Bh + off : Bh, ok ? bytes : 0);
+      if constexpr (DF) cp16(sB + NT * TS_LDK + 16 * e * TS_LDK, ok ? Bl + off : Bl, ok ? bytes : 0);
     }
   };
 
@@ -153,15 +142,14 @@ __global__ void __launch_bounds__(TS_TH, 3) k_tsm_nn(int64_t M, int N, int64_t K
 
   if (nst > 0) {
     issue_a(0, 0);
-    if constexpr (!DF) issue_b32(0, 0);
+    issue_b32(0, 0);
     cp_commit();
   }
   for (int s = 0; s < nst; ++s) {
     const int buf = s & 1;
-    if constexpr (DF) load_b64(s, buf);
     if (s + 1 < nst) {
       issue_a(s + 1, buf ^ 1);
-      if constexpr (!DF) issue_b32(s + 1, buf ^ 1);
+      issue_b32(s + 1, buf ^ 1);
       cp_commit();
       cp_wait_one();
     } else {
@@ -251,8 +239,8 @@ __global__ void __launch_bounds__(TS_TH, 3) k_tsm_nn(int64_t M, int N, int64_t K
 // head and tail).
 template <int NPT, bool DF>
 __global__ void __launch_bounds__(TS_TH, 3) k_tsm_tn(int64_t R, int64_t D, int N, int64_t rows_per_chunk,
-                                                  const float* __restrict__ Z, int64_t ldz, const void* __restrict__ Tv,
-                                                  int64_t ldt, void* Wv, int64_t ldw) {
+                                                  const float* __restrict__ Z, int64_t ldz, const float* __restrict__ Th,
+                                                  const float* __restrict__ Tl, int64_t ldt, void* Wv, int64_t ldw) {
   using Cfg = TsCfg<DF>;
   constexpr int RPT = Cfg::RPT, BD = Cfg::BM, NT = 8 * NPT, LDZ = BD + 4;
   constexpr int Z_FL = TS_BK * LDZ, T_FL = (DF ? 2 : 1) * NT * TS_LDK, ST_FL = Z_FL + T_FL;
@@ -281,9 +269,9 @@ __global__ void __launch_bounds__(TS_TH, 3) k_tsm_tn(int64_t R, int64_t D, int N
       cp16(sZ + ZR * e * LDZ, ok ? z_col + gi * ldz : Z, ok ? zbytes : 0);
     }
   };
+  // T (FP32), or the FP32 head and tail of an FP64 T (DF), into the stage's T area
   auto issue_t32 = [&](int s, int buf) {
     float* sT = smem + buf * ST_FL + Z_FL + rt * TS_LDK + c4 * 4;
-    const float* T = (const float*)Tv;
     const int64_t gi = r0 + (int64_t)s * TS_BK + c4 * 4;
     const int bytes = clamp16((r1 - gi) * 4);
 #pragma unroll
@@ -291,22 +279,9 @@ __global__ void __launch_bounds__(TS_TH, 3) k_tsm_tn(int64_t R, int64_t D, int N
       const int j = rt + 16 * e;
       if (j >= NT) break;
       const bool ok = (j0 + j) < N && bytes;
-      cp16(sT + 16 * e * TS_LDK, ok ? T + (int64_t)(j0 + j) * ldt + gi : T, ok ? bytes : 0);
-    }
-  };
-  auto load_t64 = [&](int s, int buf) {
-    float* sTh = smem + buf * ST_FL + Z_FL;
-    float* sTl = sTh + NT * TS_LDK;
-    const double* T = (const double*)Tv;
-    const int64_t i0 = r0 + (int64_t)s * TS_BK;
-    for (int q = tid; q < NT * TS_BK; q += TS_TH) {
-      const int j = q >> 5, ii = q & 31;
-      const int64_t gi = i0 + ii;
-      const double v = ((j0 + j) < N && gi < r1) ? T[(int64_t)(j0 + j) * ldt + gi] : 0.0;
-      float h, l;
-      split_f64(v, h, l);
-      sTh[j * TS_LDK + ii] = h;
-      sTl[j * TS_LDK + ii] = l;
+      const int64_t off = (int64_t)(j0 + j) * ldt + gi;
+      cp16(sT + 16 * e * TS_LDK, ok ? Th + off : Th, ok ? bytes : 0);
+      if constexpr (DF) cp16(sT + NT * TS_LDK + 16 * e * TS_LDK, ok ? Tl + off : Tl, ok ? bytes : 0);
     }
   };
 
@@ -321,15 +296,14 @@ __global__ void __launch_bounds__(TS_TH, 3) k_tsm_tn(int64_t R, int64_t D, int N
 
   if (nst > 0) {
     issue_z(0, 0);
-    if constexpr (!DF) issue_t32(0, 0);
+    issue_t32(0, 0);
     cp_commit();
   }
   for (int s = 0; s < nst; ++s) {
     const int buf = s & 1;
-    if constexpr (DF) load_t64(s, buf);
     if (s + 1 < nst) {
       issue_z(s + 1, buf ^ 1);
-      if constexpr (!DF) issue_t32(s + 1, buf ^ 1);
+      issue_t32(s + 1, buf ^ 1);
       cp_commit();
       cp_wait_one();
     } else {
@@ -427,7 +401,8 @@ constexpr int tn_smem(int NPT) {
 }
 
 template <int NPT, bool DF>
-cudaError_t nn_launch(int64_t M, int N, int64_t K, double alpha, const float* A, int64_t lda, const void* B,
+cudaError_t nn_launch(int64_t M, int N, int64_t K, double alpha, const float* A, int64_t lda, const float* B,
+                      const float* Blo,
                       int64_t ldb, double beta, void* C, int64_t ldc, cudaStream_t st) {
   constexpr int smem = nn_smem<DF>(NPT);
   static_assert(8 * NPT * (TsCfg<DF>::BM + 4) * (DF ? 8 : 4) <= smem, "epilogue tile exceeds the stage buffers");
@@ -439,12 +414,13 @@ cudaError_t nn_launch(int64_t M, int N, int64_t K, double alpha, const float* A,
   // read that block of A from HBM once
   dim3 grid((unsigned)nt, (unsigned)mt);
   if (mt > 65535) return cudaErrorInvalidValue;
-  k_tsm_nn<NPT, DF><<<grid, TS_TH, smem, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  k_tsm_nn<NPT, DF><<<grid, TS_TH, smem, st>>>(M, N, K, alpha, A, lda, B, Blo, ldb, beta, C, ldc);
   return cudaGetLastError();
 }
 
 template <int NPT, bool DF>
-cudaError_t tn_launch(int64_t R, int64_t D, int N, const float* Z, int64_t ldz, const void* T, int64_t ldt,
+cudaError_t tn_launch(int64_t R, int64_t D, int N, const float* Z, int64_t ldz, const float* T, const float* Tlo,
+                      int64_t ldt,
                       double alpha, double beta, void* Y, int64_t ldy, void* work, size_t work_bytes, int sms,
                       cudaStream_t st) {
   constexpr int smem = tn_smem<DF>(NPT);
@@ -465,7 +441,7 @@ cudaError_t tn_launch(int64_t R, int64_t D, int N, const float* Z, int64_t ldz, 
   if (need > work_bytes || !work) return cudaErrorInvalidValue;
   if (dt > 0x7fffffff) return cudaErrorInvalidValue;
   dim3 grid((unsigned)dt, (unsigned)chunks, (unsigned)nt);
-  k_tsm_tn<NPT, DF><<<grid, TS_TH, smem, st>>>(R, D, N, rpc, Z, ldz, T, ldt, work, ldw);
+  k_tsm_tn<NPT, DF><<<grid, TS_TH, smem, st>>>(R, D, N, rpc, Z, ldz, T, Tlo, ldt, work, ldw);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int64_t total = D * N;
   const int rb = (int)std::min<int64_t>((total + 255) / 256, 8LL * sms);
@@ -484,12 +460,36 @@ int pick_npt(int N) { return N <= 72 ? (N + 7) / 8 : 8; }
 
 }  // namespace
 
-bool tsm_supported(const void* A, int64_t lda, const void* B, int64_t ldb, int b_f64) {
-  const uintptr_t a = (uintptr_t)A, b = (uintptr_t)B;
-  if ((a & 15) || (lda & 3)) return false;
-  if (!b_f64 && ((b & 15) || (ldb & 3))) return false;
-  if (b_f64 && (b & 7)) return false;
-  return true;
+bool tsm_supported(const void* A, int64_t lda) {
+  return !((uintptr_t)A & 15) && !(lda & 3);
+}
+
+namespace {
+// hi/lo (rows x cols, column-major, ldd >= rows) = FP32 head and tail of src (rows x
+// cols, lds); rows rows..ldd-1 of hi and lo are zeroed
+__global__ void k_split_f64(int64_t rows, int cols, const double* __restrict__ src, int64_t lds, float* hi, float* lo,
+                            int64_t ldd) {
+  const int64_t total = ldd * cols;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % ldd;
+    const int j = (int)(idx / ldd);
+    float h = 0.f, l = 0.f;
+    if (i < rows) split_f64(src[i + (int64_t)j * lds], h, l);
+    hi[idx] = h;
+    lo[idx] = l;
+  }
+}
+}  // namespace
+
+cudaError_t launch_split_f64(int64_t rows, int cols, const double* src, int64_t lds, float* hi, float* lo, int64_t ldd,
+                             cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  if (ldd < rows) return cudaErrorInvalidValue;
+  const int64_t total = ldd * cols;
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, 8192);
+  k_split_f64<<<grid, 256, 0, st>>>(rows, cols, src, lds, hi, lo, ldd);
+  return cudaGetLastError();
 }
 
 size_t tsm_tn_work_bytes(int64_t R, int64_t D, int N, int df, int sms) {
@@ -517,12 +517,14 @@ size_t tsm_tn_work_bytes(int64_t R, int64_t D, int N, int df, int sms) {
   }
 
 cudaError_t launch_tsm_nn(int df, int64_t M, int N, int64_t K, double alpha, const float* A, int64_t lda,
-                          const void* B, int64_t ldb, double beta, void* C, int64_t ldc, cudaStream_t st) {
+                          const float* B, const float* Blo, int64_t ldb, double beta, void* C, int64_t ldc,
+                          cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (!tsm_supported(A, lda, B, ldb, df)) return cudaErrorInvalidValue;
+  if (!tsm_supported(A, lda) || !tsm_supported(B, ldb) || (df && !tsm_supported(Blo, ldb)))
+    return cudaErrorInvalidValue;
   const int npt = pick_npt(N);
-#define NN_F32(P) nn_launch<P, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st)
-#define NN_DF(P) nn_launch<P, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st)
+#define NN_F32(P) nn_launch<P, false>(M, N, K, alpha, A, lda, B, Blo, ldb, beta, C, ldc, st)
+#define NN_DF(P) nn_launch<P, true>(M, N, K, alpha, A, lda, B, Blo, ldb, beta, C, ldc, st)
   if (df) {
     BK_NPT_DISPATCH(npt, NN_DF)
   } else {
@@ -532,14 +534,15 @@ cudaError_t launch_tsm_nn(int df, int64_t M, int N, int64_t K, double alpha, con
 #undef NN_DF
 }
 
-cudaError_t launch_tsm_tn(int df, int64_t R, int64_t D, int N, const float* Z, int64_t ldz, const void* T,
-                          int64_t ldt, double alpha, double beta, void* Y, int64_t ldy, void* work, size_t work_bytes,
-                          int sms, cudaStream_t st) {
+cudaError_t launch_tsm_tn(int df, int64_t R, int64_t D, int N, const float* Z, int64_t ldz, const float* T,
+                          const float* Tlo, int64_t ldt, double alpha, double beta, void* Y, int64_t ldy, void* work,
+                          size_t work_bytes, int sms, cudaStream_t st) {
   if (D <= 0 || N <= 0) return cudaSuccess;
-  if (!tsm_supported(Z, ldz, T, ldt, df)) return cudaErrorInvalidValue;
+  if (!tsm_supported(Z, ldz) || !tsm_supported(T, ldt) || (df && !tsm_supported(Tlo, ldt)))
+    return cudaErrorInvalidValue;
   const int npt = pick_npt(N);
-#define TN_F32(P) tn_launch<P, false>(R, D, N, Z, ldz, T, ldt, alpha, beta, Y, ldy, work, work_bytes, sms, st)
-#define TN_DF(P) tn_launch<P, true>(R, D, N, Z, ldz, T, ldt, alpha, beta, Y, ldy, work, work_bytes, sms, st)
+#define TN_F32(P) tn_launch<P, false>(R, D, N, Z, ldz, T, Tlo, ldt, alpha, beta, Y, ldy, work, work_bytes, sms, st)
+#define TN_DF(P) tn_launch<P, true>(R, D, N, Z, ldz, T, Tlo, ldt, alpha, beta, Y, ldy, work, work_bytes, sms, st)
   if (df) {
     BK_NPT_DISPATCH(npt, TN_DF)
   } else {
