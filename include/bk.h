@@ -62,8 +62,10 @@ typedef enum { BK_F64 = 0, BK_F32 = 1 } bk_dtype;
  * the refinement residual are FP64 in every mode.
  *   BK_PREC_F32X2: FP64 blocks; block products of FP32-stored values (16-byte aligned
  *   rows) in compensated FP32-pair arithmetic on the FP32 pipe (each product exact,
- *   sums to about 2^-44 of sum |a_ik p_k|). Lanczos drivers only (bk_ridge_path,
- *   bk_sample); bk_solve and bk_solve_batched return BK_ERR_UNSUPPORTED. */
+ *   sums to about 2^-44 of sum |a_ik p_k|), and the basis products (reorthogonalisation,
+ *   block QR) in the same arithmetic; the Grams that give T_t, the band solves and the
+ *   refinement stay FP64. Lanczos drivers only (bk_ridge_path, bk_sample,
+ *   bk_sample_isqrt); bk_solve and bk_solve_batched return BK_ERR_UNSUPPORTED. */
 typedef enum { BK_PREC_FP64 = 0, BK_PREC_FP32 = 1, BK_PREC_F32X2 = 2 } bk_prec;
 
 /* The matrix A (without the shift mu).

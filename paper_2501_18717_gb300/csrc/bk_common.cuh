@@ -150,6 +150,11 @@ cudaError_t launch_gemm_split(int is_f64, int64_t M, int64_t N, int64_t K, doubl
                               int64_t sai, int64_t sak, const void* B, int64_t sbk, int64_t sbj, double beta, void* C,
                               int64_t ldc, void* work, size_t work_bytes, int sms, cudaStream_t st);
 size_t gemm_split_work_bytes(int is_f64, int64_t M, int64_t N, int64_t K, int sms);
+// Double-float launch_gemm_split for FP64 A, B, C (compensated FP32-pair products,
+// about 2^-44 relative; see k_gemm.cu); same strides, same split-K work size.
+cudaError_t launch_gemm_dd(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
+                           const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t ldc, void* work,
+                           size_t work_bytes, int sms, cudaStream_t st);
 // ---- tall-skinny products of the Lanczos drivers (k_tsm.cu)
 // df = 0: FP32 B / T (the *lo arguments unused) and FP32 output; df = 1: B / T is an
 // FP64 operand given as its FP32 head and tail (launch_split_f64, same leading

@@ -221,14 +221,23 @@ struct Lanczos {
 
   // Split-K general product for tall reductions (Grams, Q^T W): K = d is long and the
   // output has few tiles.
+  // In an F32X2 run the products that build the basis (reorthogonalisation, the
+  // three-term step, Q = W R^{-1}) use the double-float GEMM, about 2^-44 relative
+  // (CholQR2's second pass restores orthogonality); the Grams that give the entries of
+  // T_t (allow_dd = false) stay in FP64, since the shifted solves and the square root
+  // resolve T_t's smallest eigenvalues. FP64 runs use the FP64 GEMM throughout.
   cudaError_t gemm_k(int out64, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int a_f64, int64_t sai,
-                     int64_t sak, const void* B, int64_t sbk, int64_t sbj, double beta, void* C, int64_t ldc) {
+                     int64_t sak, const void* B, int64_t sbk, int64_t sbj, double beta, void* C, int64_t ldc,
+                     bool allow_dd = true) {
     const size_t wb = bk::gemm_split_work_bytes(out64, M, N, K, c->sms);
     void* wk = nullptr;
     if (wb) {
       cudaError_t e = ws_get(c, WS_SPLIT, wb, &wk);
       if (e != cudaSuccess) return e;
     }
+    if (allow_dd && df && is64 && out64 && a_f64 == 1)
+      return bk::launch_gemm_dd(M, N, K, alpha, (const double*)A, sai, sak, (const double*)B, sbk, sbj, beta,
+                                (double*)C, ldc, wk, wb, c->sms, st);
     return bk::launch_gemm_split(out64, M, N, K, alpha, A, a_f64, sai, sak, B, sbk, sbj, beta, C, ldc, wk, wb, c->sms,
                                  st);
   }
@@ -241,12 +250,12 @@ struct Lanczos {
       const void* src = pass == 0 ? Wb : Qout;
       double* R = pass == 0 ? R1 : R2;
       double* Ri = pass == 0 ? Ri1 : Ri2;
-      if ((e = gemm_k(1, m, m, d, 1.0, src, gaf, ldq, 1, src, 1, ldq, 0.0, G, m)) != cudaSuccess)
+      if ((e = gemm_k(1, m, m, d, 1.0, src, gaf, ldq, 1, src, 1, ldq, 0.0, G, m, false)) != cudaSuccess)
         return e;
       if ((e = bk::launch_chol_inv(m, G, rank_tol, work, R, Ri, keep, rank, st)) != cudaSuccess) return e;
       // Qout = src * Ri (Ri row-major: element (k, j) at Ri[k m + j])
       if (is64) {
-        e = bk::launch_gemm(1, d, m, m, 1.0, src, 1, 1, ldq, Ri, m, 1, 0.0, Qout, ldq, st);
+        e = gemm_k(1, d, m, m, 1.0, src, 1, 1, ldq, Ri, m, 1, 0.0, Qout, ldq);
       } else {
         if ((e = bk::launch_copy_cols(1, 0, (int64_t)m * m, 1, Ri, (int64_t)m * m, Rt, (int64_t)m * m, st)) !=
             cudaSuccess)
@@ -274,17 +283,16 @@ struct Lanczos {
     if (prof) prof->begin();
     // A_k = Q_k^T (A Q_k) with FP64 accumulation
     const int gaf = is64 ? 1 : 2;
-    if ((e = gemm_k(1, m, m, d, 1.0, Qk, gaf, ldq, 1, W, 1, ldq, 0.0, Ak, m)) != cudaSuccess) return e;
+    if ((e = gemm_k(1, m, m, d, 1.0, Qk, gaf, ldq, 1, W, 1, ldq, 0.0, Ak, m, false)) != cudaSuccess) return e;
     // three-term recurrence W -= Q_{k-1} B_{k-1}^T + Q_k A_k (Bk still holds B_{k-1}),
     // then one classical Gram-Schmidt pass against Q_0..Q_k for what rounding left along
     // the older blocks (full reorthogonalisation; the first pass of a CGS2 against all
     // blocks would remove the same two terms, so the result equals it up to rounding)
     if ((e = bk::launch_three_term(is64, m, k == 0, Ak, Bk, M3, st)) != cudaSuccess) return e;
     if (k == 0)
-      e = bk::launch_gemm(is64, d, m, m, -1.0, Qk, is64, 1, ldq, (const char*)M3 + (size_t)m * es, 1, 2 * m, 1.0, W,
-                          ldq, st);
+      e = gemm_k(is64, d, m, m, -1.0, Qk, is64, 1, ldq, (const char*)M3 + (size_t)m * es, 1, 2 * m, 1.0, W, ldq);
     else
-      e = bk::launch_gemm(is64, d, m, 2 * m, -1.0, qblock(k - 1), is64, 1, ldq, M3, 1, 2 * m, 1.0, W, ldq, st);
+      e = gemm_k(is64, d, m, 2 * m, -1.0, qblock(k - 1), is64, 1, ldq, M3, 1, 2 * m, 1.0, W, ldq);
     if (e != cudaSuccess) return e;
     const int64_t nk = (int64_t)(k + 1) * m;
     if ((e = gemm_k(is64, nk, m, d, 1.0, Q, is64, ldq, 1, W, 1, ldq, 0.0, C, nk)) != cudaSuccess) return e;

@@ -102,6 +102,111 @@ __global__ void __launch_bounds__(GTH) k_gemm(int64_t M, int64_t N, int64_t K, T
   }
 }
 
+// Double-float form of k_gemm for FP64 A, B, C: each FP64 operand is split into an FP32
+// head and tail as it is staged, and the products run in compensated FP32-pair
+// arithmetic (head-head product exact by FMA, the cross terms added to its error,
+// TwoSum accumulation), about 2^-44 relative to sum |a_ik b_kj|, on the FP32 pipe that
+// GB300 runs 64 times faster than its FP64 pipe. Same tiles, strides and split-K as
+// k_gemm.
+__device__ __forceinline__ void gemm_dd_mac(float& s, float& c, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+__global__ void __launch_bounds__(GTH) k_gemm_dd(int64_t M, int64_t N, int64_t K, double alpha,
+                                                const double* __restrict__ A, int64_t sai, int64_t sak,
+                                                const double* __restrict__ B, int64_t sbk, int64_t sbj, double beta,
+                                                double* __restrict__ C, int64_t ldc, int64_t kchunk, int64_t zstride) {
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
+  C += (int64_t)blockIdx.z * zstride;
+  __shared__ float sAh[GBK][GBM + 4], sAl[GBK][GBM + 4];
+  __shared__ float sBh[GBK][GBN + 4], sBl[GBK][GBN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int64_t i0 = (int64_t)blockIdx.x * GBM, j0 = (int64_t)blockIdx.y * GBN;
+  float s[4][4], c[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) s[a][b] = c[a][b] = 0.f;
+  const bool a_rows_fast = (sai == 1);
+  const bool b_rows_fast = (sbk == 1);
+  for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
+#pragma unroll
+    for (int e = 0; e < (GBM * GBK) / GTH; ++e) {
+      const int idx = tid + e * GTH;
+      int ii, kk;
+      if (a_rows_fast) {
+        ii = idx % GBM;
+        kk = idx / GBM;
+      } else {
+        kk = idx % GBK;
+        ii = idx / GBK;
+      }
+      const int64_t gi = i0 + ii, gk = k0 + kk;
+      const double v = (gi < M && gk < kend) ? A[gi * sai + gk * sak] : 0.0;
+      const float h = (float)v;
+      sAh[kk][ii] = h;
+      sAl[kk][ii] = (float)(v - (double)h);
+    }
+#pragma unroll
+    for (int e = 0; e < (GBN * GBK) / GTH; ++e) {
+      const int idx = tid + e * GTH;
+      int jj, kk;
+      if (b_rows_fast) {
+        kk = idx % GBK;
+        jj = idx / GBK;
+      } else {
+        jj = idx % GBN;
+        kk = idx / GBN;
+      }
+      const int64_t gj = j0 + jj, gk = k0 + kk;
+      const double v = (gj < N && gk < kend) ? B[gk * sbk + gj * sbj] : 0.0;
+      const float h = (float)v;
+      sBh[kk][jj] = h;
+      sBl[kk][jj] = (float)(v - (double)h);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ah[u] = sAh[kk][ty + 16 * u];
+        al[u] = sAl[kk][ty + 16 * u];
+        bh[u] = sBh[kk][tx + 16 * u];
+        bl[u] = sBl[kk][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) gemm_dd_mac(s[u][v], c[u][v], ah[u], al[u], bh[v], bl[v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t gi = i0 + ty + 16 * u;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int64_t gj = j0 + tx + 16 * v;
+      if (gj >= N) continue;
+      double* cp = C + gi + gj * ldc;
+      const double val = (double)s[u][v] + (double)c[u][v];
+      *cp = (beta == 0.0) ? alpha * val : fma(alpha, val, beta * *cp);
+    }
+  }
+}
+
 }  // namespace
 
 namespace {
@@ -183,6 +288,30 @@ cudaError_t launch_gemm_split(int is_f64, int64_t M, int64_t N, int64_t K, doubl
     k_gemm_reduce<double><<<rb, 256, 0, st>>>(M, N, nzz, (const double*)work, beta, (double*)C, ldc);
   else
     k_gemm_reduce<float><<<rb, 256, 0, st>>>(M, N, nzz, (const float*)work, beta, (float*)C, ldc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_dd(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
+                           const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t ldc, void* work,
+                           size_t work_bytes, int sms, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  int nz = gemm_split_count(M, N, K, sms);
+  if (nz > 1 && (!work || (size_t)nz * M * N * 8 > work_bytes)) nz = 1;
+  dim3 grid((unsigned)((M + GBM - 1) / GBM), (unsigned)((N + GBN - 1) / GBN), 1);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  if (nz <= 1) {
+    k_gemm_dd<<<grid, GTH, 0, st>>>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, ldc, K, 0);
+    return cudaGetLastError();
+  }
+  int64_t kchunk = (K + nz - 1) / nz;
+  kchunk = (kchunk + GBK - 1) / GBK * GBK;
+  const int nzz = (int)((K + kchunk - 1) / kchunk);
+  grid.z = (unsigned)nzz;
+  k_gemm_dd<<<grid, GTH, 0, st>>>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, 0.0, (double*)work, M, kchunk, M * N);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int rb = (int)std::min<int64_t>((M * N + 255) / 256, 4LL * sms);
+  k_gemm_reduce<double><<<rb, 256, 0, st>>>(M, N, nzz, (const double*)work, beta, C, ldc);
   return cudaGetLastError();
 }
 

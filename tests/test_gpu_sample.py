@@ -147,9 +147,10 @@ def test_rbf_operator_exact_integral_on_same_basis(bk, ctx):
 def test_rbf_operator_subset_literal_nugget(bk, ctx, fn):
     """The sampling validation problem with the kernel formed on the fly instead of
     stored in FP32: the first 2000 points, 256 samples, the configuration's nugget 1e-6,
-    against the oracle's eigendecomposition of the FP64 kernel. Pair-arithmetic error
-    about 1e-13 ||K||, amplified by at most sqrt(kappa) (square root) or kappa (inverse
-    square root) relative."""
+    against the oracle's eigendecomposition of the FP64 kernel. An F32X2 basis is built
+    with compensated-pair products (2^-44 each); over the steps and the two CholQR
+    passes its relative accuracy is about 1e-12 ||K||, amplified by at most sqrt(kappa)
+    (square root) or kappa (inverse square root) relative."""
     d, m, nug = 2000, 256, 1e-6
     pts = W.rbf_points(W.BASE_SEED + 4, 40000)[:d].copy()
     K = W.rbf_kernel(pts)
@@ -162,6 +163,6 @@ def test_rbf_operator_subset_literal_nugget(bk, ctx, fn):
     ref = (direct.sqrtm_apply if fn == "sqrt" else direct.isqrtm_apply)(K, B, shift=nug)
     lam = np.linalg.eigvalsh(K) + nug
     kap = lam[-1] / lam[0]
-    tol = 1e-13 * (np.sqrt(kap) if fn == "sqrt" else kap)
+    tol = 1e-12 * (np.sqrt(kap) if fn == "sqrt" else kap)
     err = np.linalg.norm(S - ref) / np.linalg.norm(ref)
     assert err <= max(tol, 1e-9), (err, tol, info.as_dict())
