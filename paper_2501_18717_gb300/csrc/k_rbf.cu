@@ -13,12 +13,10 @@
 // therefore accurate to FP64 rounding, far below the nugget, unlike an FP32-stored K
 // whose rounding is a perturbation of norm ~3e-6 at 40,000 points.
 //
-// Tile: 192 threads as 6 row groups x 32 column groups, two CTAs per SM; 24 rows x
-// 256 columns per CTA (4 rows x 8 columns per thread), so each exp serves all columns
-// of a block of up to 256 (measured 13 % faster than one CTA of 384 threads per SM,
-// whose slice barriers stalled the whole SM). The K slice (24 rows x 16 points) is
-// generated into shared memory per stage; the X slice (16 rows x 256 columns) comes in
-// as FP32 head and tail.
+// Tile: 384 threads as 12 row groups x 32 column groups; 48 rows x 256 columns per CTA
+// (4 rows x 8 columns per thread), so each exp serves all columns of a block of up to
+// 256. The K slice (48 rows x 16 points) is generated into shared memory per stage; the
+// X slice (16 rows x 256 columns) is split into head and tail in shared memory.
 #include <algorithm>
 
 #include "bk_common.cuh"
@@ -26,7 +24,7 @@
 namespace bk {
 namespace {
 
-constexpr int RB_TH = 192, RB_RG = 6, RB_BM = 4 * RB_RG, RB_BN = 256, RB_BK = 16, RB_NPT = 8;
+constexpr int RB_TH = 128, RB_RG = 4, RB_BM = 4 * RB_RG, RB_BN = 256, RB_BK = 16, RB_NPT = 8;
 constexpr int RB_LDK = RB_BM + 4, RB_LDX = RB_BN + 4;
 static_assert((RB_BM * RB_BK) % RB_TH == 0, "whole K-slice entries per thread");
 
@@ -114,7 +112,7 @@ __device__ __forceinline__ void exp_df(double t, float& h, float& l) {
 // builds its part of slice s + 1 (FP64 exp, FP64 splits) and then runs its products on
 // slice s, with one barrier per slice, so the FP64 work of some warps overlaps the FP32
 // multiply-adds of others.
-__global__ void __launch_bounds__(RB_TH, 2) k_rbf_apply(int64_t d, int N, const double* __restrict__ pts,
+__global__ void __launch_bounds__(RB_TH, 3) k_rbf_apply(int64_t d, int N, const double* __restrict__ pts,
                                                         int64_t ldp, double h, const float* __restrict__ Xh,
                                                         const float* __restrict__ Xl, int64_t ldx,
                                                         double* __restrict__ Y, int64_t ldy) {
