@@ -13,10 +13,13 @@
 // therefore accurate to FP64 rounding, far below the nugget, unlike an FP32-stored K
 // whose rounding is a perturbation of norm ~3e-6 at 40,000 points.
 //
-// Tile: 384 threads as 12 row groups x 32 column groups; 48 rows x 256 columns per CTA
-// (4 rows x 8 columns per thread), so each exp serves all columns of a block of up to
-// 256. The K slice (48 rows x 16 points) is generated into shared memory per stage; the
-// X slice (16 rows x 256 columns) is split into head and tail in shared memory.
+// Tile: 128 threads as 4 row groups x 32 column groups, three CTAs per SM; 16 rows x
+// 256 columns per CTA (4 rows x 8 columns per thread), so each exp serves all columns
+// of a block of up to 256. Smaller CTAs measured faster (one CTA of 384 threads per
+// SM: 249 ms per 40,000-point load; two of 192: 216 ms; three of 128: 204 ms), since
+// the slice barriers of one CTA no longer stall the whole SM. The K slice (16 rows x
+// 16 points) is generated into shared memory per stage; the X slice (16 rows x 256
+// columns) comes in as FP32 head and tail.
 #include <algorithm>
 
 #include "bk_common.cuh"
