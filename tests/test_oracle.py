@@ -321,3 +321,93 @@ def test_thm_main(s):
             eb = anorm(xs - xb)
             ep = anorm(xs - pc[t - s - 1])
             assert eb <= (1 + 1e-8) * ep + 1e-12 * anorm(xs), (mu, t)
+
+
+# ---------------------------------------------------------------- O5 (f4)
+from oracle import deflated  # noqa: E402
+
+
+def _defl_problem(seed, d, k):
+    lam = np.concatenate([np.geomspace(1e3, 20.0, 8), np.linspace(2.0, 0.1, d - 8)])
+    a = spd(d, lam, seed)
+    b = W.normals(seed, 2, d)
+    Wb = np.linalg.qr(W.omega(seed, d, k))[0] if k else np.zeros((d, 0))
+    return a, b, Wb
+
+
+@pytest.mark.parametrize("k", [0, 4, 9])
+def test_deflated_cg_brute_force_galerkin(k):
+    """Def-CG: x_j minimises the A_mu-norm error over span(W) + K_j(P A_mu, r_0),
+    P = I - A_mu W (W^T A_mu W)^{-1} W^T, r_0 = b - A_mu x_0."""
+    d, mu = 70, 0.02
+    a, b, Wb = _defl_problem(21, d, k)
+    am = a + mu * np.eye(d)
+    xs = deflated.deflated_cg(a, mu, b, Wb, 6)
+    if k:
+        P = np.eye(d) - am @ Wb @ np.linalg.solve(Wb.T @ am @ Wb, Wb.T)
+        x0 = Wb @ np.linalg.solve(Wb.T @ am @ Wb, Wb.T @ b)
+    else:
+        P, x0 = np.eye(d), np.zeros(d)
+    r0 = b - am @ x0
+    for j in range(0, 7):
+        K = [np.linalg.matrix_power(P @ am, i) @ r0 for i in range(j)]
+        S = np.column_stack([Wb] + K) if (k or j) else np.zeros((d, 0))
+        if S.shape[1] == 0:
+            assert np.linalg.norm(xs[0]) == 0.0
+            continue
+        S = np.linalg.qr(S / np.linalg.norm(S, axis=0))[0]
+        xg = S @ np.linalg.solve(S.T @ am @ S, S.T @ b)
+        assert rel(xs[j], xg) < 1e-9, (k, j)
+
+
+def test_deflated_cg_invariant_subspace_is_cg():
+    """W spanning eigenvectors of A leaves the projection inert (A_mu W = W Lambda_mu and
+    r_j orthogonal to W give mu_j = 0), so Def-CG runs SciPy's CG. Diagonal A with b zero
+    on W's coordinates keeps that exact in rounding too (a rotated basis would leave
+    rounding-level components along W that CG amplifies by the eigenvalue ratio)."""
+    d, k, mu = 60, 5, 0.1
+    lam = np.concatenate([np.geomspace(400.0, 50.0, k), np.linspace(10.0, 0.2, d - k)])
+    a = np.diag(lam)
+    b = W.normals(22, 2, d)
+    b[:k] = 0.0
+    Wb = np.eye(d)[:, :k]
+    xs = deflated.deflated_cg(a, mu, b, Wb, 9)
+    assert np.linalg.norm(xs[0]) == 0.0
+    for t in [1, 3, 9]:
+        ref, _ = spla.cg(a + mu * np.eye(d), b, x0=np.zeros(d), maxiter=t, rtol=0.0, atol=0.0)
+        assert rel(xs[t], ref) < 1e-12, t
+        ref0 = nystrom.pcg(a, mu, b, None, t)[-1]  # and the textbook CG of the comparator
+        assert rel(xs[t], ref0) < 1e-12, t
+
+
+def test_deflated_cg_finite_termination():
+    """The iterate space reaches R^d after d - dim(W) iterations: exact there, not two
+    iterations earlier (W random, so not an invariant subspace)."""
+    d, k, mu = 40, 32, 0.05
+    a = spd(d, np.geomspace(1e3, 1.0, d), 23)
+    b = W.normals(23, 2, d)
+    Wb = np.linalg.qr(W.omega(23, d, k))[0]
+    xs = deflated.deflated_cg(a, mu, b, Wb, d - k)
+    xstar = direct.solve(a, mu, b)
+    assert rel(xs[d - k], xstar) < 1e-9
+    assert rel(xs[d - k - 2], xstar) > 1e-6
+
+
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_shrink_start_and_inclusion(s):
+    """j = 0 is the block-CG iterate after s loads on [b Omega] (Def. BCG, brute force);
+    span(W) + K_j(P A_mu, r_0) lies in K_{s+j}(A, [b Omega]) (r_0 is in K_{s+1} and P A_mu
+    maps K_{s+i} into K_{s+i+1}), so block-CG after s + j loads is at least as accurate in
+    the A_mu-norm."""
+    d, l, mu = 90, 5, 1e-3
+    a, b, _ = _defl_problem(24, d, 0)
+    om = W.omega(24, d, l)
+    B = np.column_stack([b, om])
+    xs = deflated.shrink_solve(a, mu, b, om, s, 8)
+    assert rel(xs[0], galerkin.bcg_iterate(a, mu, B, s)) < 1e-9
+    xstar = direct.solve(a, mu, b)
+    am = a + mu * np.eye(d)
+    anorm = lambda v: np.sqrt(v @ am @ v)
+    for j in range(1, 9):
+        xb = lanczos.shifted_iterates(lanczos.block_lanczos(a, B, s + j), [mu])[:, 0]
+        assert anorm(xstar - xb) <= (1 + 1e-7) * anorm(xstar - xs[j]) + 1e-12 * anorm(xstar), (s, j)
