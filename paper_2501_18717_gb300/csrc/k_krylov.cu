@@ -212,6 +212,77 @@ __global__ void __launch_bounds__(256) k_band_factor(int n, int bw, const double
   if (tid == 0) flags[j] = s_bad;
 }
 
+// The same factorisation with the active window in shared memory, for bw <= 112: the
+// columns c .. c + bw are the only ones column c's step reads or updates, so a ring of
+// bw + 1 columns (slot c mod (bw + 1), entry r = L(c + r, c)) holds them; a finished
+// column goes to `work` and the band's next column takes its slot. Global memory then
+// sees each entry once instead of once per trailing update.
+__global__ void __launch_bounds__(256) k_band_factor_smem(int n, int bw, const double* __restrict__ band, int ldb,
+                                                          const double* __restrict__ mus, double* work, int* flags) {
+  extern __shared__ double win[];
+  const int j = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+  const int W = bw + 1;
+  double* Lb = work + (size_t)j * (bw + 2) * n;
+  double* invL = Lb + (size_t)(bw + 1) * n;
+  const double mu = mus[j];
+  __shared__ double s_inv;
+  __shared__ int s_bad;
+  auto band_entry = [&](int c, int r) {
+    double v = (c + r < n) ? band[(size_t)r * ldb + c] : 0.0;
+    if (r == 0) v = (v == 0.0) ? 1.0 : v + mu;
+    return v;
+  };
+  const int first = min(n, W);
+  for (int idx = tid; idx < first * W; idx += nth) {
+    const int c = idx / W, r = idx - c * W;
+    win[c * W + r] = band_entry(c, r);
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int c = 0; c < n; ++c) {
+    double* col = win + (c % W) * W;
+    // the band's column c + W, fetched now so that its latency overlaps this step
+    const bool next = c + W < n;
+    const double pre = (next && tid < W) ? band_entry(c + W, tid) : 0.0;
+    if (tid == 0) {
+      const double x = col[0];
+      if (!(x > 0.0)) {  // not positive: drop this direction (see k_band_factor)
+        s_bad = 1;
+        s_inv = 0.0;
+        col[0] = 1.0;
+      } else {
+        const double r = rsqrt_nr(x);
+        col[0] = x * r;
+        s_inv = r;
+      }
+      invL[c] = s_inv;
+    }
+    __syncthreads();
+    const double inv = s_inv;
+    const int w = min(bw, n - 1 - c);
+    for (int r = 1 + tid; r <= w; r += nth) col[r] *= inv;
+    __syncthreads();
+    if (inv != 0.0) {
+      for (int a = 1 + warp; a <= w; a += nw) {
+        const double la = col[a];
+        for (int b = 1 + lane; b <= a; b += 32) {
+          double* t = win + ((c + b) % W) * W + (a - b);
+          *t = fma(-la, col[b], *t);
+        }
+      }
+      __syncthreads();
+    }
+    // column c is final: out to the factor, and the band's column c + W into its slot
+    if (tid < W) {
+      Lb[(size_t)tid * n + c] = (tid <= w) ? col[tid] : 0.0;
+      if (next) col[tid] = pre;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) flags[j] = s_bad;
+}
+
 __global__ void __launch_bounds__(256) k_band_subst(int n, int bw, const double* __restrict__ rhs,
                                                     const int* __restrict__ rhs_col, int nrhs, int per_cta,
                                                     const double* __restrict__ work, double* Z,
@@ -415,8 +486,17 @@ cudaError_t launch_band_solve(int n, int bw, const double* band, int ldb, int L,
                               const double* rhs, const int* rhs_col, int nrhs, double* work, double* Z, int* flags,
                               cudaStream_t st) {
   if (L <= 0) return cudaSuccess;
-  k_band_factor<<<L, 256, 0, st>>>(n, bw, band, ldb, mus, work, flags);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (bw <= 112) {
+    const size_t smem = (size_t)(bw + 1) * (bw + 1) * 8;
+    if ((e = cudaFuncSetAttribute(k_band_factor_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return e;
+    k_band_factor_smem<<<L, 256, smem, st>>>(n, bw, band, ldb, mus, work, flags);
+  } else {
+    k_band_factor<<<L, 256, 0, st>>>(n, bw, band, ldb, mus, work, flags);
+  }
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // right-hand-side slices: about two CTAs per SM in total, at least 8 columns each
   int dev = 0, sms = 152;
