@@ -46,6 +46,11 @@ SEED = W.BASE_SEED + 2
 OMEGA_SEED = W.BASE_SEED + 3
 METRIC = "solves/s at rel. residual 1e-8 and HBM GB/s per iteration, mixed vs FP64 plain"
 WORKLOAD = "csr_diffusion_128^3_d2097152_nnz14581760_mu1e-4_l32"
+
+
+def workload_name(grid, d, nnz):
+    """The diffusion workload string for a grid size (the 128^3 default is WORKLOAD)."""
+    return f"csr_diffusion_{grid}^3_d{d}_nnz{nnz}_mu1e-4_l32"
 KERNEL_SOURCES = ["paper_2501_18717_gb300/csrc/k_ops.cu", "paper_2501_18717_gb300/csrc/k_block.cu",
                   "paper_2501_18717_gb300/csrc/bk_tile.cuh", "paper_2501_18717_gb300/csrc/bk_update.cuh"]
 
@@ -57,7 +62,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="diffusion", choices=["diffusion", "batched", "dense-product", "ridge",
-                                                                 "sample", "nystrom"])
+                                                                 "sample", "nystrom", "shrink"])
     ap.add_argument("--ridge-n", type=int, default=200000)
     ap.add_argument("--ridge-d", type=int, default=4096)
     ap.add_argument("--sample-d", type=int, default=40000)
@@ -801,9 +806,134 @@ def run_nystrom(args, world, rank, local, dev):
             "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 (block-CG FP64 and PCG), f32 blocks + f64 refinement (block-CG mixed)",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sketch_l": SKETCH, "tol": TOL, "mu": MU,
+            "config": {"workload": workload_name(args.grid, d, int(va.shape[0])), "sketch_l": SKETCH, "tol": TOL,
+                       "mu": MU,
                        "l2": "working set larger than L2; no flush"},
             "methods": rows, "clocks": clk.summary(), "cpu_baseline": None}), flush=True)
+    ctx.close()
+    return 0
+
+
+def oracle_shrink_sample(rp, ci, va, b, om, s_lock, iters, seconds):
+    """The FP64 oracle's block-shrinking solve (locked basis of K_s(A, [b Omega]), then
+    Def-CG) on the full workload: the basis and a bounded number of one-column steps are
+    timed, and the time of a whole solve is the basis time plus the per-step time times
+    the GPU's step count."""
+    from oracle import deflated, operators
+    op = operators.CSR(rp, ci, va)
+    t0 = time.perf_counter()
+    Wb = deflated.locked_basis(op, b, om, s_lock)
+    t_basis = time.perf_counter() - t0
+    k = 2
+    while True:
+        t0 = time.perf_counter()
+        deflated.deflated_cg(op, MU, b, Wb, k)
+        t_k = time.perf_counter() - t0
+        if t_basis + t_k >= seconds or k >= 64:
+            break
+        k *= 2
+    t1 = time.perf_counter()
+    deflated.deflated_cg(op, MU, b, Wb, 0)
+    t_setup = time.perf_counter() - t1
+    per_step = max(t_k - t_setup, 1e-9) / k
+    return t_basis + t_setup + per_step * iters, k, t_basis, per_step
+
+
+def run_shrink(args, world, rank, local, dev):
+    """Block shrinking (the outlook's deflation to a smaller block, Sec. CG_pro's locked
+    reorthogonalisation) on the 128^3 diffusion system (FP64 values, mu 1e-4, tol 1e-8):
+    s block steps on [b Omega] (33 columns) lock V, then one-column deflated CG against V.
+    Compared with randomized block-CG (mixed) on the same Omega. Reports loads, time and
+    the recomputed FP64 residual of each; roofline is the deflation products (HBM)."""
+    import torch
+    from paper_2501_18717_gb300 import bk
+
+    rp, ci, va, d = W.diffusion_csr(SEED, args.grid)
+    b = W.normals(SEED, W.STREAM_RHS, d)
+    A = bk.csr_operator(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), torch.from_numpy(va).to(dev))
+    bd = torch.from_numpy(b).to(dev)
+    x = torch.zeros(d, dtype=torch.float64, device=dev)
+    ctx = bk.Context(local)
+    stream = torch.cuda.Stream(dev)
+    ctx.set_stream(stream.cuda_stream)
+    rows = {}
+    head_s = 3
+    m = SKETCH + 1
+
+    def timed(fn, reps=1):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                info = fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        return info, e0.elapsed_time(e1) / reps
+
+    def shrink_opts(profile=0):
+        return bk.default_opts(tol=TOL, sketch=SKETCH, seed=OMEGA_SEED, check_every=32, max_loads=args.max_loads,
+                               profile=profile)
+
+    with ClockSampler(local) as clk:
+        info, ms = timed(lambda: bk.solve(ctx, A, MU, bd, x, bk.default_opts(
+            tol=TOL, sketch=SKETCH, seed=OMEGA_SEED, inner="fp32", inner_tol=1e-5, check_every=16,
+            max_loads=args.max_loads), check=False))
+        rows["block_cg_mixed"] = {"loads": info.loads, "ms": ms, "rel_residual": info.rel_residual,
+                                  "status": info.status, "block_width": m}
+        for s_lock in (1, 3):
+            info, ms = timed(lambda: bk.solve_shrink(ctx, A, MU, bd, x, s_lock, shrink_opts(), check=False),
+                             reps=args.steps if s_lock == head_s else 1)
+            rows[f"shrink_s{s_lock}"] = {"loads": info.loads, "block_loads": s_lock,
+                                         "one_column_steps": info.loads - s_lock - 1, "ms": ms,
+                                         "rel_residual": info.rel_residual, "status": info.status,
+                                         "locked_columns": info.refinements}
+        with torch.cuda.stream(stream):
+            pinfo = bk.solve_shrink(ctx, A, MU, bd, x, head_s, shrink_opts(profile=1), check=False)
+            torch.cuda.synchronize(dev)
+    names = bk.KERNEL_CLASSES
+    groups = {}
+    for k in ("operator", "orth"):
+        j = names.index(k)
+        groups[k] = {"ms": pinfo.ms_kernel[j], "calls": int(pinfo.launches[j]),
+                     "avg_ms": pinfo.ms_kernel[j] / max(pinfo.launches[j], 1),
+                     "share_of_call": pinfo.ms_kernel[j] / max(pinfo.ms_total, 1e-9)}
+    n_lock = head_s * m
+    nb = n_lock + m
+    # one direction update: [V Q_s]^T r (nb columns) and p = r + V c + beta p (n columns),
+    # the basis as FP32 head + tail (8 bytes an entry); r read twice, p read and written
+    defl_bytes = 8.0 * d * (nb + n_lock + 4)
+    peak, peak_src = measured_peaks()
+    gbs = defl_bytes / (groups["orth"]["avg_ms"] * 1e-3) / 1e9
+    head = rows[f"shrink_s{head_s}"]
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        om = W.omega(OMEGA_SEED, d, SKETCH)
+        t_solve, k, t_basis, per_step = oracle_shrink_sample(rp, ci, va, b, om, head_s, head["one_column_steps"],
+                                                             args.cpu_seconds)
+        cpu = {"value": 1.0 / t_solve, "unit": "solves/s", "cores": threads_used(), "kind": "oracle",
+               "sample": f"FP64 oracle (NumPy/SciPy) locked basis of K_{head_s}(A, [b Omega]) "
+                         f"({t_basis:.1f} s) and {k} Def-CG steps ({per_step * 1e3:.1f} ms each) on the full "
+                         f"workload; a solve = basis + {head['one_column_steps']} steps, the GPU's count"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "solves/s at rel. residual 1e-8: block-CG shrunk to one column after s block steps "
+                      "(deflated CG on the locked block-Krylov basis)",
+            "value": 1e3 / head["ms"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (locked basis, deflated CG; FP64 CSR values)", "data": "synthetic",
+            "config": {"workload": workload_name(args.grid, d, int(va.shape[0])), "sketch_l": SKETCH, "s_lock": head_s,
+                       "tol": TOL, "mu": MU,
+                       "l2": "locked basis 2.2 GB, larger than L2; no flush"},
+            "methods": rows, "groups": groups,
+            "roofline": {"bound": "hbm", "kernel": f"deflation products [V Q_s]^T r ({nb} cols) and p = r + V c + beta p "
+                                                   f"({n_lock} cols), FP32 head/tail basis, k_defl_t + k_defl_reduce + "
+                                                   "k_defl_coef + k_defl_np",
+                         "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+                         "peak_source": peak_src},
+            "clocks": clk.summary(), "cpu_baseline": cpu}), flush=True)
     ctx.close()
     return 0
 
@@ -832,6 +962,8 @@ def main():
         return run_sample(args, world, rank, local, dev)
     if args.workload == "nystrom":
         return run_nystrom(args, world, rank, local, dev)
+    if args.workload == "shrink":
+        return run_shrink(args, world, rank, local, dev)
 
     def barrier():
         if world > 1:

@@ -255,6 +255,42 @@ bk_status bk_sample_isqrt(bk_ctx* ctx, const bk_operator* K, double nugget, int3
 bk_status bk_nystrom_pcg(bk_ctx* ctx, const bk_operator* A, double mu, const double* b, double* x, int32_t s_ny,
                          const bk_opts* opts, bk_info* info);
 
+/* Block-CG whose block shrinks to one column after s_lock steps (the outlook's
+ * deflation to a smaller block; Sec. CG_pro's scheme of full reorthogonalisation for
+ * the first blocks and orthogonalisation against only those afterwards), for
+ * (A + mu I) x = b:
+ *   1. s_lock block-Lanczos steps with full reorthogonalisation on [b Omega] (block width
+ *      m = 1 + sketch; Omega as bk_solve's) lock V = [Q_0 .. Q_{s-1}], an orthonormal
+ *      basis of K_s(A, [b Omega]), and T_s = V^T A V; x_0 = V (T_s + mu I)^{-1} V^T b is
+ *      the block-CG iterate after s_lock loads (Eq. bcg_alg), r_0 = b - A_mu x_0.
+ *   2. one-column deflated CG with deflation space V (Def-CG of Saad, Yeung, Erhel and
+ *      Guyomarc'h, SIAM J. Sci. Comput. 21, 2000): directions are kept A_mu-orthogonal
+ *      to V and residuals orthogonal to it, with the coefficients
+ *      (T_s + mu I)^{-1} (A_mu V)^T r = V^T r + K Q_s^T r, K = (T_s + mu I)^{-1} E_s B_s^T,
+ *      from the Lanczos relation A V = V T_s + Q_s B_s E_s^T (no stored A V). Each
+ *      iteration is one single-column load plus one pass over [V Q_s] (d x (s + 1) m)
+ *      and one over V (d x s m), on a copy of the basis split once into FP32 head and
+ *      tail arrays, in compensated FP32-pair arithmetic (about 2^-44 relative; FP64
+ *      FMAs would bound these products by the FP64 pipe).
+ * The iterate after j deflated steps minimises the A_mu-norm error over
+ * span(V) + K_j(P A_mu, r_0), P = I - A_mu V (V^T A_mu V)^{-1} V^T.
+ *   A      BK_DENSE, BK_GRAM, BK_CSR or BK_RBF; FP64 or FP32 values (promoted; FP32 dense
+ *          and Gram single-column products use the compensated FP32-pair kernels)
+ *   s_lock locked block steps, 1..16; (s_lock + 1)(1 + sketch) <= 768
+ *   b, x   d doubles (host or device); x is output
+ *   opts   sketch (>= 0; 0 gives CG with s_lock locked Lanczos vectors), seed, tol (stop
+ *          when the recurrence residual meets tol ||b|| and the FP64 residual recomputed
+ *          from the stored values confirms it; checked every check_every iterations),
+ *          max_loads (cap on s_lock + 1 + iterations, counting block loads as one)
+ *   info   loads (s_lock block loads, the load for r_0, one per iteration),
+ *          refinements (columns of the locked basis, s_lock m), residual_loads
+ *          (recomputed residual checks), rel_residual (recomputed)
+ * Returns BK_NOT_CONVERGED at the load cap (x holds the last iterate), BK_BREAKDOWN if
+ * T_s + mu I is not positive definite or p^T A_mu p or r^T r stopped being positive,
+ * BK_ERR_UNSUPPORTED if (s_lock + 1)(1 + sketch) > 768. */
+bk_status bk_solve_shrink(bk_ctx* ctx, const bk_operator* A, double mu, const double* b, double* x, int32_t s_lock,
+                          const bk_opts* opts, bk_info* info);
+
 /* Many independent systems (A_i + mu_i I) x_i = b_i of uneven size, i < n, solved
  * together (bk_solve on each, batched): systems are grouped by padded block width and
  * every step of the block-CG recurrence (Def. BCG) runs as one launch over all systems

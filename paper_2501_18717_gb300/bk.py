@@ -29,7 +29,8 @@ BK_PREC_FP64, BK_PREC_FP32, BK_PREC_F32X2 = 0, 1, 2
 EXPORTS = ("bk_default_opts", "bk_create", "bk_destroy", "bk_set_stream", "bk_status_string", "bk_last_error",
            "bk_solve",
            "bk_block_apply", "bk_gram", "bk_chol_solve", "bk_gaussian", "bk_block_apply_static", "bk_ridge_path",
-           "bk_sqrt_quadrature", "bk_sample", "bk_solve_batched", "bk_autotune")
+           "bk_sqrt_quadrature", "bk_sample", "bk_solve_batched", "bk_autotune", "bk_nystrom_pcg", "bk_sample_isqrt",
+           "bk_solve_shrink")
 
 
 class Operator(ctypes.Structure):
@@ -90,6 +91,8 @@ def _load():
         "bk_nystrom_pcg": (i32, [vp, ctypes.POINTER(Operator), dbl, vp, vp, i32, ctypes.POINTER(Opts),
                                  ctypes.POINTER(Info)]),
         "bk_sample_isqrt": (i32, [vp, ctypes.POINTER(Operator), dbl, i32, vp, vp, i32, ctypes.POINTER(Opts),
+                                  ctypes.POINTER(Info)]),
+        "bk_solve_shrink": (i32, [vp, ctypes.POINTER(Operator), dbl, vp, vp, i32, ctypes.POINTER(Opts),
                                   ctypes.POINTER(Info)]),
     }
     for name, (res, args) in sig.items():
@@ -317,6 +320,21 @@ def nystrom_pcg(ctx: Context, A: OperatorRef, mu: float, b, x, s_ny: int = 1, op
                             ctypes.byref(info))
     if check and s != BK_OK:
         raise BKError(s, "bk_nystrom_pcg", ctx.last_error())
+    return info
+
+
+def solve_shrink(ctx: Context, A: OperatorRef, mu: float, b, x, s_lock: int = 3, opts: Opts | None = None,
+                 check=True) -> Info:
+    """bk_solve_shrink: x ~= (A + mu I)^{-1} b by s_lock block steps on [b Omega], then
+    one-column deflated CG against the locked basis."""
+    info = Info()
+    pb, kb = _ptr(b)
+    px, kx = _ptr(x)
+    o = opts if opts is not None else default_opts()
+    s = _lib.bk_solve_shrink(ctx.handle, ctypes.byref(A.op), float(mu), pb, px, int(s_lock), ctypes.byref(o),
+                             ctypes.byref(info))
+    if check and s != BK_OK:
+        raise BKError(s, "bk_solve_shrink", ctx.last_error())
     return info
 
 

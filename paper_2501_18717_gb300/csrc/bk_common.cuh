@@ -180,6 +180,9 @@ int gemv_parts();
 // 3: sc[3] = a^T b. parts: pcg_parts() doubles.
 cudaError_t launch_dot_scalar(int kind, int64_t n, const double* a, const double* b, double* parts, double* sc,
                               cudaStream_t st);
+// the same with a^T (b + mu a); kind 4 (beta from sc[3], no dot) ignores a, b, mu
+cudaError_t launch_dot_shift_scalar(int kind, int64_t n, const double* a, const double* b, double mu, double* parts,
+                                    double* sc, cudaStream_t st);
 cudaError_t launch_pcg_xr(int64_t d, const double* sc, double mu, const double* p, const double* q, double* x,
                           double* r, double* parts, cudaStream_t st);
 cudaError_t launch_pcg_p(int64_t d, const double* sc, const double* z, double* p, cudaStream_t st);
@@ -189,6 +192,18 @@ cudaError_t launch_gemv_t(int64_t d, int r, const double* U, int64_t ldu, const 
                           cudaStream_t st);
 cudaError_t launch_gemv_n(int64_t d, int r, const double* U, int64_t ldu, const double* c, double* z,
                           cudaStream_t st);
+cudaError_t launch_defl_coef(int n, int m, const double* K, const double* g, double* out, cudaStream_t st);
+// Products with a d x nc basis held as FP32 head/tail arrays (column-major, ld ldv), in
+// compensated FP32-pair arithmetic (about 2^-44 relative): g = V^T r (parts:
+// defl_parts(d) x nc doubles) and z = r + V c (z may alias r).
+int defl_parts(int64_t d);
+cudaError_t launch_defl_t(int64_t d, int nc, const float* Vh, const float* Vl, int64_t ldv, const double* r,
+                          double* parts, double* g, cudaStream_t st);
+cudaError_t launch_defl_n(int64_t d, int nc, const float* Vh, const float* Vl, int64_t ldv, const double* coef,
+                          const double* r, double* z, int sms, cudaStream_t st);
+// p = r + V c + sc[2] p in one pass
+cudaError_t launch_defl_np(int64_t d, int nc, const float* Vh, const float* Vl, int64_t ldv, const double* coef,
+                           const double* sc, const double* r, double* p, int sms, cudaStream_t st);
 // ---- on-the-fly RBF kernel (k_rbf.cu): Y = K X, K_ij = exp(-|x_i - x_j|^2 / (2 l^2))
 // accurate to about 2^-46, compensated FP32-pair products; X is given as the FP32 head
 // and tail of an FP64 block (launch_split_f64, ldx a multiple of 4), Y d x N FP64.

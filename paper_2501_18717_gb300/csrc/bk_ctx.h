@@ -15,7 +15,7 @@ enum Slot {
   WS_OP_VALS, WS_OP_ROW, WS_OP_COL, WS_VALS_INNER, WS_NORMP, WS_TMP_IN, WS_TMP_OUT, WS_TMP_G, WS_TMP_S,
   // block-Lanczos drivers
   WS_LQ, WS_LW, WS_LV, WS_LC, WS_LSMALL, WS_LBAND, WS_LBWORK, WS_LZ, WS_LRHS, WS_LX, WS_LAX, WS_LRES, WS_LB0,
-  WS_LSHIFT, WS_LB64, WS_LQ2, WS_SPLIT, WS_TSM, WS_NYU, WS_PCG, WS_SPLITB,
+  WS_LSHIFT, WS_LB64, WS_LQ2, WS_SPLIT, WS_TSM, WS_NYU, WS_PCG, WS_SPLITB, WS_DEFL,
   // batched solver
   WS_BATCH, WS_BATCH_VALS,
   // tensor-core dense product: P^T head/tail, timeout flag

@@ -1128,3 +1128,237 @@ extern "C" bk_status bk_nystrom_pcg(bk_ctx* c, const bk_operator* A, double mu, 
   }
   return result;
 }
+
+namespace {
+
+// Cholesky of the symmetric band matrix T + mu I (bandwidth bw, Lb[r * n + c] = T(c + r, c),
+// n x (bw + 1) entries) in place: Lb then holds L with L L^T = T + mu I. A diagonal entry
+// of T that is exactly zero (a direction the block QR dropped: its row and column are
+// zero) is replaced by 1, which decouples it. Returns false on a non-positive pivot.
+bool host_band_chol(int n, int bw, std::vector<double>& Lb, double mu) {
+  for (int c = 0; c < n; ++c) Lb[c] = Lb[c] == 0.0 ? 1.0 : Lb[c] + mu;
+  for (int c = 0; c < n; ++c) {
+    const double x = Lb[c];
+    if (!(x > 0.0) || !std::isfinite(x)) return false;
+    const double l = std::sqrt(x);
+    Lb[c] = l;
+    const int w = std::min(bw, n - 1 - c);
+    for (int r = 1; r <= w; ++r) Lb[(size_t)r * n + c] /= l;
+    for (int a = 1; a <= w; ++a)
+      for (int b = 1; b <= a; ++b) Lb[(size_t)(a - b) * n + c + b] -= Lb[(size_t)a * n + c] * Lb[(size_t)b * n + c];
+  }
+  return true;
+}
+
+// y = (L L^T)^{-1} y for the factor of host_band_chol.
+void host_band_solve(int n, int bw, const std::vector<double>& Lb, double* y) {
+  for (int c = 0; c < n; ++c) {
+    double s = y[c];
+    for (int r = 1; r <= bw && c - r >= 0; ++r) s -= Lb[(size_t)r * n + c - r] * y[c - r];
+    y[c] = s / Lb[c];
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    double s = y[c];
+    for (int r = 1; r <= bw && c + r < n; ++r) s -= Lb[(size_t)r * n + c] * y[c + r];
+    y[c] = s / Lb[c];
+  }
+}
+
+}  // namespace
+
+extern "C" bk_status bk_solve_shrink(bk_ctx* c, const bk_operator* A, double mu, const double* b, double* x,
+                                     int32_t s_lock, const bk_opts* opts_in, bk_info* info) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!c || !b || !x || s_lock < 1 || s_lock > 16 || !(mu >= 0.0) || !std::isfinite(mu)) return BK_ERR_ARG;
+  err_ctx() = c;
+  c->last_error[0] = 0;
+  LzOp o;
+  bk_status s = check_pcg_operator(A, &o);
+  if (s != BK_OK) return s;
+  bk_opts opts;
+  if (opts_in)
+    opts = *opts_in;
+  else
+    bk_default_opts(&opts);
+  if (!(opts.tol > 0.0) || opts.sketch < 0 || opts.max_loads < 1 || opts.check_every < 1) return BK_ERR_ARG;
+  const int64_t d = o.d;
+  const int l = (int)std::min<int64_t>(opts.sketch, d - 1);
+  const int m = 1 + l;                 // block [b Omega]
+  const int n = s_lock * m;            // columns of the locked basis V
+  const int nb = n + m;                // columns of [V Q_s]
+  if (nb > 768) return BK_ERR_UNSUPPORTED;
+  BK_CK(cudaSetDevice(c->device));
+  cudaStream_t st = c->stream;
+  cudaEvent_t ev0, ev1;
+  BK_CK(cudaEventCreate(&ev0));
+  BK_CK(cudaEventCreate(&ev1));
+  BK_CK(cudaEventRecord(ev0, st));
+  Prof prof;  // with opts.profile: events around the one-column loads and the deflation
+  prof.on = opts.profile != 0;
+  prof.st = st;
+  BK_CK(stage_pcg_operator(c, A, &o));
+  const double* bd = nullptr;
+  BK_CK(stage_in(c, WS_B64, b, (size_t)d * 8, (const void**)&bd));
+  double* pw = nullptr;
+  BK_CK(ws_get(c, WS_PCG, (size_t)d * 5 * 8 + 4096 * 8, (void**)&pw));
+  double *xd = pw, *rd = pw + d, *zd = pw + 2 * d, *pd = pw + 3 * d, *qd = pw + 4 * d;
+  double* parts = pw + 5 * d;
+  double* sc = parts + bk::pcg_parts();
+  BK_CK(bk::launch_dot_scalar(3, d, bd, bd, parts, sc, st));
+  BK_CK(cudaMemcpyAsync(c->hparts, sc, 8 * 8, cudaMemcpyDeviceToHost, st));
+  BK_CK(cudaStreamSynchronize(st));
+  const double bnorm = std::sqrt(c->hparts[3]);
+  if (bnorm == 0.0) {
+    BK_CK(cudaMemsetAsync(xd, 0, (size_t)d * 8, st));
+    BK_CK(cudaMemcpyAsync(x, xd, (size_t)d * 8, cudaMemcpyDefault, st));
+    BK_CK(cudaStreamSynchronize(st));
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (info) info->status = BK_OK;
+    return BK_OK;
+  }
+
+  // --- block phase (Sec. CG_pro): s block-Lanczos steps with full reorthogonalisation on
+  // [b / ||b||, Omega / sqrt(d)] (the column scales change R_0, not the spans), giving
+  // V = [Q_0 .. Q_{s-1}] of K_s(A, [b Omega]), T_s = V^T A V and the Lanczos relation
+  // A V = V T_s + Q_s B_s E_s^T.
+  Lanczos lz;
+  BK_CK(lz.init(c, o, 1, m, s_lock));
+  double* B0 = nullptr;
+  BK_CK(ws_get(c, WS_LB0, (size_t)d * m * 8 + 4096 * 8, (void**)&B0));
+  double* scales = B0 + (size_t)d * m;
+  BK_CK(cudaMemcpyAsync(B0, bd, (size_t)d * 8, cudaMemcpyDeviceToDevice, st));
+  if (l > 0) BK_CK(bk::launch_gaussian(opts.seed, 3u, d * (int64_t)l, 0, B0 + d, st));
+  std::vector<double> hs(m, 1.0 / std::sqrt((double)d));
+  hs[0] = 1.0 / bnorm;
+  BK_CK(cudaMemcpyAsync(scales, hs.data(), (size_t)m * 8, cudaMemcpyHostToDevice, st));
+  BK_CK(bk::launch_scale_cols(1, d, m, d, scales, B0, st));
+  BK_CK(bk::launch_copy_cols(1, 1, d, m, B0, d, lz.W, lz.ldq, st));
+  BK_CK(lz.start(lz.W));
+  for (int k = 0; k < s_lock; ++k) BK_CK(lz.step());
+  // [Q_0 .. Q_s] split once into FP32 head and tail arrays (column-major, ld ldq): the
+  // products with the locked basis then run in compensated FP32-pair arithmetic
+  float* Vh = nullptr;
+  BK_CK(ws_get(c, WS_DEFL, (size_t)2 * lz.ldq * nb * 4 + 256, (void**)&Vh));
+  float* Vl = Vh + (size_t)lz.ldq * nb;
+  BK_CK(bk::launch_split_f64(d, nb, (const double*)lz.Q, lz.ldq, Vh, Vl, lz.ldq, st));
+
+  // --- small host work: (T_s + mu I) = L L^T, y_0 = (T_s + mu I)^{-1} V^T b and
+  // K = (T_s + mu I)^{-1} E_s B_s^T (n x m), so that for any r
+  //   (T_s + mu I)^{-1} (A_mu V)^T r = V^T r + K Q_s^T r.
+  double* small = nullptr;
+  BK_CK(ws_get(c, WS_NYU, ((size_t)n * m + 2 * (size_t)nb + n + 64) * 8, (void**)&small));
+  double* Kd = small;
+  double* g = Kd + (size_t)n * m;     // [V Q_s]^T r  (nb)
+  double* coef = g + nb;              // -(V^T r + K Q_s^T r)  (n)
+  double* y0 = coef + n;              // n
+  double* gparts = nullptr;
+  BK_CK(ws_get(c, WS_SPLIT, (size_t)bk::defl_parts(d) * nb * 8 + 4096, (void**)&gparts));
+  BK_CK(bk::launch_defl_t(d, n, Vh, Vl, lz.ldq, bd, gparts, g, st));
+  std::vector<double> hband((size_t)(m + 1) * lz.ldb()), hB((size_t)m * m), hg(n);
+  BK_CK(cudaMemcpyAsync(hband.data(), lz.band, hband.size() * 8, cudaMemcpyDeviceToHost, st));
+  BK_CK(cudaMemcpyAsync(hB.data(), lz.Bk, hB.size() * 8, cudaMemcpyDeviceToHost, st));
+  BK_CK(cudaMemcpyAsync(hg.data(), g, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+  BK_CK(cudaStreamSynchronize(st));
+  std::vector<double> Lb((size_t)(m + 1) * n, 0.0);
+  for (int r = 0; r <= m; ++r)
+    for (int col = 0; col + r < n; ++col) Lb[(size_t)r * n + col] = hband[(size_t)r * lz.ldb() + col];
+  if (!host_band_chol(n, m, Lb, mu)) {
+    std::snprintf(c->last_error, sizeof(c->last_error), "T_s + mu I not positive definite");
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    return BK_BREAKDOWN;
+  }
+  host_band_solve(n, m, Lb, hg.data());
+  std::vector<double> hK((size_t)n * m, 0.0);
+  for (int q = 0; q < m; ++q) {
+    double* col = hK.data() + (size_t)q * n;
+    // column q of E_s B_s^T: B_s(q, i) in row n - m + i (B_s row-major)
+    for (int i = 0; i < m; ++i) col[n - m + i] = hB[(size_t)q * m + i];
+    host_band_solve(n, m, Lb, col);
+  }
+  BK_CK(cudaMemcpyAsync(Kd, hK.data(), hK.size() * 8, cudaMemcpyHostToDevice, st));
+  BK_CK(cudaMemcpyAsync(y0, hg.data(), (size_t)n * 8, cudaMemcpyHostToDevice, st));
+
+  // --- x_0 = V y_0 (the block-CG iterate after s loads), r_0 = b - A_mu x_0 (one load)
+  double* Vw = nullptr;
+  if (o.kind == BK_GRAM) BK_CK(ws_get(c, WS_LB64, (size_t)o.nrows * 8, (void**)&Vw));
+  BK_CK(cudaMemsetAsync(xd, 0, (size_t)d * 8, st));
+  BK_CK(bk::launch_defl_n(d, n, Vh, Vl, lz.ldq, y0, xd, xd, c->sms, st));
+  BK_CK(apply_fp64(c, o, xd, d, 1, qd, Vw, true));
+  BK_CK(bk::launch_axpy(d, mu, xd, qd, st));
+  BK_CK(cudaMemcpyAsync(rd, bd, (size_t)d * 8, cudaMemcpyDeviceToDevice, st));
+  BK_CK(bk::launch_axpy(d, -1.0, qd, rd, st));
+  // The direction p = r - V (V^T r + K Q_s^T r) + beta p is A_mu-orthogonal to V (Def-CG
+  // with the coefficients from the Lanczos relation); one pass over [V Q_s] for the
+  // coefficients, one over V for the update.
+  auto direction = [&]() -> cudaError_t {
+    cudaError_t e = bk::launch_defl_t(d, nb, Vh, Vl, lz.ldq, rd, gparts, g, st);
+    if (e != cudaSuccess) return e;
+    if ((e = bk::launch_defl_coef(n, m, Kd, g, coef, st)) != cudaSuccess) return e;
+    return bk::launch_defl_np(d, n, Vh, Vl, lz.ldq, coef, sc, rd, pd, c->sms, st);
+  };
+  BK_CK(cudaMemsetAsync(sc, 0, 16 * 8, st));  // beta = 0 and no breakdown for p_0
+  BK_CK(cudaMemsetAsync(pd, 0, (size_t)d * 8, st));
+  BK_CK(direction());
+  BK_CK(bk::launch_dot_scalar(2, d, rd, rd, parts, sc, st));  // rz := r^T r
+
+  // --- one-column deflated CG; scalars stay on the device. r_0 was formed from the
+  // stored values, so x_0 may already meet tol (a locked basis that spans R^d).
+  int loads = lz.loads + 1, iters = 0, checks = 0;
+  bk_status result = BK_NOT_CONVERGED;
+  BK_CK(cudaMemcpyAsync(c->hparts, sc, 8, cudaMemcpyDeviceToHost, st));
+  BK_CK(cudaStreamSynchronize(st));
+  double rel = std::sqrt(c->hparts[0]) / bnorm;
+  if (rel <= opts.tol) result = BK_OK;
+  double* rtrue = qd;
+  while (result != BK_OK && loads < opts.max_loads) {
+    prof.begin();
+    BK_CK(apply_fp64(c, o, pd, d, 1, qd, Vw, true));  // q = A p
+    prof.end(BK_K_OPERATOR);
+    ++loads;
+    ++iters;
+    BK_CK(bk::launch_dot_shift_scalar(0, d, pd, qd, mu, parts, sc, st));  // alpha = r^T r / p^T A_mu p
+    BK_CK(bk::launch_pcg_xr(d, sc, mu, pd, qd, xd, rd, parts, st));       // x, r and rr = r^T r
+    BK_CK(bk::launch_dot_shift_scalar(4, d, nullptr, nullptr, 0.0, parts, sc, st));  // beta = rr / rz
+    prof.begin();
+    BK_CK(direction());
+    prof.end(BK_K_ORTH);
+    if (iters % opts.check_every != 0 && loads < opts.max_loads) continue;
+    BK_CK(cudaMemcpyAsync(c->hparts, sc, 8 * 8, cudaMemcpyDeviceToHost, st));
+    BK_CK(cudaStreamSynchronize(st));
+    if (c->hparts[5] != 0.0) {
+      result = BK_BREAKDOWN;
+      break;
+    }
+    if (std::sqrt(c->hparts[3]) > opts.tol * bnorm && loads < opts.max_loads) continue;
+    // the recurrence residual met tol (or the cap): confirm with the FP64 residual
+    BK_CK(apply_fp64(c, o, xd, d, 1, rtrue, Vw, true));
+    BK_CK(bk::launch_axpy(d, mu, xd, rtrue, st));
+    BK_CK(bk::launch_axpy(d, -1.0, bd, rtrue, st));
+    BK_CK(bk::launch_dot_scalar(3, d, rtrue, rtrue, parts, sc + 8, st));
+    BK_CK(cudaMemcpyAsync(c->hparts, sc + 8, 8 * 8, cudaMemcpyDeviceToHost, st));
+    BK_CK(cudaStreamSynchronize(st));
+    rel = std::sqrt(c->hparts[3]) / bnorm;
+    ++checks;
+    if (rel <= opts.tol) result = BK_OK;
+    if (loads >= opts.max_loads) break;
+  }
+  BK_CK(cudaMemcpyAsync(x, xd, (size_t)d * 8, cudaMemcpyDefault, st));
+  BK_CK(cudaEventRecord(ev1, st));
+  BK_CK(cudaEventSynchronize(ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  prof.report(info);
+  if (info) {
+    info->status = result;
+    info->loads = loads;
+    info->refinements = n;  // columns of the locked basis
+    info->residual_loads = checks;
+    info->rel_residual = rel;
+    info->ms_total = ms;
+  }
+  return result;
+}
