@@ -926,7 +926,8 @@ def run_shrink(args, world, rank, local, dev):
             "vs_baseline": None, "dtype": "f64 (locked basis, deflated CG; FP64 CSR values)", "data": "synthetic",
             "config": {"workload": workload_name(args.grid, d, int(va.shape[0])), "sketch_l": SKETCH, "s_lock": head_s,
                        "tol": TOL, "mu": MU,
-                       "l2": "locked basis 2.2 GB, larger than L2; no flush"},
+                       "l2": f"locked basis {8.0 * d * nb / 1e9:.2f} GB (FP32 head + tail), "
+                             + ("larger than L2; no flush" if 8.0 * d * nb > 2e8 else "L2-resident")},
             "methods": rows, "groups": groups,
             "roofline": {"bound": "hbm", "kernel": f"deflation products [V Q_s]^T r ({nb} cols) and p = r + V c + beta p "
                                                    f"({n_lock} cols), FP32 head/tail basis, k_defl_t + k_defl_reduce + "

@@ -100,3 +100,27 @@ def test_sample_full_size_fp32_floor(bk, ctx):
     info = bk.sample(ctx, bk.dense_operator(K), 1e-6, Bt.T, S.T, 32,
                      bk.default_opts(tol=1e-6, inner="f32x2", check_every=4, max_loads=16), check=False)
     assert info.status == bk.BK_BREAKDOWN, info.as_dict()
+
+
+def test_shrink_full_size(bk, ctx):
+    """The 128^3 diffusion system (d = 2,097,152, FP64 CSR values, mu 1e-4) as the
+    shrink leg of bench.py runs it: one block step on [b Omega] (33 columns) locks V,
+    then one-column deflated CG to 1e-8. The oracle recomputes b - A_mu x in FP64 from
+    the stored CSR values; the iterate must also beat the block-CG iterate after the
+    single locked step (x_0) by many orders."""
+    seed, omega_seed, grid = W.BASE_SEED + 2, W.BASE_SEED + 3, 128  # the bench's seeds
+    rp, ci, va, d = W.diffusion_csr(seed, grid)
+    b = W.normals(seed, W.STREAM_RHS, d)
+    mu = 1e-4
+    op = bk.csr_operator(torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda(), torch.from_numpy(va).cuda())
+    x = torch.zeros(d, dtype=torch.float64, device="cuda")
+    info = bk.solve_shrink(ctx, op, mu, torch.from_numpy(b).cuda(), x, 1,
+                           bk.default_opts(tol=1e-8, sketch=32, seed=omega_seed, check_every=32, max_loads=20000))
+    A = operators.CSR(rp, ci, va)
+    res = direct.rel_residual(A, mu, x.cpu().numpy(), b)
+    assert res <= 1e-8, (res, info.as_dict())
+    assert info.refinements == 33 and info.loads < 4000, info.as_dict()
+    x0 = torch.zeros(d, dtype=torch.float64, device="cuda")
+    bk.solve_shrink(ctx, op, mu, torch.from_numpy(b).cuda(), x0, 1,
+                    bk.default_opts(tol=1e-30, sketch=32, seed=omega_seed, max_loads=2), check=False)
+    assert direct.rel_residual(A, mu, x0.cpu().numpy(), b) > 1e3 * res
