@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="diffusion", choices=["diffusion", "batched", "dense-product", "ridge",
-                                                                 "sample", "nystrom", "shrink"])
+                                                                 "sample", "nystrom", "shrink", "csr-product"])
     ap.add_argument("--ridge-n", type=int, default=200000)
     ap.add_argument("--ridge-d", type=int, default=4096)
     ap.add_argument("--sample-d", type=int, default=40000)
@@ -363,6 +363,59 @@ def run_batched(args, world, rank, local, dev):
             "fp64_plain": fp64, "clocks": clk.summary(), "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_csr_product(args, world, rank, local, dev):
+    """One block product of the diffusion operator with its Gram, Y = A P + mu P and
+    P^T Y (FP32 values, 33 columns in 36-wide panels), through bk_block_apply: the
+    operator kernel of the headline solve in isolation, for a small ncu capture.
+    value = algorithmic GB/s per call (CUDA events around the calls, so each includes
+    the call's host synchronisation)."""
+    import torch
+    from paper_2501_18717_gb300 import bk
+
+    rp, ci, va, d = W.diffusion_csr(SEED, args.grid)
+    m = SKETCH + 1
+    ld = (d + 31) // 32 * 32
+    nq = (m + 3) // 4
+    g = torch.Generator(device=dev)
+    g.manual_seed(BATCH_SEED)
+    P = torch.randn((nq, ld, 4), device=dev, dtype=torch.float32, generator=g)
+    P[:, d:, :] = 0
+    if m % 4:
+        P[-1, :, m % 4:] = 0
+    Y = torch.zeros_like(P)
+    G = torch.zeros((m, m), dtype=torch.float64, device=dev)
+    ctx = bk.Context(local)
+    stream = torch.cuda.Stream(dev)
+    ctx.set_stream(stream.cuda_stream)
+    op = bk.csr_operator(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev),
+                         torch.from_numpy(va.astype(np.float32)).to(dev))
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            bk.block_apply(ctx, op, MU, P, Y, G, m, ld)
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            bk.block_apply(ctx, op, MU, P, Y, G, m, ld)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    nnz = int(va.shape[0])
+    gb = (8.0 * nnz + 4.0 * (d + 1) + 2 * 4.0 * d * 36) / 1e9  # the operator's per-launch bytes
+    gbs = gb / (ms / 1e3)
+    peak, src = measured_peaks()
+    if rank == 0:
+        print(json.dumps({"metric": "CSR block product + Gram (operator kernel), algorithmic GB/s per call",
+                          "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": workload_name(args.grid, d, nnz), "block_width": m},
+                          "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                       "frac": gbs / peak, "traffic": None, "peak_source": src}}), flush=True)
     ctx.close()
     return 0
 
@@ -965,6 +1018,8 @@ def main():
         return run_nystrom(args, world, rank, local, dev)
     if args.workload == "shrink":
         return run_shrink(args, world, rank, local, dev)
+    if args.workload == "csr-product":
+        return run_csr_product(args, world, rank, local, dev)
 
     def barrier():
         if world > 1:
