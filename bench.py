@@ -174,6 +174,25 @@ def dist_init():
     return world, rank, local
 
 
+def max_over_ranks(x, dev=None):
+    """The maximum of a host number over the ranks of the default process group (the
+    slowest replica bounds the job); the number itself without one. dev is the device
+    of the collective's buffer (a CUDA device for NCCL, None for gloo on the host)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev if dev is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, steps, ms):
+    """Whole-job solves/s of `world` independent replicas, each timing `steps` solves,
+    from the slowest replica's time in ms."""
+    return world * steps / (ms / 1e3)
+
+
 # ---------------------------------------------------------------------------------- oracle
 def oracle_sample(rp, ci, va, b, seconds, max_loads=60):
     """Time the FP64 oracle's block-CG recurrence on the full workload for a bounded
@@ -1059,13 +1078,8 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize(dev)
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
+    value = replica_throughput(world, args.steps, ms)
     rel_res = max(i.rel_residual for i in infos)
     loads = [i.loads for i in infos]
 
@@ -1130,11 +1144,7 @@ def main():
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dev)
     h2d = rp.nbytes + ci.nbytes + va.nbytes + b.nbytes
     d2h = d * 8
 
