@@ -100,3 +100,29 @@ def test_shrink_edge_cases(bk, ctx):
         bk.solve_shrink(ctx, bk.dense_operator(np.eye(400)), 0.0, np.ones(400), np.zeros(400), 3,
                         bk.default_opts(sketch=200))
     assert e.value.status == bk.BK_ERR_UNSUPPORTED
+
+
+def test_shrink_dense_fp32_values(bk, ctx):
+    """Dense FP32 values (single-column products through the compensated FP32-pair
+    kernels): 1e-10 in the oracle's residual of the stored matrix promoted to FP64."""
+    a, b = _problem(d=320)
+    a32 = np.ascontiguousarray(a.astype(np.float32))
+    x = np.zeros(320)
+    info = bk.solve_shrink(ctx, bk.dense_operator(torch.from_numpy(a32).cuda()), 1e-3, b, x, 2,
+                           bk.default_opts(tol=1e-10, sketch=12, seed=66, max_loads=3000, check_every=4))
+    res = direct.rel_residual(operators.Dense(a32.astype(np.float64)), 1e-3, x, b)
+    assert res <= 1e-10, (res, info.as_dict())
+
+
+def test_shrink_rbf_operator(bk, ctx):
+    """The kernel matrix formed on the fly (BK_RBF, 500 points, lengthscale 0.2): 1e-10
+    in the residual the oracle recomputes from its FP64 kernel matrix."""
+    d, mu = 500, 1e-3
+    pts = W.rbf_points(W.BASE_SEED + 67, d)
+    K = W.rbf_kernel(pts)
+    b = W.normals(W.BASE_SEED + 67, W.STREAM_RHS, d)
+    x = np.zeros(d)
+    info = bk.solve_shrink(ctx, bk.rbf_operator(torch.from_numpy(pts).cuda(), 0.2), mu, b, x, 2,
+                           bk.default_opts(tol=1e-10, sketch=16, seed=68, max_loads=5000, check_every=4))
+    res = direct.rel_residual(operators.Dense(K), mu, x, b)
+    assert res <= 1e-10, (res, info.as_dict())
