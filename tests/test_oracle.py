@@ -411,3 +411,17 @@ def test_shrink_start_and_inclusion(s):
     for j in range(1, 9):
         xb = lanczos.shifted_iterates(lanczos.block_lanczos(a, B, s + j), [mu])[:, 0]
         assert anorm(xstar - xb) <= (1 + 1e-7) * anorm(xstar - xs[j]) + 1e-12 * anorm(xstar), (s, j)
+
+
+@pytest.mark.parametrize("s", [1, 3, 5])
+def test_shrink_one_column_block_is_cg(s):
+    """Sec. CG_pro: with a one-column block (no Omega) the locked space is K_s(A, b),
+    and span(W) + K_j(P A_mu, r_0) = K_{s+j}(A, b), so the shrunk iterate after j
+    deflated steps is CG's iterate after s + j steps (SciPy's CG)."""
+    d, mu = 60, 0.05
+    a = spd(d, np.linspace(1.0, 8.0, d), 25)
+    b = W.normals(25, 2, d)
+    xs = deflated.shrink_solve(a, mu, b, np.zeros((d, 0)), s, 6)
+    for j in [0, 2, 6]:
+        ref, _ = spla.cg(a + mu * np.eye(d), b, x0=np.zeros(d), maxiter=s + j, rtol=0.0, atol=0.0)
+        assert rel(xs[j], ref) < 1e-10, (s, j)
