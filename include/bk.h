@@ -234,7 +234,9 @@ bk_status bk_sample_isqrt(bk_ctx* ctx, const bk_operator* K, double nugget, int3
  * from the sketch Omega of opts (d x sketch Gaussian, the same Philox key and stream as
  * bk_solve's, so both methods see the same Omega), theta = its smallest eigenvalue
  * (Sec. 7), P^{-1} = (theta + mu) U (D + mu)^{-1} U^T + (I - U U^T), then PCG from
- * x = 0 on (A + mu I) x = b, everything in FP64 on the device. The approximation comes
+ * x = 0 on (A + mu I) x = b, on the device: vectors and scalars in FP64, the
+ * preconditioner's products with U in compensated FP32-pair arithmetic on a copy of U
+ * split once into FP32 head and tail arrays (about 2^-44 relative). The approximation comes
  * from s_ny block-Lanczos steps on Omega (s_ny loads): with V = [Q_0 .. Q_{s-1}] and the
  * Lanczos relation A V = V T + Q_s B E_s^T, the factor F = A V (V^T A V)^{+1/2} is
  * [V Q_s] H for a small H, so U and D follow from two small eigendecompositions on

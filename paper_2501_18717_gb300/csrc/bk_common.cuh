@@ -175,7 +175,6 @@ size_t tsm_tn_work_bytes(int64_t R, int64_t D, int N, int df, int sms);
 cudaError_t launch_csr_cols(int vals_f64, int64_t d, const int* rowptr, const int* colidx, const void* vals, int nc,
                             const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t st);
 int pcg_parts();
-int gemv_parts();
 // kind 0: sc[1] = sc[0] / (a^T b); 1: sc[2] = (a^T b) / sc[0], sc[0] = a^T b; 2: sc[0] = a^T b;
 // 3: sc[3] = a^T b. parts: pcg_parts() doubles.
 cudaError_t launch_dot_scalar(int kind, int64_t n, const double* a, const double* b, double* parts, double* sc,
@@ -187,11 +186,6 @@ cudaError_t launch_pcg_xr(int64_t d, const double* sc, double mu, const double* 
                           double* r, double* parts, cudaStream_t st);
 cudaError_t launch_pcg_p(int64_t d, const double* sc, const double* z, double* p, cudaStream_t st);
 cudaError_t launch_scale_vec(int n, const double* f, double* c, cudaStream_t st);
-// c = U^T v (parts: gemv_parts() x r doubles), z += U c; r <= 768
-cudaError_t launch_gemv_t(int64_t d, int r, const double* U, int64_t ldu, const double* v, double* parts, double* c,
-                          cudaStream_t st);
-cudaError_t launch_gemv_n(int64_t d, int r, const double* U, int64_t ldu, const double* c, double* z,
-                          cudaStream_t st);
 cudaError_t launch_defl_coef(int n, int m, const double* K, const double* g, double* out, cudaStream_t st);
 // Products with a d x nc basis held as FP32 head/tail arrays (column-major, ld ldv), in
 // compensated FP32-pair arithmetic (about 2^-44 relative): g = V^T r (parts:

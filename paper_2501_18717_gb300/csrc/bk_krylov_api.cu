@@ -1049,15 +1049,21 @@ extern "C" bk_status bk_nystrom_pcg(bk_ctx* c, const bk_operator* A, double mu, 
   BK_CK(cudaMemcpyAsync(Gd, Gc.data(), Gc.size() * 8, cudaMemcpyHostToDevice, st));
   BK_CK(cudaMemcpyAsync(fd, f.data(), f.size() * 8, cudaMemcpyHostToDevice, st));
   BK_CK(bk::launch_gemm(1, d, r, nb, 1.0, lz.Q, 1, 1, lz.ldq, Gd, 1, nb, 0.0, U, d, st));
+  // U split once into FP32 head and tail arrays: its two products per iteration then run
+  // in compensated FP32-pair arithmetic (about 2^-44 relative) and are bound by HBM, not
+  // by the FP64 pipe
+  float* Uh = nullptr;
+  BK_CK(ws_get(c, WS_DEFL, (size_t)2 * d * r * 4 + 256, (void**)&Uh));
+  float* Ul = Uh + (size_t)d * r;
+  BK_CK(bk::launch_split_f64(d, r, U, d, Uh, Ul, d, st));
   double* gparts = nullptr;
-  BK_CK(ws_get(c, WS_SPLIT, (size_t)bk::gemv_parts() * r * 8 + 4096, (void**)&gparts));
+  BK_CK(ws_get(c, WS_SPLIT, (size_t)bk::defl_parts(d) * r * 8 + 4096, (void**)&gparts));
   auto precond = [&](const double* rin, double* zout) -> cudaError_t {
     // z = r + U diag(f) U^T r  ==  (theta + mu) U (D + mu)^{-1} U^T r + (I - U U^T) r
-    cudaError_t e = bk::launch_gemv_t(d, r, U, d, rin, gparts, cv, st);
+    cudaError_t e = bk::launch_defl_t(d, r, Uh, Ul, d, rin, gparts, cv, st);
     if (e != cudaSuccess) return e;
     if ((e = bk::launch_scale_vec(r, fd, cv, st)) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(zout, rin, (size_t)d * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
-    return bk::launch_gemv_n(d, r, U, d, cv, zout, st);
+    return bk::launch_defl_n(d, r, Uh, Ul, d, cv, rin, zout, c->sms, st);
   };
   double* Vw = nullptr;
   if (o.kind == BK_GRAM) BK_CK(ws_get(c, WS_LB64, (size_t)o.nrows * 8, (void**)&Vw));

@@ -1,5 +1,7 @@
-// Kernels of the Nystrom-preconditioned CG comparator (Def. PCG with the preconditioner
-// of Eq. precond_def; the comparison of Thm. main), all FP64:
+// Kernels of the one-column solvers: the Nystrom-preconditioned CG comparator (Def. PCG
+// with the preconditioner of Eq. precond_def; the comparison of Thm. main) and the
+// one-column phase of the shrunk block-CG. Vectors and scalars are FP64; products with
+// a stored basis (U of the preconditioner, the locked basis) use its FP32 head/tail copy.
 //   k_csr_cols   Y = A X for CSR A and a column-major block X (the block products that
 //                build the Nystrom approximation, and the single-vector products of PCG)
 //   k_dot_parts  per-CTA partials of a^T b
@@ -8,14 +10,13 @@
 //   k_pcg_xr     x += alpha p, r -= alpha (q + mu p), partials of ||r||^2
 //   k_pcg_p      p = z + beta p
 //   k_scale_vec  c_i *= f_i (the preconditioner's diagonal on U^T r)
-//   k_gemv_t     per-CTA partials of U^T v (U d x r column-major), reduced in CTA order
-//   k_gemv_n     z += U c
 //   k_defl_coef  the deflation coefficients of the shrunk block-CG (one-column Def-CG on
 //                the locked basis): out = -(g_V + K g_Q)
-//   k_defl_t     per-CTA partials of V^T r against the locked basis held as FP32
-//                head/tail arrays, in compensated FP32-pair arithmetic
+//   k_defl_t     per-CTA partials of V^T r for a basis V held as FP32 head/tail arrays
+//                (U or the locked basis), in compensated FP32-pair arithmetic
 //   k_defl_reduce  their sum over CTAs
 //   k_defl_n     z = r + V c, the same arithmetic
+//   k_defl_np    p = r + V c + beta p (the shrunk solver's direction update)
 #include <algorithm>
 
 #include "bk_common.cuh"
@@ -122,72 +123,6 @@ __global__ void k_pcg_p(int64_t d, const double* __restrict__ sc, const double* 
 
 __global__ void k_scale_vec(int n, const double* __restrict__ f, double* c) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) c[i] *= f[i];
-}
-
-// U^T v partials: columns in chunks of 8; each thread accumulates its rows for the 8
-// columns of a chunk in registers (8 independent loads per row in flight), then the
-// warp reduces them once and writes its sums to shared memory; the CTA adds its warps
-// in a fixed order and writes parts[cta][j].
-constexpr int kGemvCh = 8;
-__global__ void k_gemv_t(int64_t d, int r, const double* __restrict__ U, int64_t ldu, const double* __restrict__ v,
-                         double* parts) {
-  extern __shared__ double wacc[];  // [warps][r]
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int j0 = 0; j0 < r; j0 += kGemvCh) {
-    double acc[kGemvCh];
-#pragma unroll
-    for (int u = 0; u < kGemvCh; ++u) acc[u] = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d; i += stride) {
-      const double vi = v[i];
-#pragma unroll
-      for (int u = 0; u < kGemvCh; ++u)
-        if (j0 + u < r) acc[u] = fma(U[i + (int64_t)(j0 + u) * ldu], vi, acc[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < kGemvCh; ++u) {
-      double s = acc[u];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0 && j0 + u < r) wacc[w * r + j0 + u] = s;
-    }
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < r; j += blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < nw; ++k) s += wacc[k * r + j];
-    parts[(size_t)blockIdx.x * r + j] = s;
-  }
-}
-
-// c[j] = sum over CTAs of parts[cta][j]: one warp per column, lanes stride over the
-// CTAs, then a fixed shuffle tree (deterministic).
-__global__ void k_gemv_t_reduce(int r, int nparts, const double* __restrict__ parts, double* c) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= r) return;
-  double s = 0.0;
-  for (int k = lane; k < nparts; k += 32) s += parts[(size_t)k * r + warp];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) c[warp] = s;
-}
-
-// z += U c: thread per row, 8 columns of loads in flight per step.
-__global__ void k_gemv_n(int64_t d, int r, const double* __restrict__ U, int64_t ldu, const double* __restrict__ c,
-                         double* z) {
-  extern __shared__ double sc_[];
-  for (int j = threadIdx.x; j < r; j += blockDim.x) sc_[j] = c[j];
-  __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = z[i];
-    for (int j0 = 0; j0 < r; j0 += kGemvCh) {
-      double uv[kGemvCh];
-#pragma unroll
-      for (int u = 0; u < kGemvCh; ++u) uv[u] = j0 + u < r ? U[i + (int64_t)(j0 + u) * ldu] : 0.0;
-#pragma unroll
-      for (int u = 0; u < kGemvCh; ++u)
-        if (j0 + u < r) s = fma(uv[u], sc_[j0 + u], s);
-    }
-    z[i] = s;
-  }
 }
 
 // out[i] = -(g[i] + sum_q K[i + q n] g[n + q]), i < n: minus the coefficients mu_j of
@@ -317,7 +252,6 @@ __global__ void __launch_bounds__(256) k_defl_np(int64_t d, int nc, const float*
 }  // namespace
 
 int pcg_parts() { return 1216; }  // 8 CTAs of 256 threads per SM on 152 SMs
-int gemv_parts() { return 1216; }  // 8 CTAs of 256 threads per SM on 152 SMs
 
 cudaError_t launch_csr_cols(int vals_f64, int64_t d, const int* rowptr, const int* colidx, const void* vals, int nc,
                             const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t st) {
@@ -372,27 +306,6 @@ cudaError_t launch_scale_vec(int n, const double* f, double* c, cudaStream_t st)
 }  // namespace bk
 
 namespace bk {
-
-cudaError_t launch_gemv_t(int64_t d, int r, const double* U, int64_t ldu, const double* v, double* parts, double* c,
-                          cudaStream_t st) {
-  if (r <= 0) return cudaSuccess;
-  const size_t smem = (size_t)(kPcgThreads / 32) * r * 8;
-  if (smem > 48 * 1024) return cudaErrorInvalidValue;
-  k_gemv_t<<<gemv_parts(), kPcgThreads, smem, st>>>(d, r, U, ldu, v, parts);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_gemv_t_reduce<<<(r * 32 + 255) / 256, 256, 0, st>>>(r, gemv_parts(), parts, c);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gemv_n(int64_t d, int r, const double* U, int64_t ldu, const double* c, double* z,
-                          cudaStream_t st) {
-  if (r <= 0) return cudaSuccess;
-  if ((size_t)r * 8 > 48 * 1024) return cudaErrorInvalidValue;
-  const int grid = (int)std::min<int64_t>((d + kPcgThreads - 1) / kPcgThreads, 4096);
-  k_gemv_n<<<grid, kPcgThreads, (size_t)r * 8, st>>>(d, r, U, ldu, c, z);
-  return cudaGetLastError();
-}
 
 }  // namespace bk
 
