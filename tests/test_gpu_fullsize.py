@@ -124,3 +124,23 @@ def test_shrink_full_size(bk, ctx):
     bk.solve_shrink(ctx, op, mu, torch.from_numpy(b).cuda(), x0, 1,
                     bk.default_opts(tol=1e-30, sketch=32, seed=omega_seed, max_loads=2), check=False)
     assert direct.rel_residual(A, mu, x0.cpu().numpy(), b) > 1e3 * res
+
+
+@pytest.mark.parametrize("inner,tol", [("fp32", 1e-8), ("fp64", 1e-10)])
+def test_headline_solve_full_size(bk, ctx, inner, tol):
+    """The headline system as bench.py times it: 128^3 diffusion (d = 2,097,152, FP64 CSR
+    values), mu 1e-4, Omega of 32 columns, FP32 blocks with FP64 refinement (tol 1e-8)
+    or FP64 blocks (tol 1e-10). The oracle recomputes b - A_mu x in FP64 from the stored
+    CSR values (a property that holds at any size)."""
+    seed, omega_seed, grid = W.BASE_SEED + 2, W.BASE_SEED + 3, 128  # the bench's seeds
+    rp, ci, va, d = W.diffusion_csr(seed, grid)
+    b = W.normals(seed, W.STREAM_RHS, d)
+    mu = 1e-4
+    op = bk.csr_operator(torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda(), torch.from_numpy(va).cuda())
+    x = torch.zeros(d, dtype=torch.float64, device="cuda")
+    info = bk.solve(ctx, op, mu, torch.from_numpy(b).cuda(), x,
+                    bk.default_opts(tol=tol, sketch=32, seed=omega_seed, inner=inner,
+                                    inner_tol=1e-5 if inner == "fp32" else 1e-6, check_every=16))
+    res = direct.rel_residual(operators.CSR(rp, ci, va), mu, x.cpu().numpy(), b)
+    assert res <= tol, (res, info.as_dict())
+    assert info.loads < 2000, info.as_dict()
