@@ -144,3 +144,29 @@ def test_headline_solve_full_size(bk, ctx, inner, tol):
     res = direct.rel_residual(operators.CSR(rp, ci, va), mu, x.cpu().numpy(), b)
     assert res <= tol, (res, info.as_dict())
     assert info.loads < 2000, info.as_dict()
+
+
+def test_batched_full_size(bk, ctx):
+    """The batched workload at full size: 512 uneven FP32 systems (d log-uniform in
+    [500, 16000], 75 GB of matrices) solved together in mixed precision to 1e-8 (block
+    width 17 for every system instead of the autotuner's pick). The oracle recomputes
+    the FP64 residual from the stored FP32 values of three sampled systems (the
+    smallest, a median and the largest)."""
+    seed = W.BASE_SEED + 5  # the bench's batch seed
+    ds = [int(v) for v in W.batch_sizes(seed, 512)]
+    dev = torch.device("cuda:0")
+    mats, bs = [], []
+    for i, d in enumerate(ds):
+        A, b = W.batch_system_torch(seed, i, d, dev)
+        mats.append(A)
+        bs.append(b)
+    xs = [torch.zeros(d, dtype=torch.float64, device=dev) for d in ds]
+    infos = bk.solve_batched(ctx, bk.Batch(mats, np.zeros(len(ds)), bs, xs),
+                             bk.default_opts(tol=1e-8, sketch=16, seed=W.BASE_SEED + 3, inner="fp32",
+                                             inner_tol=1e-5, check_every=16))
+    assert all(i.status == bk.BK_OK for i in infos)
+    order = np.argsort(ds)
+    for i in (int(order[0]), int(order[len(ds) // 2]), int(order[-1])):
+        A = mats[i].cpu().numpy().astype(np.float64)
+        res = direct.rel_residual(operators.Dense(A), 0.0, xs[i].cpu().numpy(), bs[i].cpu().numpy())
+        assert res <= 1e-8, (i, ds[i], res, infos[i].as_dict())
