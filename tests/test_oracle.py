@@ -144,6 +144,24 @@ def test_refined_solve_reaches_tolerance():
     out = bcg.refined_solve(a, 1e-3, b, om, tol=1e-11, inner_tol=1e-6)
     assert out["rel_residual"] <= 1e-11
     assert direct.rel_residual(operators.Dense(a), 1e-3, out["x"], b) <= 1e-11
+    assert out["loads"] == out["inner_loads"] + out["refinements"]
+
+
+def test_refined_solve_adaptive_inner_target():
+    """With the adaptive inner target the last pass stops once the outer target is met
+    (with margin 2), so the solve still reaches tol, needs no more block products than
+    with the fixed inner target, and does not overshoot tol by orders of magnitude."""
+    d, l = 300, 8
+    a = spd(d, W.decay_spectrum(d, 1e4, 1e-2), 7)
+    b = W.normals(7, 2, d)
+    om = W.omega(7, d, l)
+    fixed = bcg.refined_solve(a, 1e-3, b, om, tol=1e-8, inner_tol=1e-6)
+    adapt = bcg.refined_solve(a, 1e-3, b, om, tol=1e-8, inner_tol=1e-6, adaptive_inner=True)
+    res = direct.rel_residual(operators.Dense(a), 1e-3, adapt["x"], b)
+    assert res <= 1e-8
+    assert adapt["inner_loads"] <= fixed["inner_loads"]
+    # the fixed rule solves the last pass to 1e-6 of an already small residual
+    assert fixed["rel_residual"] < 1e-3 * res
 
 
 # ---------------------------------------------------------------- O2 Lanczos
