@@ -77,9 +77,13 @@ typedef enum { BK_PREC_FP64 = 0, BK_PREC_FP32 = 1, BK_PREC_F32X2 = 2 } bk_prec;
  *   BK_RBF:   K_ij = exp(-||x_i - x_j||^2 / (2 param^2)) formed on the fly, never stored
  *             (the matrix-free access mode of Sec. 1): vals is d points of 3 FP64
  *             coordinates, row stride ld >= 3, rows = cols = d, dtype BK_F64, param > 0
- *             the lengthscale. Entries in FP64 (library exp), products in compensated
- *             FP32 pairs (about 2^-44). Accepted by bk_sample and bk_sample_isqrt with
- *             FP64 blocks (inner BK_PREC_FP64 or BK_PREC_F32X2).
+ *             the lengthscale. Each entry exp(t) is evaluated in FP32-pair arithmetic
+ *             from the FP64 exponent t: relative error about 2^-46 for t >= -70;
+ *             below, the pair's tail leaves the FP32 normal range and the absolute
+ *             error stays under 2^-126; entries with t < -100 are 0. Products in
+ *             compensated FP32 pairs (about 2^-44). Accepted by bk_sample,
+ *             bk_sample_isqrt (FP64 blocks: inner BK_PREC_FP64 or BK_PREC_F32X2) and
+ *             bk_apply.
  *   dtype gives the element type of vals. A must be symmetric positive definite
  *   (or positive semi-definite with mu > 0); the library does not check symmetry. */
 typedef struct {
@@ -108,6 +112,14 @@ typedef struct {
   int32_t profile;        /* nonzero: time every step kernel with CUDA events recorded
                              between launches (kept inside the CUDA graph) and report
                              the sums in bk_info.ms_kernel / launches */
+  int64_t timeout_cycles; /* limit, in SM clock cycles, of each bounded wait of the
+                             tensor-core block products on their copy and MMA
+                             pipeline barriers (bk_solve, bk_solve_batched); 0 = the
+                             library default of 4e9 cycles (about 2 s). A wait that
+                             gives up makes the kernel drain the copies and MMAs it
+                             has issued, free its tensor memory and return; the call
+                             then returns BK_TIMEOUT and the context stays usable.
+                             Negative values are BK_ERR_ARG. */
 } bk_opts;
 
 /* Kernel classes reported by a profiled solve. */
@@ -134,6 +146,10 @@ typedef struct {
   int32_t launches[8];    /* profiled solves: active launches per class */
   int32_t kernel_launches;/* all kernels this call launched, including graph replays
                              and steps that found the solve already finished */
+  int32_t deflations;     /* bk_solve, bk_solve_batched: block columns dropped as
+                             numerically dependent (rank test of the small
+                             factorisation of R^T R), summed over the inner solves; a
+                             dropped column stays out until the next restart */
 } bk_info;
 
 /* Fills *opts with defaults: tol 1e-10, max_loads 20000, sketch 20, seed 0,
@@ -335,6 +351,20 @@ bk_status bk_autotune(bk_ctx* ctx, int32_t n, const bk_operator* A, const double
  * Abramowitz & Stegun 16.4. z2, w: n doubles each (host). 0 < lo <= hi. */
 bk_status bk_sqrt_quadrature(double lo, double hi, int32_t n, double* z2, double* w);
 
+/* Y = A X + mu X for L columns in FP64 (one "matrix-load" of Sec. 1.2 at the accuracy of
+ * the FP64 refinement residual). X and Y are d x L column-major with leading dimensions
+ * ldx, ldy >= d, host or device (host arrays are staged through the context workspace;
+ * the call synchronises the context stream before it returns). A may be BK_DENSE,
+ * BK_CSR, BK_GRAM (d = cols) or BK_RBF. The products are FP64-accurate: FP64 values
+ * through FP64 products; FP32-stored dense and Gram-form values, promoted, through
+ * compensated FP32-pair products (about 2^-44 relative to sum |a_ik x_k|, 16-byte
+ * aligned rows with ld a multiple of 4; FP64 products otherwise); BK_RBF entries formed
+ * on the fly as described for BK_RBF. Returns BK_ERR_ARG for a null pointer, L < 1, a
+ * leading dimension below d or a non-finite mu, and the operator's checks as in
+ * bk_solve / bk_sample. */
+bk_status bk_apply(bk_ctx* ctx, const bk_operator* A, double mu, int32_t L, const double* X, int64_t ldx,
+                   double* Y, int64_t ldy);
+
 /* One block product with its Gram matrix (one "matrix-load", Sec. 1.2):
  *   Y = A P + mu P  and  G = P^T Y  (m x m, FP64, row-major).
  * P and Y are d x m blocks in the panel layout above (leading dimension ld), element type `dtype`
@@ -371,10 +401,14 @@ bk_status bk_gaussian(bk_ctx* ctx, uint64_t seed, uint32_t stream, int64_t n, in
  * budget (a library cudaMalloc would be invisible to it), or a latency-sensitive caller
  * that cannot afford the device-wide synchronisation a cudaMalloc or cudaFree implies.
  *
- * It computes the same Y = A P + mu P and G = P^T Y as bk_block_apply, with the same
- * kernels and launch shape, but takes no context and allocates nothing:
+ * It computes the same Y = A P + mu P and G = P^T Y as bk_block_apply and checks its
+ * arguments by the same rules, but takes no context and allocates nothing. CSR
+ * operators and FP64 dense operators run the same kernels and launch shape as
+ * bk_block_apply. FP32 dense operators always run the CUDA-core dense kernel here,
+ * while bk_block_apply may take the tensor-core product for them (it needs a scratch
+ * copy of P), so the two round differently within the FP32 tolerance.
  *   - every array (A's arrays, P, Y, G) must be device memory of the current device
- *     (BK_ERR_ARG otherwise): there is no staging copy;
+ *     (BK_ERR_ARG otherwise, also for memory of another GPU): there is no staging copy;
  *   - A->dtype must equal dtype (BK_ERR_UNSUPPORTED otherwise): there is no converted
  *     copy of the values;
  *   - the Gram partials use a fixed scratch array of 4 MiB (2^19 doubles) compiled into
@@ -382,13 +416,14 @@ bk_status bk_gaussian(bk_ctx* ctx, uint64_t seed, uint32_t stream, int64_t n, in
  *     until the process exits. A call whose partials would not fit (more CTAs times
  *     Gram entries than 2^19) returns BK_ERR_TOO_LARGE; on GB300 every supported size
  *     fits.
- * The first call on a device looks up the scratch address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture. All calls share
- * the scratch, so calls whose kernels overlap on the GPU (different streams or host
- * threads, same device) race on it and must be serialised by the caller. Each call
- * rewrites every partial it reads, so no clearing is needed. Work is enqueued on
- * `cuda_stream` (a cudaStream_t, NULL for the legacy default stream) and the call
- * returns after synchronising that stream. 1 <= m <= 36. */
+ * The first call on a device does a one-time set-up: it looks up the scratch address
+ * (cudaGetSymbolAddress) with that device current. Make that first call before any
+ * stream capture. All calls share the scratch, so calls whose kernels overlap on the
+ * GPU (different streams or host threads, same device) race on it and must be
+ * serialised by the caller. Each call rewrites every partial it reads, so no clearing
+ * is needed. Work is enqueued on `cuda_stream` (a cudaStream_t, NULL for the legacy
+ * default stream), and the call synchronises that stream before it returns.
+ * 1 <= m <= 36. */
 bk_status bk_block_apply_static(const bk_operator* A, double mu, int32_t dtype, int64_t m, const void* P,
                                 void* Y, int64_t ld, double* G, void* cuda_stream);
 

@@ -43,14 +43,15 @@ class Operator(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_loads", ctypes.c_int32), ("sketch", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("inner", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("max_refine", ctypes.c_int32), ("check_every", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("max_refine", ctypes.c_int32), ("check_every", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("timeout_cycles", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("loads", ctypes.c_int32), ("refinements", ctypes.c_int32),
                 ("residual_loads", ctypes.c_int32), ("rel_residual", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_kernel", ctypes.c_double * 8), ("launches", ctypes.c_int32 * 8),
-                ("kernel_launches", ctypes.c_int32)]
+                ("kernel_launches", ctypes.c_int32), ("deflations", ctypes.c_int32)]
 
     def as_dict(self):
         out = {}
@@ -94,6 +95,7 @@ def _load():
                                   ctypes.POINTER(Info)]),
         "bk_solve_shrink": (i32, [vp, ctypes.POINTER(Operator), dbl, vp, vp, i32, ctypes.POINTER(Opts),
                                   ctypes.POINTER(Info)]),
+        "bk_apply": (i32, [vp, ctypes.POINTER(Operator), dbl, i32, vp, i64, vp, i64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -336,6 +338,24 @@ def solve_shrink(ctx: Context, A: OperatorRef, mu: float, b, x, s_lock: int = 3,
     if check and s != BK_OK:
         raise BKError(s, "bk_solve_shrink", ctx.last_error())
     return info
+
+
+def apply(ctx: Context, A: OperatorRef, mu: float, X, Y, ldx: int | None = None, ldy: int | None = None) -> None:
+    """bk_apply: Y = A X + mu X in FP64. X and Y are column-major (a Fortran-ordered
+    NumPy array or a transposed contiguous torch tensor) with the operator's d rows
+    first in each column; the leading dimensions default to the column strides."""
+    def cols(a):
+        if len(a.shape) == 1:
+            return 1, int(a.shape[0])
+        st = a.strides[1] // a.itemsize if isinstance(a, np.ndarray) else a.stride(1)
+        return int(a.shape[1]), int(st)
+    L, sx = cols(X)
+    _, sy = cols(Y)
+    px, kx = _ptr(X)
+    py, ky = _ptr(Y)
+    s = _lib.bk_apply(ctx.handle, ctypes.byref(A.op), float(mu), L, px, int(ldx or sx), py, int(ldy or sy))
+    if s != BK_OK:
+        raise BKError(s, "bk_apply", ctx.last_error())
 
 
 def block_apply(ctx: Context, A: OperatorRef, mu: float, P, Y, G, m: int, ld: int, dtype=None) -> None:

@@ -30,18 +30,6 @@ struct OpDev {
   const int* colidx;
 };
 
-bk_status check_operator(const bk_operator* A) {
-  if (!A || !A->vals) return BK_ERR_ARG;
-  if (A->kind != BK_DENSE && A->kind != BK_CSR) return BK_ERR_UNSUPPORTED;
-  if (A->dtype != BK_F64 && A->dtype != BK_F32) return BK_ERR_UNSUPPORTED;
-  if (A->rows <= 0 || A->rows != A->cols) return BK_ERR_ARG;
-  if (A->rows > (int64_t)INT32_MAX - 1) return BK_ERR_UNSUPPORTED;
-  if (A->kind == BK_DENSE && A->ld < A->cols) return BK_ERR_ARG;
-  if (A->kind == BK_CSR && (!A->rowptr || !A->colidx || A->nnz < 0 || A->nnz > (int64_t)INT32_MAX))
-    return BK_ERR_ARG;
-  return BK_OK;
-}
-
 cudaError_t stage_operator(bk_ctx* c, const bk_operator* A, OpDev* o) {
   o->kind = A->kind;
   o->dtype = A->dtype;
@@ -326,7 +314,7 @@ bk_status bk_block_apply(bk_ctx* c, const bk_operator* A, double mu, int32_t dty
     BK_CK(ws_get(c, WS_TCERR, 64, (void**)&tcerr));
     BK_CK(cudaMemsetAsync(tcerr, 0, sizeof(int), c->stream));
     BK_CK(bk::launch_dense_gram_tc(mp, d, (const float*)vin, lda_in, mu, (const float*)p, (float*)yo, ld, (int)m,
-                                   parts, np, nullptr, pt, tcerr, c->stream));
+                                   parts, np, nullptr, pt, tcerr, 0, c->stream));
   } else
     BK_CK(bk::launch_dense_gram(is64, mp, d, vin, lda_in, mu, p, yo, ld, (int)m, parts, np, nullptr, c->stream));
   BK_CK(bk::launch_reduce_gram(mp, (int)m, parts, np, go, nullptr, c->stream));
@@ -357,7 +345,7 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
   else
     bk_default_opts(&opts);
   if (!(mu >= 0.0) || !std::isfinite(mu) || !(opts.tol > 0.0) || opts.sketch < 0 || opts.max_loads < 1 ||
-      opts.max_refine < 1 || !(opts.inner_tol > 0.0) || opts.check_every < 1)
+      opts.max_refine < 1 || !(opts.inner_tol > 0.0) || opts.check_every < 1 || opts.timeout_cycles < 0)
     return BK_ERR_ARG;
   if (opts.inner != BK_PREC_FP64 && opts.inner != BK_PREC_FP32) return BK_ERR_UNSUPPORTED;
   // a block wider than the space it lives in is rank deficient from the start
@@ -434,7 +422,7 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
   BK_CK(host_sum(c, w.normp, nnp, &bnorm2));
   const double bnorm = std::sqrt(bnorm2);
 
-  int loads = 0, refinements = 0, residual_loads = 0, stagnant = 0;
+  int loads = 0, refinements = 0, residual_loads = 0, stagnant = 0, deflations = 0;
   // Inner target floor: an inner solve in FP32 blocks stops reducing the true residual
   // at a level set by the block precision and the conditioning (the recurrence keeps
   // going below it). When a pass that met its target reduced the FP64 residual by far
@@ -477,7 +465,7 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
                                    w.state, st);
     else if (use_tc)
       e = bk::launch_dense_gram_tc(mp, d, (const float*)vin, lda_in, mu, (const float*)w.P, (float*)w.Y, ld, m,
-                                   w.partsG, w.npG, w.state, w.pt, &w.state->timeout, st);
+                                   w.partsG, w.npG, w.state, w.pt, &w.state->timeout, opts.timeout_cycles, st);
     else
       e = bk::launch_dense_gram(is64, mp, d, vin, lda_in, mu, w.P, w.Y, ld, m, w.partsG, w.npG, w.state, st);
     if (e != cudaSuccess) return e;
@@ -559,10 +547,11 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
             n_k[kClass[k]] += 1;
           }
       }
-      if (c->hstate->done_a || c->hstate->done_b) break;
+      if (c->hstate->done_a || c->hstate->done_b || c->hstate->timeout) break;
     }
     const DevState hs = *c->hstate;
     loads += hs.loads;
+    deflations += m - hs.kept;
     refinements += 1;
     if (hs.timeout) {
       std::snprintf(c->last_error, sizeof(c->last_error), "tensor-core pipeline wait timed out");
@@ -609,6 +598,7 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
   if (info) {
     info->status = result;
     info->loads = loads;
+    info->deflations = deflations;
     info->refinements = refinements;
     info->residual_loads = residual_loads;
     info->rel_residual = bnorm > 0 ? rnorm / bnorm : 0.0;

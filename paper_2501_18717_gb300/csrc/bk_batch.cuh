@@ -40,6 +40,7 @@ struct BatchTc {
   const int* tile_row = nullptr;
   int ntiles = 0;
   const void* maps = nullptr;
+  long long wait_cycles = 0;  // limit of each pipeline wait in SM clocks (0: the default)
 };
 cudaError_t launch_batch_dense_tc(int mp, BSys* sys, const int* cta_sys, int ncta, const BatchTc& tc,
                                   cudaStream_t st);

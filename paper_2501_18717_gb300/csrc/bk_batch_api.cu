@@ -63,7 +63,7 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
   else
     bk_default_opts(&opts);
   if (!(opts.tol > 0.0) || opts.max_loads < 1 || opts.max_refine < 1 || opts.check_every < 1 ||
-      !(opts.inner_tol > 0.0))
+      !(opts.inner_tol > 0.0) || opts.timeout_cycles < 0)
     return BK_ERR_ARG;
   if (opts.inner != BK_PREC_FP64 && opts.inner != BK_PREC_FP32) return BK_ERR_UNSUPPORTED;
   const int is64 = opts.inner == BK_PREC_FP64;
@@ -108,7 +108,7 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
   const double rank_tol = is64 ? 1e-12 : 1e-6;
   const int sms = c->sms > 0 ? c->sms : 152;
   std::vector<double> bnorm(n, 0.0), rnorm(n, 0.0);
-  std::vector<int> loads(n, 0), refine(n, 0), status(n, BK_NOT_CONVERGED);
+  std::vector<int> loads(n, 0), refine(n, 0), status(n, BK_NOT_CONVERGED), defl(n, 0);
   // per-system inner target floor and the target and residual of the last pass (the
   // rule of bk_solve: after a pass that met its target but reduced the FP64 residual by
   // far less, later passes stop at half the reduction it achieved)
@@ -260,6 +260,7 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
     g->btc.tile_sys = tiles;
     g->btc.tile_row = tiles + g->btc.ntiles;
     g->btc.maps = maps;
+    g->btc.wait_cycles = opts.timeout_cycles;
   }
   std::vector<double> hparts(total_cta + 16);
   std::vector<bk::DevState> hst(n);
@@ -340,6 +341,22 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
       }
       BK_CKG(cudaMemcpyAsync(hst.data(), dstates, sizeof(bk::DevState) * n, cudaMemcpyDeviceToHost, st));
       BK_CKG(cudaStreamSynchronize(st));
+      // a tensor-core product whose pipeline wait gave up left an invalid block: stop
+      bool timed_out = false;
+      for (int i = 0; i < n; ++i) timed_out = timed_out || hst[i].timeout != 0;
+      if (timed_out) {
+        std::snprintf(c->last_error, sizeof(c->last_error), "tensor-core pipeline wait timed out");
+        for (int i = 0; i < n; ++i)
+          if (infos) {
+            infos[i].status = BK_TIMEOUT;
+            infos[i].loads = loads[i] + hst[i].loads;
+            infos[i].refinements = refine[i];
+          }
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        cleanup();
+        return BK_TIMEOUT;
+      }
       bool all = true;
       for (int i = 0; i < n; ++i) all = all && (hst[i].done_a || hst[i].done_b);
       if (all) break;
@@ -349,6 +366,7 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
         if (s.active) {
           loads[s.index] += hst[s.index].loads;
           refine[s.index] += 1;
+          defl[s.index] += s.m - hst[s.index].kept;
         }
     std::vector<int> conv_inner(n, 0);
     for (int i = 0; i < n; ++i) conv_inner[i] = hst[i].status == bk::ST_CONVERGED;
@@ -385,6 +403,7 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
       infos[i].residual_loads = refine[i] + 1;
       infos[i].rel_residual = bnorm[i] > 0 ? rnorm[i] / bnorm[i] : 0.0;
       infos[i].ms_total = ms_total;
+      infos[i].deflations = defl[i];
     }
   cleanup();
 #undef BK_CKG

@@ -16,7 +16,7 @@ namespace bk {
 //   done_a, pending_x, loads, first   written by the alpha small-solve (CTA 0); loads
 //                                     is read back only by the beta small-solve, first
 //                                     only by the direction update
-//   done_b, res                       written by the beta small-solve (CTA 0)
+//   done_b, res, kept                 written by the beta small-solve (CTA 0)
 //   status                            written by whichever sets a done flag
 struct DevState {
   int done_a;       // G unusable (negative or non-finite diagonal, or no kept column)
@@ -27,6 +27,7 @@ struct DevState {
   int status;       // ST_* below
   int max_loads;    // cap for this inner solve
   int timeout;      // set by a kernel whose bounded wait on a pipeline barrier gave up
+  int kept;         // columns kept by the latest factorisation of S = W^T W (block rank)
   double tol_abs;   // target on ||R e_1|| = ||c|| (column 0 starts with norm 1)
   double res;       // latest ||c|| from the recurrence
 };
@@ -68,13 +69,14 @@ int dense_gram_grid(int is_f64, int mp, int64_t d, int device);
 // Tensor-core variant for FP32 values (k_tc.cu): usable when A is 16-byte aligned, lda
 // is a multiple of 4 and mp <= 36. One CTA per 128-row tile (nparts = dense_tc_tiles(d));
 // pt is scratch for P^T head and tail (dense_tc_pt_bytes). *err is set to 1 if a
-// pipeline wait timed out (the product is then invalid).
+// pipeline wait gave up after wait_cycles SM clocks (0: the default, about 2 s); the
+// product is then invalid.
 bool dense_tc_usable(int64_t d, const void* A, int64_t lda, int mp);
 int dense_tc_tiles(int64_t d);
 size_t dense_tc_pt_bytes(int64_t d, int mp);
 cudaError_t launch_dense_gram_tc(int mp, int64_t d, const float* A, int64_t lda, double mu, const float* P, float* Y,
                                  int64_t ld, int m, double* parts, int nparts, const DevState* state, float* pt,
-                                 int* err, cudaStream_t st);
+                                 int* err, long long wait_cycles, cudaStream_t st);
 
 // Partials of G = X^T Y.
 cudaError_t launch_gram(int is_f64, int mp, int64_t d, const void* X, const void* Y, int64_t ld, int m,

@@ -99,6 +99,20 @@ inline bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Argument checks of a dense or CSR operator, shared by every entry point that takes
+// one (the same rules for the context calls and the allocation-free block product).
+inline bk_status check_operator(const bk_operator* A) {
+  if (!A || !A->vals) return BK_ERR_ARG;
+  if (A->kind != BK_DENSE && A->kind != BK_CSR) return BK_ERR_UNSUPPORTED;
+  if (A->dtype != BK_F64 && A->dtype != BK_F32) return BK_ERR_UNSUPPORTED;
+  if (A->rows <= 0 || A->rows != A->cols) return BK_ERR_ARG;
+  if (A->rows > (int64_t)INT32_MAX - 1) return BK_ERR_UNSUPPORTED;
+  if (A->kind == BK_DENSE && A->ld < A->cols) return BK_ERR_ARG;
+  if (A->kind == BK_CSR && (!A->rowptr || !A->colidx || A->nnz < 0 || A->nnz > (int64_t)INT32_MAX))
+    return BK_ERR_ARG;
+  return BK_OK;
+}
+
 // Device view of a borrowed input array: the pointer itself, or a staged copy.
 inline cudaError_t stage_in(bk_ctx* c, Slot s, const void* p, size_t bytes, const void** out) {
   if (is_device_ptr(p)) {

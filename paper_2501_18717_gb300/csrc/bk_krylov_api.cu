@@ -1368,3 +1368,35 @@ extern "C" bk_status bk_solve_shrink(bk_ctx* c, const bk_operator* A, double mu,
   }
   return result;
 }
+
+extern "C" bk_status bk_apply(bk_ctx* c, const bk_operator* A, double mu, int32_t L, const double* X, int64_t ldx,
+                              double* Y, int64_t ldy) {
+  if (!c || !X || !Y || L < 1 || !std::isfinite(mu)) return BK_ERR_ARG;
+  err_ctx() = c;
+  c->last_error[0] = 0;
+  LzOp o;
+  bk_status s = check_pcg_operator(A, &o);
+  if (s != BK_OK) return s;
+  const int64_t d = o.d;
+  if (ldx < d || ldy < d) return BK_ERR_ARG;
+  BK_CK(cudaSetDevice(c->device));
+  cudaStream_t st = c->stream;
+  BK_CK(stage_pcg_operator(c, A, &o));
+  const size_t xbytes = ((size_t)(L - 1) * ldx + d) * 8;
+  const double* Xd = nullptr;
+  BK_CK(stage_in(c, WS_TMP_IN, X, xbytes, (const void**)&Xd));
+  // the products write d x L with leading dimension ldx; Y itself when it is device
+  // memory with the same leading dimension, otherwise a workspace copied out after
+  double* Yd = Y;
+  const bool direct = is_device_ptr(Y) && ldy == ldx;
+  if (!direct) BK_CK(ws_get(c, WS_TMP_OUT, xbytes, (void**)&Yd));
+  double* Vw = nullptr;
+  if (o.kind == BK_GRAM) BK_CK(ws_get(c, WS_LV, (size_t)o.nrows * L * 8, (void**)&Vw));
+  BK_CK(apply_fp64(c, o, Xd, ldx, L, Yd, Vw, true));
+  if (mu != 0.0)
+    for (int j = 0; j < L; ++j) BK_CK(bk::launch_axpy(d, mu, Xd + (size_t)j * ldx, Yd + (size_t)j * ldx, st));
+  if (!direct)
+    BK_CK(cudaMemcpy2DAsync(Y, (size_t)ldy * 8, Yd, (size_t)ldx * 8, (size_t)d * 8, L, cudaMemcpyDefault, st));
+  BK_CK(cudaStreamSynchronize(st));
+  return BK_OK;
+}

@@ -3,9 +3,9 @@
 // descriptors, tcgen05.mma / commit / ld. Written from the PTX ISA descriptions of
 // these instructions; used by the tensor-core block products (k_tc.cu).
 //
-// Every wait is bounded: mbar_wait gives up after kWaitCycles SM clocks and returns
-// false, so a kernel whose barrier never completes can record an error and leave
-// instead of spinning forever.
+// Every wait is bounded: mbar_wait gives up after a limit of SM clocks (kWaitCycles
+// unless the caller passes its own) and returns false, so a kernel whose barrier never
+// completes can record an error and leave instead of spinning forever.
 #pragma once
 
 #include <cuda.h>
@@ -15,7 +15,7 @@
 namespace bk {
 namespace sm100 {
 
-constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz (the default limit)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -45,13 +45,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the phase with the given parity to complete; false after kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity to complete; false once `limit` SM clocks
+// have passed. The clock is read before every (possibly suspending) try_wait, so a
+// limit of a few clocks gives up at the first phase that is not already complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kWaitCycles) {
+  if (mbar_test_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
-  return true;
+  while (clock64() - t0 <= limit)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
 }
 
 // Generic-proxy writes to shared memory become visible to the async proxy (tensor

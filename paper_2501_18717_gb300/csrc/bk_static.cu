@@ -9,15 +9,19 @@
 // on it, and each call overwrites every partial it reads (nothing needs clearing).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "../../include/bk.h"
 #include "bk_common.cuh"
+#include "bk_ctx.h"
 
 namespace {
 
-// 4 MiB of FP64 partials: the full grid of the block-product kernel (three CTAs per SM
-// on up to 240 SMs) times the 720 partial entries of the widest block (m <= 36).
+// 4 MiB of FP64 partials. The widest block (m <= 36) has 720 partial entries per CTA
+// and the block-product grids run at most four CTAs per SM, so the array holds the
+// partials of every launch on GPUs with up to 182 SMs (4 x 182 x 720 <= 2^19); larger
+// grids are refused with BK_ERR_TOO_LARGE.
 constexpr size_t kStaticParts = (size_t)1 << 19;
 __device__ __align__(256) double g_static_parts[kStaticParts];
 
@@ -41,37 +45,44 @@ cudaError_t static_parts(int device, double** out) {
   return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// True if p is device (or managed) memory that the given device owns. Memory of another
+// GPU is refused: the kernels run on the current device and would otherwise read it
+// over the peer link or fault.
+bool on_device(const void* p, int device) {
   if (!p) return false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 }  // namespace
 
 extern "C" bk_status bk_block_apply_static(const bk_operator* A, double mu, int32_t dtype, int64_t m,
                                            const void* P, void* Y, int64_t ld, double* G, void* cuda_stream) {
-  if (!A || !A->vals || !P || !Y || !G) return BK_ERR_ARG;
-  if (A->kind != BK_DENSE && A->kind != BK_CSR) return BK_ERR_UNSUPPORTED;
+  // the same operator and argument checks as bk_block_apply
+  bk_status s = bkx::check_operator(A);
+  if (s != BK_OK) return s;
+  if (!P || !Y || !G) return BK_ERR_ARG;
+  if (m < 1 || ld < A->rows || !std::isfinite(mu)) return BK_ERR_ARG;
   if (dtype != BK_F64 && dtype != BK_F32) return BK_ERR_UNSUPPORTED;
   // no conversion buffer: the values must already be in the block precision
   if (A->dtype != dtype) return BK_ERR_UNSUPPORTED;
-  if (A->rows <= 0 || A->rows != A->cols || A->rows > (int64_t)INT32_MAX - 1) return BK_ERR_ARG;
-  if (m < 1 || ld < A->rows || !(mu == mu)) return BK_ERR_ARG;
-  if (A->kind == BK_DENSE && A->ld < A->cols) return BK_ERR_ARG;
-  if (A->kind == BK_CSR && (!A->rowptr || !A->colidx || A->nnz < 0)) return BK_ERR_ARG;
   const int mp = bk::padded_width((int)m);
   if (mp < 0 || m > bk::kMaxWidth) return BK_ERR_UNSUPPORTED;
-  // no staging buffer either: every array must be device-accessible
-  if (!on_device(A->vals) || !on_device(P) || !on_device(Y) || !on_device(G)) return BK_ERR_ARG;
-  if (A->kind == BK_CSR && (!on_device(A->rowptr) || !on_device(A->colidx))) return BK_ERR_ARG;
-
   int device = 0;
-  if (cudaGetDevice(&device) != cudaSuccess) return BK_ERR_CUDA;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    return BK_ERR_CUDA;
+  }
+  // no staging buffer either: every array must be memory of the current device
+  if (!on_device(A->vals, device) || !on_device(P, device) || !on_device(Y, device) || !on_device(G, device))
+    return BK_ERR_ARG;
+  if (A->kind == BK_CSR && (!on_device(A->rowptr, device) || !on_device(A->colidx, device))) return BK_ERR_ARG;
+
   const int is64 = dtype == BK_F64;
   const int64_t d = A->rows;
   const int nparts = (A->kind == BK_CSR) ? bk::csr_spmm_gram_grid(is64, mp, d, device)

@@ -347,6 +347,7 @@ __global__ void __launch_bounds__(kBSmall) k_bsmall(BSys* __restrict__ sys, int 
   }
   for (int i = threadIdx.x; i < m; i += kBSmall) S.cvec[i] = cn[i];
   if (threadIdx.x == 0) {
+    st->kept = rank;
     double ss = 0.0;
     for (int i = 0; i < m; ++i) ss = fma(cn[i], cn[i], ss);
     const double res = sqrt(ss);
@@ -378,6 +379,7 @@ __global__ void k_bstart(BSys* __restrict__ sys, const int* __restrict__ cta_sys
       st->status = S.active ? ST_RUNNING : ST_CONVERGED;
       st->max_loads = S.max_loads;
       st->timeout = 0;
+      st->kept = S.m;
       st->tol_abs = S.tol_abs;
       st->res = 1.0;
     }

@@ -240,6 +240,7 @@ __global__ void k_small_beta(int m, int mp, const double* S, double* cvec, T* ti
   __syncthreads();
   for (int i = threadIdx.x; i < m; i += kSmallThreads) cvec[i] = cn[i];
   if (threadIdx.x == 0) {
+    state->kept = rank;
     double ss = 0.0;
     for (int i = 0; i < m; ++i) ss = fma(cn[i], cn[i], ss);
     const double res = sqrt(ss);
@@ -438,6 +439,7 @@ __global__ void k_init_state(DevState* s, int max_loads, double tol_abs, double*
     s->status = ST_RUNNING;
     s->max_loads = max_loads;
     s->timeout = 0;
+    s->kept = m;
     s->tol_abs = tol_abs;
     s->res = 1.0;
   }

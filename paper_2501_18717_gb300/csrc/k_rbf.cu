@@ -6,8 +6,9 @@
 // double-float arithmetic (pairs of FP32): Cody-Waite reduction t = k ln2 + r in FP64,
 // |r| <= ln2 / 2, then the Taylor polynomial of exp(r) to degree 14 by Horner's rule in
 // pair arithmetic (Dekker's product and Knuth's sum, error-free by FMA), scaled by 2^k;
-// relative error about 2^-46, and the entry comes out as the head and tail the products
-// need. X (FP64) is split into head and tail; the products use compensated FP32-pair
+// relative error about 2^-46 (for t >= -70), and the entry comes out as the head and tail the products
+// need; for t < -70 the tail falls below the FP32 normal range, so there the error is
+// absolute, under 2^-126, and exp(t) for t < -100 is taken as 0. X (FP64) is split into head and tail; the products use compensated FP32-pair
 // arithmetic (the head-head product made exact by FMA, the two cross terms added to its
 // error, TwoSum accumulation), about 2^-44 relative to sum |K_ik x_k|. The entries are
 // therefore accurate to about 1e-14, far below the nugget, unlike an FP32-stored K

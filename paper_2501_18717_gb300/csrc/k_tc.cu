@@ -122,7 +122,8 @@ __global__ void k_pt_split(int64_t d, const float* __restrict__ P, int64_t ld, i
 template <int MP>
 __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const CUtensorMap* bmap_p, int64_t d,
                                               int tile, const float* __restrict__ P, float* __restrict__ Y,
-                                              int64_t ld, int m, float mu, double* parts, int nparts, int* err) {
+                                              int64_t ld, int m, float mu, double* parts, int nparts, int* err,
+                                              long long wait) {
   using SH = TcShape<MP>;
   constexpr int N = SH::N, R = SH::R, RB = SH::RB, W = SH::W, NH = N / 2;
   constexpr int kConv = kTcThreads - 96;  // split / drain threads (warps 3..10)
@@ -183,7 +184,7 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
       for (int kb = 0; kb < nk; ++kb) {
         const int s = kb % R;
         if (*s_abort) break;
-        if (kb >= R && !mbar_wait(raw_empty + s, (uint32_t)((kb / R) - 1) & 1)) {
+        if (kb >= R && !mbar_wait(raw_empty + s, (uint32_t)((kb / R) - 1) & 1, wait)) {
           *s_abort = 1;
           break;
         }
@@ -199,7 +200,7 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
       for (int kb = 0; kb < nk; ++kb) {
         const int t = kb % RB;
         if (*s_abort) break;
-        if (kb >= RB && !mbar_wait(b_empty + t, (uint32_t)((kb / RB) - 1) & 1)) {
+        if (kb >= RB && !mbar_wait(b_empty + t, (uint32_t)((kb / RB) - 1) & 1, wait)) {
           *s_abort = 1;
           break;
         }
@@ -222,16 +223,16 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
       for (int kb = 0; kb < nk; ++kb) {
         const int w = kb % W, t = kb % RB, b = kb & 1;
         if (*s_abort) break;
-        if (kb >= 2 && !mbar_wait(acc_empty + b, (uint32_t)((kb >> 1) - 1) & 1)) {
+        if (kb >= 2 && !mbar_wait(acc_empty + b, (uint32_t)((kb >> 1) - 1) & 1, wait)) {
           *s_abort = 1;
           break;
         }
-        if (!mbar_wait(b_full + t, (uint32_t)(kb / RB) & 1)) {
+        if (!mbar_wait(b_full + t, (uint32_t)(kb / RB) & 1, wait)) {
           *s_abort = 1;
           break;
         }
         *s_b_consumed = kb + 1;
-        if (!mbar_wait(w_split + w, (uint32_t)(kb / W) & 1)) {
+        if (!mbar_wait(w_split + w, (uint32_t)(kb / W) & 1, wait)) {
           *s_abort = 1;
           break;
         }
@@ -264,11 +265,11 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
       if (__any_sync(0xffffffffu, *s_abort != 0)) break;
       if (kb < nk) {
         const int s = kb % R, w = kb % W;
-        if (!__all_sync(0xffffffffu, mbar_wait(raw_full + s, (uint32_t)(kb / R) & 1))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(raw_full + s, (uint32_t)(kb / R) & 1, wait))) {
           *s_abort = 1;
           break;
         }
-        if (kb >= W && !__all_sync(0xffffffffu, mbar_wait(w_empty + w, (uint32_t)((kb / W) - 1) & 1))) {
+        if (kb >= W && !__all_sync(0xffffffffu, mbar_wait(w_empty + w, (uint32_t)((kb / W) - 1) & 1, wait))) {
           *s_abort = 1;
           break;
         }
@@ -306,7 +307,7 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
       }
       if (kb >= 1) {  // drain the accumulator of k-block kb - 1
         const int kp = kb - 1, b = kp & 1;
-        if (!__all_sync(0xffffffffu, mbar_wait(acc_full + b, (uint32_t)(kp >> 1) & 1))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(acc_full + b, (uint32_t)(kp >> 1) & 1, wait))) {
           *s_abort = 1;
           break;
         }
@@ -332,7 +333,9 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
   __syncthreads();
   const bool aborted = *s_abort != 0;
   if (aborted) {
-    // let issued loads land and issued MMAs finish before the memory is reused or freed
+    // let issued loads land and issued MMAs finish before the memory is reused or freed;
+    // these waits keep the default limit whatever the caller's: they wait for copies
+    // and MMAs already issued, which complete by themselves
     if (warp == 0 && lane == 0)
       for (int kb = *s_a_consumed; kb < issued; ++kb) mbar_wait(raw_full + kb % R, (uint32_t)(kb / R) & 1);
     if (warp == 2 && lane == 0)
@@ -394,21 +397,21 @@ template <int MP>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_dense_tc(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap, int64_t d,
                const float* __restrict__ P, float* __restrict__ Y, int64_t ld, int m, float mu, double* parts,
-               int nparts, const DevState* state, int* err) {
+               int nparts, const DevState* state, int* err, long long wait) {
   if (state && (state->done_a | state->done_b)) return;
-  dense_tc_tile<MP>(&amap, &bmap, d, blockIdx.x, P, Y, ld, m, mu, parts, nparts, err);
+  dense_tc_tile<MP>(&amap, &bmap, d, blockIdx.x, P, Y, ld, m, mu, parts, nparts, err, wait);
 }
 
 // Batched: CTA i computes row tile tile_row[i] of system tile_sys[i].
 template <int MP>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_bdense_tc(const BSys* __restrict__ sys, const int* __restrict__ tile_sys, const int* __restrict__ tile_row,
-                const CUtensorMap* __restrict__ maps) {
+                const CUtensorMap* __restrict__ maps, long long wait) {
   const int k = tile_sys[blockIdx.x];
   const BSys& S = sys[k];
   if (S.st->done_a | S.st->done_b) return;
   dense_tc_tile<MP>(maps + 2 * k, maps + 2 * k + 1, S.d, tile_row[blockIdx.x], static_cast<const float*>(S.P),
-                    static_cast<float*>(S.Y), S.ld, S.m, (float)S.mu, S.Gp, S.npG, &S.st->timeout);
+                    static_cast<float*>(S.Y), S.ld, S.m, (float)S.mu, S.Gp, S.npG, &S.st->timeout, wait);
 }
 
 // Batched P^T split over the group's thread-block ranges.
@@ -452,7 +455,8 @@ cudaError_t batch_tc_impl(BSys* sys, const int* cta_sys, int ncta, const BatchTc
   auto k = k_bdense_tc<MP>;
   if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::kSmem)) != cudaSuccess) return e;
   k<<<tc.ntiles, kTcThreads, SH::kSmem, st>>>(sys, tc.tile_sys, tc.tile_row,
-                                               static_cast<const CUtensorMap*>(tc.maps));
+                                               static_cast<const CUtensorMap*>(tc.maps),
+                                               tc.wait_cycles > 0 ? tc.wait_cycles : sm100::kWaitCycles);
   return cudaGetLastError();
 }
 
@@ -489,7 +493,7 @@ cudaError_t make_map(CUtensorMap* map, const float* ptr, int64_t x, int64_t y, i
 template <int MP>
 cudaError_t dense_tc_impl(int64_t d, const float* A, int64_t lda, double mu, const float* P, float* Y, int64_t ld,
                           int m, double* parts, int nparts, const DevState* state, float* pt, int* err,
-                          cudaStream_t st) {
+                          long long wait, cudaStream_t st) {
   using SH = TcShape<MP>;
   const int64_t ldk = (d + 31) & ~int64_t(31);
   CUtensorMap amap, bmap;
@@ -502,7 +506,8 @@ cudaError_t dense_tc_impl(int64_t d, const float* A, int64_t lda, double mu, con
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   auto k = k_dense_tc<MP>;
   if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::kSmem)) != cudaSuccess) return e;
-  k<<<nparts, kTcThreads, SH::kSmem, st>>>(amap, bmap, d, P, Y, ld, m, (float)mu, parts, nparts, state, err);
+  k<<<nparts, kTcThreads, SH::kSmem, st>>>(amap, bmap, d, P, Y, ld, m, (float)mu, parts, nparts, state, err,
+                                           wait > 0 ? wait : sm100::kWaitCycles);
   return cudaGetLastError();
 }
 
@@ -543,14 +548,14 @@ size_t dense_tc_pt_bytes(int64_t d, int mp) {
 
 cudaError_t launch_dense_gram_tc(int mp, int64_t d, const float* A, int64_t lda, double mu, const float* P, float* Y,
                                  int64_t ld, int m, double* parts, int nparts, const DevState* state, float* pt,
-                                 int* err, cudaStream_t st) {
+                                 int* err, long long wait_cycles, cudaStream_t st) {
   if (nparts != dense_tc_tiles(d)) return cudaErrorInvalidValue;
   switch (mp) {
-    case 4: return dense_tc_impl<4>(d, A, lda, mu, P, Y, ld, m, parts, nparts, state, pt, err, st);
-    case 8: return dense_tc_impl<8>(d, A, lda, mu, P, Y, ld, m, parts, nparts, state, pt, err, st);
-    case 16: return dense_tc_impl<16>(d, A, lda, mu, P, Y, ld, m, parts, nparts, state, pt, err, st);
-    case 24: return dense_tc_impl<24>(d, A, lda, mu, P, Y, ld, m, parts, nparts, state, pt, err, st);
-    case 36: return dense_tc_impl<36>(d, A, lda, mu, P, Y, ld, m, parts, nparts, state, pt, err, st);
+    case 4: return dense_tc_impl<4>(d, A, lda, mu, P, Y, ld, m, parts, nparts, state, pt, err, wait_cycles, st);
+    case 8: return dense_tc_impl<8>(d, A, lda, mu, P, Y, ld, m, parts, nparts, state, pt, err, wait_cycles, st);
+    case 16: return dense_tc_impl<16>(d, A, lda, mu, P, Y, ld, m, parts, nparts, state, pt, err, wait_cycles, st);
+    case 24: return dense_tc_impl<24>(d, A, lda, mu, P, Y, ld, m, parts, nparts, state, pt, err, wait_cycles, st);
+    case 36: return dense_tc_impl<36>(d, A, lda, mu, P, Y, ld, m, parts, nparts, state, pt, err, wait_cycles, st);
     default: return cudaErrorInvalidValue;
   }
 }

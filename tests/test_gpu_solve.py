@@ -98,6 +98,9 @@ def test_exact_recovery(bk, ctx):
     info = bk.solve(ctx, bk.dense_operator(a), 0.0, b, x, bk.default_opts(tol=1e-10, sketch=l, seed=9))
     # two loads reach the kappa(A) = 1e5 rounding floor; one refinement load may follow
     assert info.loads <= 3, info.as_dict()
+    # after one load the new residual directions span at most the k outlier directions:
+    # the rank test drops the other l + 1 - k columns of the block (reported, Q1 reading)
+    assert info.deflations >= l + 1 - k, info.as_dict()
     assert direct.rel_residual(operators.Dense(a), 0.0, x, b) <= 1e-10
 
 
