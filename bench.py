@@ -65,6 +65,7 @@ def parse():
                                                                  "sample", "nystrom", "shrink", "csr-product"])
     ap.add_argument("--ridge-n", type=int, default=200000)
     ap.add_argument("--ridge-d", type=int, default=4096)
+    ap.add_argument("--ridge-inner", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--sample-d", type=int, default=40000)
     ap.add_argument("--sample-m", type=int, default=256)
     ap.add_argument("--sample-loads", type=int, default=16)
@@ -570,14 +571,16 @@ def run_ridge(args, world, rank, local, dev):
 
     def opts(inner, profile=0):
         return bk.default_opts(tol=TOL, sketch=RIDGE_SKETCH, seed=OMEGA_SEED, inner=inner,
-                               inner_tol=1e-5 if inner == "fp32" else 1e-6, check_every=2, max_loads=400,
+                               inner_tol=1e-5 if inner in ("fp32", "bf16") else 1e-6, check_every=2, max_loads=400,
                                profile=profile)
 
     def call(o, op_=op, b_=b, X_=X):
         with torch.cuda.stream(stream):
             return bk.ridge_path(ctx, op_, mus, b_, X_, o, check=False)
 
-    mixed = opts("fp32")
+    inner = args.ridge_inner
+    other = "bf16" if inner == "fp32" else "fp32"
+    mixed = opts(inner)
     for _ in range(args.warmup):
         call(mixed)
     torch.cuda.synchronize(dev)
@@ -595,7 +598,7 @@ def run_ridge(args, world, rank, local, dev):
 
     # one profiled call: CUDA events around the operator loads, residual products and
     # orthogonalisation inside the driver
-    pinfo = call(opts("fp32", profile=1))
+    pinfo = call(opts(inner, profile=1))
     names = bk.KERNEL_CLASSES
     kms = list(pinfo.ms_kernel)
     kn = list(pinfo.launches)
@@ -630,6 +633,33 @@ def run_ridge(args, world, rank, local, dev):
         roof = {"bound": "alu", "kernel": "Gram-form load Z^T (Z P) (k_tsm nn + tn, FFMA)", "achieved": op_tf,
                 "peak": peak_tf, "unit": "TFLOP/s", "frac": (op_tf / peak_tf) if op_tf else None, "traffic": None,
                 "peak_source": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz"}
+
+    # the other inner precision of the loads (FP32 FFMA or BF16 tensor cores), timed the
+    # same way, with the operator group from one profiled call
+    alt = None
+    if args.steps > 0:
+        ao = opts(other)
+        call(ao)
+        torch.cuda.synchronize(dev)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        ainfos = [call(ao) for _ in range(args.steps)]
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        ams = a0.elapsed_time(a1) / args.steps
+        ap_ = call(opts(other, profile=1))
+        j = names.index("operator")
+        aop = ap_.ms_kernel[j] / max(ap_.launches[j], 1)
+        # bytes of one load: Z twice (two products); BF16 loads read the head and tail
+        # copies (2 x 2 n d bytes per product), FP32 loads the FP32 Z (4 n d per product)
+        lbytes = 8.0 * n * d
+        alt = {"inner": other, "value": world * L / (ams / 1e3), "unit": "solves/s", "ms_per_step": ams,
+               "all_converged": all(i.status == bk.BK_OK for i in ainfos),
+               "rel_residual_max": max(i.rel_residual for i in ainfos), "loads": ainfos[-1].loads,
+               "refinements": ainfos[-1].refinements, "residual_products": ainfos[-1].residual_loads,
+               "operator_avg_ms": aop, "operator_hbm_gbs": lbytes / (aop / 1e3) / 1e9,
+               "operator_frac_of_hbm": lbytes / (aop / 1e3) / 1e9 / measured_peaks()[0],
+               "operator_share_of_call": ap_.ms_kernel[j] / max(ap_.ms_total, 1e-9)}
 
     # FP64 blocks (plain) on the same GPU, one call
     fp64 = None
@@ -695,7 +725,17 @@ def run_ridge(args, world, rank, local, dev):
             "residual_product": {"achieved_tflops": res_tf, "unit": "TFLOP/s (FP64-accurate, 4 n d L flop)",
                                  "frac_of_pair_peak": (res_tf * 11.0 / peak_tf) if res_tf else None},
             "fp64_plain": fp64, "e2e": e2e, "clocks": clocks, "cpu_baseline": cpu,
+            "other_inner": alt,
         }
+        if inner == "bf16":
+            line["dtype"] = ("bf16 tensor-core products (head/tail splits, fp32 accumulation) + f64 Gram/band "
+                             "solves + compensated-f32 (~44 bit) f64 residuals")
+            lb = 8.0 * n * d
+            gbs = lb / (groups["operator"]["avg_ms"] / 1e3) / 1e9 if groups["operator"]["calls"] else None
+            line["roofline"] = {"bound": "hbm", "kernel": "BF16 Gram-form load Z^T (Z P) (k_bgemm x 2 + splits)",
+                                "achieved": gbs, "peak": peak_hbm, "unit": "GB/s",
+                                "frac": gbs / peak_hbm if gbs else None, "traffic": None, "peak_source": peak_src}
+            line["operator_load"] = {"hbm_gbs": gbs, "bytes_per_load": lb, "hbm_peak": peak_hbm}
         print(json.dumps(line), flush=True)
     ctx.close()
     return 0

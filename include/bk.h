@@ -65,8 +65,16 @@ typedef enum { BK_F64 = 0, BK_F32 = 1 } bk_dtype;
  *   sums to about 2^-44 of sum |a_ik p_k|), and the basis products (reorthogonalisation,
  *   block QR) in the same arithmetic; the Grams that give T_t, the band solves and the
  *   refinement stay FP64. Lanczos drivers only (bk_ridge_path, bk_sample,
- *   bk_sample_isqrt); bk_solve and bk_solve_batched return BK_ERR_UNSUPPORTED. */
-typedef enum { BK_PREC_FP64 = 0, BK_PREC_FP32 = 1, BK_PREC_F32X2 = 2 } bk_prec;
+ *   bk_sample_isqrt); bk_solve and bk_solve_batched return BK_ERR_UNSUPPORTED.
+ *   BK_PREC_BF16: FP32 blocks; the block products of a Gram-form operator (BK_GRAM,
+ *   FP32 or FP64 Z, promoted to FP32) run on the BF16 tensor cores with FP32
+ *   accumulation. Z is split once per call into a BF16 head and tail (a row-major and
+ *   a transposed copy, 4 n d bytes each) and the block likewise at every product; a
+ *   product is the sum of the three head/tail products, about 2^-16 of
+ *   sum |z_ik x_k|. The refinement residual stays FP64-accurate (compensated
+ *   products of the stored Z). bk_ridge_path only, with at most 128 block columns;
+ *   other entry points and operator kinds return BK_ERR_UNSUPPORTED. */
+typedef enum { BK_PREC_FP64 = 0, BK_PREC_FP32 = 1, BK_PREC_F32X2 = 2, BK_PREC_BF16 = 3 } bk_prec;
 
 /* The matrix A (without the shift mu).
  *   BK_DENSE: vals is rows x cols row-major with leading dimension ld, rows = cols = d.

@@ -24,7 +24,7 @@ BK_OK, BK_ERR_ARG, BK_ERR_CUDA, BK_ERR_OOM, BK_NOT_CONVERGED, BK_BREAKDOWN, BK_S
     BK_ERR_UNSUPPORTED, BK_ERR_TOO_LARGE = range(10)
 BK_DENSE, BK_CSR, BK_GRAM, BK_RBF = 0, 1, 2, 3
 BK_F64, BK_F32 = 0, 1
-BK_PREC_FP64, BK_PREC_FP32, BK_PREC_F32X2 = 0, 1, 2
+BK_PREC_FP64, BK_PREC_FP32, BK_PREC_F32X2, BK_PREC_BF16 = 0, 1, 2, 3
 
 EXPORTS = ("bk_default_opts", "bk_create", "bk_destroy", "bk_set_stream", "bk_status_string", "bk_last_error",
            "bk_solve",
@@ -245,7 +245,7 @@ def default_opts(**kw) -> Opts:
     _lib.bk_default_opts(ctypes.byref(o))
     for k, v in kw.items():
         if k == "inner" and isinstance(v, str):
-            v = {"fp64": BK_PREC_FP64, "fp32": BK_PREC_FP32, "f32x2": BK_PREC_F32X2}[v]
+            v = {"fp64": BK_PREC_FP64, "fp32": BK_PREC_FP32, "f32x2": BK_PREC_F32X2, "bf16": BK_PREC_BF16}[v]
         setattr(o, k, v)
     return o
 

@@ -173,6 +173,18 @@ cudaError_t launch_tsm_tn(int df, int64_t R, int64_t D, int N, const float* Z, i
                           const float* Tlo, int64_t ldt, double alpha, double beta, void* Y, int64_t ldy, void* work,
                           size_t work_bytes, int sms, cudaStream_t st);
 size_t tsm_tn_work_bytes(int64_t R, int64_t D, int N, int df, int sms);
+// ---- BF16 tensor-core Gram-form products (k_bf16.cu): Y = alpha Z^T (Z X) + beta Y for
+// FP32 X (d x N column-major, ldx) and Y (ldy), N <= 128, from BF16 head/tail copies of
+// the FP32 Z (n x d row-major, ldz) that launch_bf16_gram_split writes into `buf`
+// (bf16_gram_copy_bytes) once per operator. `work` holds bf16_gram_work_bytes; *err is
+// set to 1 if a pipeline wait gave up after wait_cycles SM clocks (0: the default).
+bool bf16_gram_usable(int64_t n, int64_t d, int N);
+size_t bf16_gram_copy_bytes(int64_t n, int64_t d);
+size_t bf16_gram_work_bytes(int64_t n, int64_t d, int N, int sms);
+cudaError_t launch_bf16_gram_split(int64_t n, int64_t d, const float* Z, int64_t ldz, void* buf, cudaStream_t st);
+cudaError_t launch_bf16_gram_apply(int64_t n, int64_t d, int N, const void* buf, const float* X, int64_t ldx, float* Y,
+                                   int64_t ldy, double alpha, double beta, void* work, size_t work_bytes,
+                                   long long wait_cycles, int* err, int sms, cudaStream_t st);
 // ---- Nystrom PCG (k_pcg.cu), FP64
 cudaError_t launch_csr_cols(int vals_f64, int64_t d, const int* rowptr, const int* colidx, const void* vals, int nc,
                             const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t st);

@@ -20,6 +20,8 @@ enum Slot {
   WS_BATCH, WS_BATCH_VALS,
   // tensor-core dense product: P^T head/tail, timeout flag
   WS_PT, WS_TCERR,
+  // BF16 Gram-form loads: head/tail copies of Z, product workspace
+  WS_BF16, WS_BF16W,
   WS_COUNT
 };
 

@@ -129,6 +129,12 @@ struct Lanczos {
   int *keep = nullptr, *rank = nullptr;
   Prof* prof = nullptr;  // optional event timing
   int df = 0;            // FP64 blocks: FP32 values through the compensated products
+  // FP32 blocks of a Gram-form operator on BF16 tensor cores (k_bf16.cu): the BF16
+  // copies of Z, the products' workspace and the timeout flag; null otherwise
+  const void* bz = nullptr;
+  void* bwork = nullptr;
+  size_t bwork_bytes = 0;
+  int* berr = nullptr;
   int t = 0;      // blocks in T_t
   int loads = 0;  // operator applications
   double rank_tol = 1e-12;
@@ -185,6 +191,9 @@ struct Lanczos {
     cudaError_t e;
     const int af = op.vals_f64;  // 1: FP64 values, 0: FP32 values
     if (!is64 && af) return cudaErrorInvalidValue;  // FP32 runs use FP32 values
+    if (!is64 && bz && op.kind == BK_GRAM)
+      return bk::launch_bf16_gram_apply(op.nrows, d, nc, bz, (const float*)X, ldx, (float*)Y, ldy, 1.0, 0.0, bwork,
+                                        bwork_bytes, 0, berr, c->sms, st);
     if (is64 && df && !af && (op.kind == BK_DENSE || op.kind == BK_GRAM) && bk::tsm_supported(op.vals, op.ld))
       return df_apply(c, op, (const double*)X, ldx, nc, (double*)Y, ldy, (double*)V, ldv, st);
     if (!is64 && (op.kind == BK_DENSE || op.kind == BK_GRAM) && bk::tsm_supported(op.vals, op.ld) &&
@@ -474,9 +483,14 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
   else
     bk_default_opts(&opts);
   if (!(opts.tol > 0.0) || opts.sketch < 0 || opts.max_loads < 1 || opts.max_refine < 1) return BK_ERR_ARG;
-  if (opts.inner != BK_PREC_FP64 && opts.inner != BK_PREC_FP32 && opts.inner != BK_PREC_F32X2)
+  if (opts.inner != BK_PREC_FP64 && opts.inner != BK_PREC_FP32 && opts.inner != BK_PREC_F32X2 &&
+      opts.inner != BK_PREC_BF16)
     return BK_ERR_UNSUPPORTED;
   if (o.kind == BK_RBF && opts.inner == BK_PREC_FP32) return BK_ERR_UNSUPPORTED;
+  const bool bf16 = opts.inner == BK_PREC_BF16;
+  if (bf16 && (o.kind != BK_GRAM || !bk::bf16_gram_usable(o.nrows, o.d, (int)std::min<int64_t>(
+                                                                   std::max<int64_t>(L, (int64_t)opts.sketch + 1), o.d))))
+    return BK_ERR_UNSUPPORTED;
   std::vector<double> hmu(L);
   BK_CK(cudaSetDevice(c->device));
   cudaStream_t st = c->stream;
@@ -484,7 +498,7 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
   BK_CK(cudaMemcpy(hmu.data(), mus, (size_t)L * 8, cudaMemcpyDefault));
   for (double v : hmu)
     if (!(v >= 0.0) || !std::isfinite(v)) return BK_ERR_ARG;
-  const int is64 = opts.inner != BK_PREC_FP32;
+  const int is64 = opts.inner != BK_PREC_FP32 && !bf16;
   const int64_t d = o.d;
   const int m = (int)std::min<int64_t>((int64_t)opts.sketch + 1, d);
   Prof prof;
@@ -500,6 +514,19 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
   LzOp o64 = o;  // refinement residuals use the values as given
   BK_CK(stage_lz_values(c, A, &o, is64, &staged));
   o64.vals = staged;
+  // BF16 loads: head/tail copies of Z (row-major and transposed), made once per call
+  void *bzc = nullptr, *bzw = nullptr;
+  size_t bzw_bytes = 0;
+  int* bzerr = nullptr;
+  if (bf16) {
+    const int nmax = (int)std::min<int64_t>(std::max<int64_t>(L, m), d);
+    BK_CK(ws_get(c, WS_BF16, bk::bf16_gram_copy_bytes(o.nrows, d), &bzc));
+    bzw_bytes = bk::bf16_gram_work_bytes(o.nrows, d, nmax, c->sms);
+    BK_CK(ws_get(c, WS_BF16W, bzw_bytes + 256, &bzw));
+    bzerr = (int*)((char*)bzw + bzw_bytes);
+    BK_CK(cudaMemsetAsync(bzerr, 0, sizeof(int), st));
+    BK_CK(bk::launch_bf16_gram_split(o.nrows, d, (const float*)o.vals, o.ld, bzc, st));
+  }
   const double* bd = nullptr;
   BK_CK(stage_in(c, WS_B64, b, (size_t)d * 8, (const void**)&bd));
   double* dmu = nullptr;
@@ -555,6 +582,12 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
     BK_CK(lz.init(c, ol, pis64, mb, tmax));
     lz.prof = &prof;
     lz.df = opts.inner == BK_PREC_F32X2 || escalated;
+    if (bf16 && !pis64) {
+      lz.bz = bzc;
+      lz.bwork = bzw;
+      lz.bwork_bytes = bzw_bytes;
+      lz.berr = bzerr;
+    }
     bool pass_flagged = false;
     // start block into W (block precision), column scales applied in FP64 first
     double* B0d = nullptr;
@@ -652,6 +685,16 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
       df_ok = false;  // recompute this residual in FP64
     }
     if (worst <= opts.tol) result = BK_OK;
+  }
+  if (bzerr) {  // a BF16 product whose pipeline wait gave up left an invalid load
+    BK_CK(cudaMemcpyAsync(c->hparts, bzerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BK_CK(cudaStreamSynchronize(st));
+    int herr = 0;
+    std::memcpy(&herr, c->hparts, sizeof(int));
+    if (herr) {
+      result = BK_TIMEOUT;
+      std::snprintf(c->last_error, sizeof(c->last_error), "tensor-core pipeline wait timed out");
+    }
   }
   BK_CK(cudaMemcpyAsync(X, Xd, (size_t)d * L * 8, cudaMemcpyDefault, st));
   BK_CK(cudaEventRecord(ev1, st));

@@ -66,35 +66,38 @@ def test_ridge_dense_path(bk, ctx, inner):
     np.testing.assert_allclose(X, direct.ridge_path(aa, mus, b), rtol=0, atol=1e-4 * np.abs(X).max())
 
 
-@pytest.mark.parametrize("inner", ["fp64", "fp32", "f32x2"])
+@pytest.mark.parametrize("inner", ["fp64", "fp32", "f32x2", "bf16"])
 def test_ridge_gram_path(bk, ctx, inner):
-    """A = Z^T Z matrix-free (two products over Z per load), FP32 Z."""
+    """A = Z^T Z matrix-free (two products over Z per load), FP32 Z. bf16: the loads on
+    the BF16 tensor cores (head/tail splits), FP64-accurate refinement residuals."""
     n, d, l = 3000, 256, 16
     Z, f, b = W.ridge_workload(W.BASE_SEED + 22, n, d, noise_std=1e-3)
     mus = np.logspace(-6, 0, 20)
-    tol = 1e-8 if inner == "fp32" else 1e-10
+    tol = 1e-8 if inner in ("fp32", "bf16") else 1e-10
     X = np.zeros((d, len(mus)), order="F")
     info = bk.ridge_path(ctx, bk.gram_operator(torch.from_numpy(Z).to(dev())), mus, b, X,
                          bk.default_opts(tol=tol, sketch=l, seed=6, inner=inner,
-                                         inner_tol=1e-5 if inner == "fp32" else 1e-6))
+                                         inner_tol=1e-5 if inner in ("fp32", "bf16") else 1e-6))
     op = operators.Gram(Z.astype(np.float64))
     res = shift_residuals(op, mus, X, b)
     assert res.max() <= tol, (res.max(), info.as_dict())
     assert info.loads <= 40 * info.refinements
 
 
-@pytest.mark.parametrize("d", [300, 257])
-def test_ridge_gram_tiles_and_ragged_edges(bk, ctx, d):
+@pytest.mark.parametrize("d,inner", [(300, "fp32"), (257, "fp32"), (300, "bf16"), (257, "bf16")])
+def test_ridge_gram_tiles_and_ragged_edges(bk, ctx, d, inner):
     """Block width 65 (sketch 64) over ragged row and column tiles. d = 300 runs the
     tall-skinny product kernels (FP32 loads, compensated FP64-accurate residuals) with a
     partial last tile in both dimensions; d = 257 has rows that are not 16-byte aligned
-    and takes the general GEMM. Both must meet 1e-8 in the oracle's FP64 residual."""
+    and takes the general GEMM. bf16: the BF16 tensor-core loads, whose TMA boxes run
+    past the last 64-wide K slice and the last 128-row tile (zero fill) in both products.
+    All must meet 1e-8 in the oracle's FP64 residual."""
     n = 5003
     Z, f, b = W.ridge_workload(W.BASE_SEED + 23, n, d, noise_std=1e-3)
     mus = np.logspace(-6, 0, 20)
     X = np.zeros((d, len(mus)), order="F")
     info = bk.ridge_path(ctx, bk.gram_operator(torch.from_numpy(Z).to(dev())), mus, b, X,
-                         bk.default_opts(tol=1e-8, sketch=64, seed=7, inner="fp32", inner_tol=1e-5, check_every=2))
+                         bk.default_opts(tol=1e-8, sketch=64, seed=7, inner=inner, inner_tol=1e-5, check_every=2))
     op = operators.Gram(Z.astype(np.float64))
     res = shift_residuals(op, mus, X, b)
     assert res.max() <= 1e-8, (res.max(), info.as_dict())
