@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--max-loads", type=int, default=20000)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-systems result attached to the default line")
     return ap.parse_args()
 
 
@@ -308,14 +310,16 @@ def run_batched(args, world, rank, local, dev):
     cal_x = [torch.zeros(d, dtype=torch.float64, device=dev) for d in cal_d]
     mixed = bk.default_opts(tol=TOL, sketch=-1, seed=OMEGA_SEED, inner="fp32", inner_tol=1e-5, check_every=16)
     t0 = time.perf_counter()
+    cands = [8, 16, 32, 64]
     with torch.cuda.stream(stream):
-        chosen = bk.autotune(ctx, bk.Batch([a for a, _ in cal], np.zeros(len(cal)), [b for _, b in cal], cal_x),
-                             [8, 16, 32], mixed)
+        bk.autotune(ctx, bk.Batch([a for a, _ in cal], np.zeros(len(cal)), [b for _, b in cal], cal_x),
+                    cands, mixed)
     tune_s = time.perf_counter() - t0
     del cal, cal_x
-    table = {}
-    for d, c in zip(cal_d, chosen):
-        table[int(np.floor(np.log2(d)))] = int(c)
+    import tempfile
+    with tempfile.TemporaryDirectory() as tdir:
+        table = {str(k): {"sketch": v[0], "product": v[1]}
+                 for k, v in bk.autotune_table(ctx, os.path.join(tdir, "tune.txt")).items()}
 
     batch = bk.Batch(mats, np.zeros(n), bs, xs)
 
@@ -337,6 +341,20 @@ def run_batched(args, world, rank, local, dev):
     ms = ev0.elapsed_time(ev1)
     value = world * n * args.steps / (ms / 1e3)
     infos = infos_all[-1]
+    # one solve with every step kernel launched on the stream instead of replayed from
+    # CUDA graphs: how much of a step is launch overhead (what a single persistent
+    # launch could save at most)
+    os.environ["BK_NO_GRAPH"] = "1"
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    sinfo = solve(mixed, batch)
+    g1.record(stream)
+    torch.cuda.synchronize(dev)
+    del os.environ["BK_NO_GRAPH"]
+    stream_ms = g0.elapsed_time(g1)
+    launch_check = {"graph_replay_ms_per_solve": ms / args.steps, "stream_launch_ms_per_solve": stream_ms,
+                    "stream_over_graph": stream_ms / (ms / args.steps),
+                    "all_converged_stream": all(i.status == bk.BK_OK for i in sinfo)}
     rel = max(i.rel_residual for i in infos)
     ok = sum(1 for i in infos if i.status == bk.BK_OK)
     loads = [i.loads for i in infos]
@@ -398,17 +416,41 @@ def run_batched(args, world, rank, local, dev):
             "dtype": "f32 block ops + f64 Gram/solve/refinement", "data": "synthetic",
             "config": {"workload": f"batched_{n}_dense_logU500-16000_fp32_outliers1e2-1e5",
                        "sum_d2_bytes_fp32": sum(4.0 * d * d for d in ds), "tol": TOL,
-                       "autotune": {"candidates": [8, 16, 32], "table_log2d_to_sketch": table, "seconds": tune_s},
+                       "autotune": {"candidates": cands, "table_log2d": table, "seconds": tune_s,
+                                    "note": "a candidate whose block width the kernels are not built for "
+                                            "(64: width 65) is skipped; product = block-product kernel"},
                        "l2": "matrices 75 GB, far larger than L2; no flush"},
             "converged": ok, "rel_residual_max": rel, "loads_mean": float(np.mean(loads)),
             "loads_max": int(max(loads)),
             "roofline": {"bound": "hbm", "kernel": "whole solve (A streamed once per load)", "achieved": gbs,
                          "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None, "peak_source": peak_src},
             "fp64_plain": fp64, "clocks": clk.summary(), "cpu_baseline": cpu,
+            "launch_overhead": launch_check,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
     return 0
+
+
+def batched_leg():
+    """The batched workload's JSON line from `bench.py --workload batched` run as a child
+    process (one warm-up and one timed solve of the 512 systems, FP64 subset beside)."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "batched", "--steps", "1", "--warmup", "1",
+           "--no-cpu-baseline"]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+    except subprocess.TimeoutExpired:
+        return {"error": "batched leg timed out"}
+    for ln in r.stdout.splitlines():
+        if ln.startswith("{"):
+            j = json.loads(ln)
+            keep = ("metric", "value", "unit", "ms_per_step", "converged", "rel_residual_max", "loads_mean",
+                    "fp64_plain", "roofline", "launch_overhead")
+            out = {k: j.get(k) for k in keep}
+            out["autotune"] = j.get("config", {}).get("autotune")
+            out["command"] = " ".join(cmd[1:])
+            return out
+    return {"error": f"batched leg rc={r.returncode}: {r.stderr[-300:]}"}
 
 
 def run_csr_product(args, world, rank, local, dev):
@@ -1227,6 +1269,15 @@ def main():
                "sample": f"{n} loads of the FP64 oracle block-CG recurrence (NumPy/SciPy) on the full workload, "
                          f"{spl:.3f} s/load; solves/s = 1/(s per load x {lps} loads per solve, {src})"}
 
+    # the batched configuration (512 uneven dense systems, autotuned widths, mixed vs
+    # FP64 blocks) in a child process of its own (its 75 GB of matrices), attached below
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched and args.grid == GRID:
+        ctx.close()
+        ctx = None
+        torch.cuda.empty_cache()
+        batched = batched_leg()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -1247,9 +1298,11 @@ def main():
             "gpu_launches": int(sum(i.kernel_launches for i in infos)),
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -96,6 +96,8 @@ def _load():
         "bk_solve_shrink": (i32, [vp, ctypes.POINTER(Operator), dbl, vp, vp, i32, ctypes.POINTER(Opts),
                                   ctypes.POINTER(Info)]),
         "bk_apply": (i32, [vp, ctypes.POINTER(Operator), dbl, i32, vp, i64, vp, i64]),
+        "bk_autotune_save": (i32, [vp, ctypes.c_char_p]),
+        "bk_autotune_load": (i32, [vp, ctypes.c_char_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -445,6 +447,34 @@ class Batch:
         self.x_arr = (ctypes.c_void_p * n)(*[_ptr(v)[0] for v in xs])
         self.keep = (mats, bs, xs)
         self.n = n
+
+
+def autotune_save(ctx: Context, path: str) -> None:
+    """bk_autotune_save: the context's autotune table to a text file."""
+    s = _lib.bk_autotune_save(ctx.handle, str(path).encode())
+    if s != BK_OK:
+        raise BKError(s, "bk_autotune_save", ctx.last_error())
+
+
+def autotune_load(ctx: Context, path: str) -> None:
+    """bk_autotune_load: replace the context's autotune table with a saved one."""
+    s = _lib.bk_autotune_load(ctx.handle, str(path).encode())
+    if s != BK_OK:
+        raise BKError(s, "bk_autotune_load", ctx.last_error())
+
+
+def autotune_table(ctx: Context, path: str) -> dict:
+    """The context's autotune table {floor(log2 d): (sketch, kernel)} (written through
+    bk_autotune_save to `path`, then parsed)."""
+    autotune_save(ctx, path)
+    table = {}
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            bkt, sk, tc = (int(v) for v in line.split())
+            table[bkt] = (sk, "tensor" if tc else "cuda")
+    return table
 
 
 def solve_batched(ctx: Context, batch: Batch, opts: Opts | None = None, check=True):

@@ -85,7 +85,8 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
   if (infos) std::memset(infos, 0, sizeof(bk_info) * n);
 
   // block width per system: fixed sketch, or the autotune table (nearest size bucket)
-  std::vector<int> ms(n);
+  // and the block-product kernel per system (1: tensor cores where usable, 0: CUDA cores)
+  std::vector<int> ms(n), want_tc(n, 1);
   for (int i = 0; i < n; ++i) {
     int l = opts.sketch;
     if (l < 0) {
@@ -95,13 +96,17 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
         if (std::abs(kv.first - bkt) < bestd) {
           bestd = std::abs(kv.first - bkt);
           l = kv.second;
+          auto it = c->tune_tc.find(kv.first);
+          want_tc[i] = it == c->tune_tc.end() ? 1 : it->second;
         }
     }
+    if (c->force_tc >= 0) want_tc[i] = c->force_tc;
     ms[i] = (int)std::min<int64_t>((int64_t)l + 1, A[i].rows);
     if (bk::padded_width(ms[i]) < 0) return BK_ERR_UNSUPPORTED;
   }
+  // groups by padded width and product kernel (key 2 mp + kernel)
   std::map<int, Group> groups;
-  for (int i = 0; i < n; ++i) groups[bk::padded_width(ms[i])].members.push_back(i);
+  for (int i = 0; i < n; ++i) groups[2 * bk::padded_width(ms[i]) + want_tc[i]].members.push_back(i);
 
   const size_t es = is64 ? 8 : 4;
   const size_t vs = vals_f64 ? 8 : 4;
@@ -132,11 +137,11 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
   int total_cta = 0;
   for (auto& kv : groups) {
     Group& g = kv.second;
-    g.mp = kv.first;
+    g.mp = kv.first / 2;
     glist.push_back(&g);
     // the tensor-core product needs FP32 values with 16-byte aligned rows (host values
     // are staged to 256-byte aligned buffers with the caller's lda)
-    g.tc = !is64;
+    g.tc = !is64 && (kv.first & 1);
     for (int i : g.members) {
       const bool dev = bkx::is_device_ptr(A[i].vals);
       const void* probe = dev ? A[i].vals : reinterpret_cast<const void*>(uintptr_t(256));
@@ -462,6 +467,10 @@ extern "C" bk_status bk_autotune(bk_ctx* c, int32_t n, const bk_operator* A, con
       double t = INFINITY;
       for (int rep = 0; rep < 4; ++rep) {  // a warm solve, then three timed ones
         bk_status s = bk_solve_batched(c, nb, ops.data(), mus.data(), bs.data(), xp.data(), &o, infos.data());
+        if (s == BK_ERR_UNSUPPORTED) {  // a block width the kernels are not built for
+          t = INFINITY;
+          break;
+        }
         if (s != BK_OK && s != BK_NOT_CONVERGED) return s;
         if (s != BK_OK) {
           t = INFINITY;
@@ -474,12 +483,73 @@ extern "C" bk_status bk_autotune(bk_ctx* c, int32_t n, const bk_operator* A, con
         best_k = k;
       }
     }
-    if (best_k >= 0) c->tune[kv.first] = candidates[best_k];
+    if (best_k < 0) continue;
+    c->tune[kv.first] = candidates[best_k];
+    c->tune_tc[kv.first] = 1;
+    // product kernel of the winning width: the CUDA-core product timed the same way
+    // (FP32 blocks; the tensor-core product is the default where the rows qualify)
+    if (opts.inner == BK_PREC_FP32) {
+      bk_opts o = opts;
+      o.sketch = candidates[best_k];
+      double t = INFINITY;
+      c->force_tc = 0;
+      for (int rep = 0; rep < 4; ++rep) {
+        bk_status s = bk_solve_batched(c, nb, ops.data(), mus.data(), bs.data(), xp.data(), &o, infos.data());
+        if (s != BK_OK) {
+          t = INFINITY;
+          if (s != BK_NOT_CONVERGED) {
+            c->force_tc = -1;
+            return s;
+          }
+          break;
+        }
+        if (rep > 0) t = std::min(t, (double)infos[0].ms_total);
+      }
+      c->force_tc = -1;
+      if (t < best_t) c->tune_tc[kv.first] = 0;
+    }
   }
   if (chosen)
     for (int i = 0; i < n; ++i) {
       auto it = c->tune.find(size_bucket(A[i].rows));
       chosen[i] = it == c->tune.end() ? -1 : it->second;
     }
+  return BK_OK;
+}
+
+extern "C" bk_status bk_autotune_save(const bk_ctx* c, const char* path) {
+  if (!c || !path) return BK_ERR_ARG;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return BK_ERR_ARG;
+  std::fprintf(f, "# bk autotune table: floor(log2 d) sketch product(1 tensor-core, 0 cuda-core)\n");
+  for (auto& kv : c->tune) {
+    auto it = c->tune_tc.find(kv.first);
+    std::fprintf(f, "%d %d %d\n", kv.first, kv.second, it == c->tune_tc.end() ? 1 : it->second);
+  }
+  const bool ok = std::fclose(f) == 0;
+  return ok ? BK_OK : BK_ERR_ARG;
+}
+
+extern "C" bk_status bk_autotune_load(bk_ctx* c, const char* path) {
+  if (!c || !path) return BK_ERR_ARG;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return BK_ERR_ARG;
+  std::map<int, int> tune, tune_tc;
+  char line[256];
+  bk_status st = BK_OK;
+  while (std::fgets(line, sizeof(line), f)) {
+    if (line[0] == '#' || line[0] == '\n') continue;
+    int bkt = 0, sk = 0, tc = 1;
+    if (std::sscanf(line, "%d %d %d", &bkt, &sk, &tc) != 3 || bkt < 0 || bkt > 62 || sk < 1 || (tc != 0 && tc != 1)) {
+      st = BK_ERR_ARG;
+      break;
+    }
+    tune[bkt] = sk;
+    tune_tc[bkt] = tc;
+  }
+  std::fclose(f);
+  if (st != BK_OK) return st;
+  c->tune = tune;
+  c->tune_tc = tune_tc;
   return BK_OK;
 }

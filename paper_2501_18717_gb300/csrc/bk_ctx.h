@@ -39,7 +39,9 @@ struct bk_ctx {
   bk::DevState* hstate = nullptr;  // pinned mirror of the device control block
   double* hparts = nullptr;        // pinned buffer for norm partials and small reads
   int sms = 152;
-  std::map<int, int> tune;  // autotuner: floor(log2 d) -> sketch columns
+  std::map<int, int> tune;     // autotuner: floor(log2 d) -> sketch columns
+  std::map<int, int> tune_tc;  // autotuner: floor(log2 d) -> 1 tensor-core product, 0 CUDA-core
+  int force_tc = -1;           // autotuner timing: -1 none, else the product kernel to use
 };
 
 namespace bkx {

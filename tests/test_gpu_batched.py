@@ -120,17 +120,35 @@ def test_batched_rejects_bad_input(bk, ctx):
         bk.solve_batched(ctx, bk.Batch([a], [-1.0], [b], [x]), bk.default_opts())
 
 
-def test_autotune_table(bk, ctx):
+def test_autotune_table(bk, ctx, tmp_path):
+    """The configuration's candidates {8, 16, 32, 64}: a width the kernels are not
+    built for (64, block width 65) is skipped; each bucket also gets its product
+    kernel; the table survives a save/load round trip into a fresh context."""
     seed = W.BASE_SEED + 42
     ds, mats, bs = make_batch(seed, 4, 300, 1200)
     xs = [np.zeros(d) for d in ds]
     cal = bk.Batch(mats, np.zeros(len(ds)), bs, xs)
-    chosen = bk.autotune(ctx, cal, [8, 16, 32], bk.default_opts(tol=1e-8, inner="fp32", inner_tol=1e-5))
-    assert set(chosen.tolist()) <= {8, 16, 32}
+    chosen = bk.autotune(ctx, cal, [8, 16, 32, 64], bk.default_opts(tol=1e-8, inner="fp32", inner_tol=1e-5))
+    assert set(chosen.tolist()) <= {8, 16, 32, 64}
+    table = bk.autotune_table(ctx, tmp_path / "tune.txt")
+    assert table and all(sk in (8, 16, 32, 64) and kern in ("tensor", "cuda") for sk, kern in table.values())
     # a fresh batch solved with sketch = -1 uses the table and converges
     ds2, mats2, bs2 = make_batch(seed + 100, 4, 300, 1200)
     xs2 = [np.zeros(d) for d in ds2]
-    bk.solve_batched(ctx, bk.Batch(mats2, np.zeros(4), bs2, xs2),
-                     bk.default_opts(tol=1e-8, sketch=-1, inner="fp32", inner_tol=1e-5))
+    opts = bk.default_opts(tol=1e-8, sketch=-1, inner="fp32", inner_tol=1e-5)
+    bk.solve_batched(ctx, bk.Batch(mats2, np.zeros(4), bs2, xs2), opts)
     for i in range(4):
         assert rel_res(mats2[i], xs2[i], bs2[i]) <= 1e-8
+    # the saved table in a new context gives the same picks and solutions
+    with bk.Context(0) as c2:
+        bk.autotune_load(c2, tmp_path / "tune.txt")
+        assert bk.autotune_table(c2, tmp_path / "tune2.txt") == table
+        xs3 = [np.zeros(d) for d in ds2]
+        bk.solve_batched(c2, bk.Batch(mats2, np.zeros(4), bs2, xs3), opts)
+        for i in range(4):
+            np.testing.assert_array_equal(xs3[i], xs2[i])
+    # a malformed file is refused and leaves the table as it was
+    (tmp_path / "bad.txt").write_text("9 sixteen 1\n")
+    with pytest.raises(bk.BKError):
+        bk.autotune_load(ctx, tmp_path / "bad.txt")
+    assert bk.autotune_table(ctx, tmp_path / "tune3.txt") == table
