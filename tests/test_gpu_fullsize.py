@@ -25,18 +25,20 @@ def ctx(bk):
     c.close()
 
 
-def test_ridge_path_full_size(bk, ctx):
+@pytest.mark.parametrize("inner", ["bf16", "fp32"])
+def test_ridge_path_full_size(bk, ctx, inner):
     """Z 200,000 x 4096 FP32 (sigma_i = 1/i plus N(0, 1e-6) noise), 64 shifts in
-    [1e-6, 1], sketch 64, FP32 inner products with FP64-accurate refinement residuals:
-    every sampled shift's residual, recomputed by the oracle in FP64 from the stored Z,
-    is at most 1e-8."""
+    [1e-6, 1], sketch 64, BF16 tensor-core loads (the configuration's precision, as the
+    bench leg runs them) or FP32 loads, with FP64-accurate refinement residuals: every
+    sampled shift's residual, recomputed by the oracle in FP64 from the stored Z, is at
+    most 1e-8."""
     dev = torch.device("cuda:0")
     n, d, L = 200000, 4096, 64
     Z, f, b = W.ridge_workload_torch(W.BASE_SEED + 3, n, d, 1e-3, dev)
     mus = np.logspace(-6, 0, L)
     X = torch.zeros((L, d), dtype=torch.float64, device=dev)
     info = bk.ridge_path(ctx, bk.gram_operator(Z), mus, b, X,
-                         bk.default_opts(tol=1e-8, sketch=64, seed=W.BASE_SEED + 3, inner="fp32", inner_tol=1e-5,
+                         bk.default_opts(tol=1e-8, sketch=64, seed=W.BASE_SEED + 3, inner=inner, inner_tol=1e-5,
                                          check_every=2, max_loads=400), check=False)
     assert info.status == bk.BK_OK, info.as_dict()
     op = operators.Gram(Z.cpu().numpy())
