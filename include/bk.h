@@ -158,6 +158,9 @@ typedef struct {
                              numerically dependent (rank test of the small
                              factorisation of R^T R), summed over the inner solves; a
                              dropped column stays out until the next restart */
+  int32_t fp64_fallback;  /* bk_solve, bk_solve_batched with BK_PREC_FP32: 1 if the
+                             FP32-block passes stopped reducing the FP64 residual and
+                             the rest of the solve ran in FP64 blocks */
 } bk_info;
 
 /* Fills *opts with defaults: tol 1e-10, max_loads 20000, sketch 20, seed 0,
@@ -190,6 +193,16 @@ const char* bk_last_error(const bk_ctx* ctx);
  * on the tensor cores (TF32 with split operands and FP32 sums of 32-wide K slices,
  * FP32 accuracy) when the rows are 16-byte aligned (base 16-byte aligned, ld a
  * multiple of 4; the library's own FP32 copy always is), else on FFMA.
+ * Each refinement pass forms x + ||r|| x_inner and its FP64 residual. An inner solve
+ * stops as a breakdown when its recurrence estimate ||c|| is not finite or above 1e8
+ * (the finite-precision recurrence lost orthogonality); a pass whose residual is not
+ * finite, or that broke down without reducing it, is discarded (x stays as it was)
+ * and ends the solve with BK_BREAKDOWN, and a second pass that reduces the residual
+ * less than twofold ends it with BK_STAGNATED. With FP32 blocks either case instead
+ * hands the rest of the solve to FP64 blocks on the residual system A_mu delta = r,
+ * x <- x + delta (info->fp64_fallback = 1). FP32 blocks wider than about 48 on systems
+ * of a few hundred unknowns, where a few loads exhaust the space, are the case seen
+ * to need it.
  * Returns BK_TIMEOUT (x holds the last refined iterate) if a tensor-core pipeline
  * wait gave up. */
 bk_status bk_solve(bk_ctx* ctx, const bk_operator* A, double mu, const double* b, double* x,
@@ -322,7 +335,11 @@ bk_status bk_solve_shrink(bk_ctx* ctx, const bk_operator* A, double mu, const do
  * every step of the block-CG recurrence (Def. BCG) runs as one launch over all systems
  * of a group, each system owning thread blocks in proportion to d_i^2 m_i; a chunk of
  * check_every steps is replayed as a CUDA graph and systems that have converged skip
- * their work. FP64 refinement restarts as in bk_solve.
+ * their work. FP64 refinement restarts as in bk_solve, with the same stopping rules
+ * per system (a pass that lost its recurrence is undone and stops that system; two
+ * passes that reduce its residual less than twofold stop it). With FP32 blocks, the
+ * systems stopped that way are solved again from x = 0 in FP64 blocks, in one nested
+ * batch (their info->fp64_fallback = 1; loads and passes add up).
  *   A      n dense operators, all FP32 or all FP64 values (BK_DENSE only). With FP32
  *          blocks, a width group whose matrices all have 16-byte aligned rows (device
  *          base 16-byte aligned, ld a multiple of 4) runs its block products on the

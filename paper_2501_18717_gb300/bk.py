@@ -51,7 +51,8 @@ class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("loads", ctypes.c_int32), ("refinements", ctypes.c_int32),
                 ("residual_loads", ctypes.c_int32), ("rel_residual", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_kernel", ctypes.c_double * 8), ("launches", ctypes.c_int32 * 8),
-                ("kernel_launches", ctypes.c_int32), ("deflations", ctypes.c_int32)]
+                ("kernel_launches", ctypes.c_int32), ("deflations", ctypes.c_int32),
+                ("fp64_fallback", ctypes.c_int32)]
 
     def as_dict(self):
         out = {}

@@ -221,7 +221,7 @@ bk_status bk_gaussian(bk_ctx* c, uint64_t seed, uint32_t stream, int64_t n, int6
 bk_status bk_chol_solve(bk_ctx* c, int64_t m, const double* G, const double* S, double* X) {
   err_ctx() = c;
   if (c) c->last_error[0] = 0;
-  if (!c || !G || !S || !X || m < 1 || m > 64) return BK_ERR_ARG;
+  if (!c || !G || !S || !X || m < 1 || m > bk::kMaxWidth) return BK_ERR_ARG;
   BK_CK(cudaSetDevice(c->device));
   size_t bytes = (size_t)m * m * 8;
   const void *g = nullptr, *s = nullptr;
@@ -331,10 +331,13 @@ bk_status bk_block_apply(bk_ctx* c, const bk_operator* A, double mu, int32_t dty
   return BK_OK;
 }
 
-bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, double* x, const bk_opts* opts_in,
-                   bk_info* info) {
+// allow_fallback: FP32-block passes that stop reducing the residual hand the rest of
+// the solve to FP64 blocks (a nested call on the residual system, which has no
+// fallback itself).
+static bk_status solve_impl(bk_ctx* c, const bk_operator* A, double mu, const double* b, double* x,
+                            const bk_opts* opts_in, bk_info* info, bool allow_fallback) {
   err_ctx() = c;
-  if (c) c->last_error[0] = 0;
+  if (c && allow_fallback) c->last_error[0] = 0;
   if (info) std::memset(info, 0, sizeof(*info));
   if (!c || !b || !x) return BK_ERR_ARG;
   bk_status s = check_operator(A);
@@ -386,6 +389,10 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
   BK_CK(ws_get(c, WS_XIN, (size_t)d * 8, (void**)&w.xin));
   BK_CK(ws_get(c, WS_X64, (size_t)d * 8, (void**)&w.x64));
   BK_CK(ws_get(c, WS_R64, (size_t)d * 8, (void**)&w.r64));
+  // trial iterate and residual of each refinement pass (swapped with x64 / r64 when kept)
+  double *xt = nullptr, *rt = nullptr;
+  BK_CK(ws_get(c, WS_XT, (size_t)d * 8, (void**)&xt));
+  BK_CK(ws_get(c, WS_RT, (size_t)d * 8, (void**)&rt));
   // dense FP32 products run on the tensor cores when the matrix layout allows TMA
   const bool use_tc = o.kind == BK_DENSE && !is64 && bk::dense_tc_usable(d, vin, lda_in, mp);
   w.npG = (o.kind == BK_CSR) ? bk::csr_spmm_gram_grid(is64, mp, d, c->device)
@@ -398,12 +405,13 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
   BK_CK(ws_get(c, WS_PARTS_G, (size_t)w.npG * ne * 8, (void**)&w.partsG));
   BK_CK(ws_get(c, WS_PARTS_S, (size_t)npSmax * ne * 8, (void**)&w.partsS));
   size_t mm = (size_t)m * m, mpp = (size_t)mp * mp;
+  const size_t ncv = mp > 64 ? (size_t)mp : 64;  // slots of c (m <= mp)
   double* mats = nullptr;
-  BK_CK(ws_get(c, WS_MATS, (2 * mm + 64 + 3 * mpp + mp) * 8 + 256, (void**)&mats));
+  BK_CK(ws_get(c, WS_MATS, (2 * mm + ncv + 3 * mpp + mp) * 8 + 256, (void**)&mats));
   w.G = mats;
   w.S = w.G + mm;
   w.cvec = w.S + mm;
-  w.gi_t = (void*)(w.cvec + 64);
+  w.gi_t = (void*)(w.cvec + ncv);
   w.ti_t = (void*)((char*)w.gi_t + mpp * 8);
   w.t_t = (void*)((char*)w.ti_t + mpp * 8);
   w.xc_t = (void*)((char*)w.t_t + mpp * 8);
@@ -423,6 +431,7 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
   const double bnorm = std::sqrt(bnorm2);
 
   int loads = 0, refinements = 0, residual_loads = 0, stagnant = 0, deflations = 0;
+  bool fallback = false;
   // Inner target floor: an inner solve in FP32 blocks stops reducing the true residual
   // at a level set by the block precision and the conditioning (the recurrence keeps
   // going below it). When a pass that met its target reduced the FP64 residual by far
@@ -558,11 +567,26 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
       result = BK_TIMEOUT;
       break;
     }
-    BK_CK(bk::launch_axpy(d, rnorm, w.xin, w.x64, st));
+    // trial iterate x + ||r|| xin and its FP64 residual. A pass whose residual is not
+    // finite, or that broke down without reducing it, lost its recurrence: x stays as
+    // it was (the next pass would repeat this one). Any other pass is kept, also one
+    // capped by the load limit whose residual grew (the CG residual 2-norm is not
+    // monotone).
+    BK_CK(bk::launch_axpy_out(d, rnorm, w.xin, w.x64, xt, st));
     double rn = 0.0;
-    BK_CK(residual(c, o, mu, w.x64, bd, w.r64, w.normp, &rn));
+    BK_CK(residual(c, o, mu, xt, bd, rt, w.normp, &rn));
     residual_loads += 1;
     launches += 2;  // axpy, residual
+    if (!std::isfinite(rn) || (hs.status == bk::ST_BREAKDOWN && !(rn < rnorm))) {
+      if (!is64 && allow_fallback) {
+        fallback = true;
+        break;
+      }
+      result = BK_BREAKDOWN;
+      break;
+    }
+    std::swap(w.x64, xt);
+    std::swap(w.r64, rt);
     if (rn <= opts.tol * bnorm) {
       rnorm = rn;
       result = BK_OK;
@@ -570,22 +594,54 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
     }
     const double achieved = rn / rnorm;
     if (hs.status == bk::ST_CONVERGED && achieved > 4.0 * target) floor_target = 0.5 * achieved;
-    if (!(rn < 0.5 * rnorm)) {
-      if (hs.status == bk::ST_BREAKDOWN && !(rn < rnorm)) {
-        rnorm = rn;
-        result = BK_BREAKDOWN;
-        break;
-      }
-      if (++stagnant >= 2) {
-        rnorm = rn;
-        result = BK_STAGNATED;
-        break;
-      }
-    }
     rnorm = rn;
+    if (!(achieved < 0.5) && ++stagnant >= 2) {
+      if (!is64 && allow_fallback) {
+        fallback = true;
+        break;
+      }
+      result = BK_STAGNATED;
+      break;
+    }
   }
   if (gexec) cudaGraphExecDestroy(gexec);
   for (auto& e : pev) cudaEventDestroy(e);
+
+  if (fallback) {
+    // FP32 blocks stopped reducing the residual: the correction delta of A_mu delta = r
+    // is solved in FP64 blocks (a nested solve with FP64 residuals as before) and
+    // x <- x + delta. x and r move to slots the nested solve does not use.
+    double *fx = nullptr, *fr = nullptr, *fd = nullptr;
+    BK_CK(ws_get(c, WS_FB_X, (size_t)d * 8, (void**)&fx));
+    BK_CK(ws_get(c, WS_FB_R, (size_t)d * 8, (void**)&fr));
+    BK_CK(ws_get(c, WS_FB_D, (size_t)d * 8, (void**)&fd));
+    BK_CK(cudaMemcpyAsync(fx, w.x64, (size_t)d * 8, cudaMemcpyDeviceToDevice, st));
+    BK_CK(cudaMemcpyAsync(fr, w.r64, (size_t)d * 8, cudaMemcpyDeviceToDevice, st));
+    w.x64 = fx;
+    result = BK_NOT_CONVERGED;
+    if (opts.max_loads > loads) {
+      bk_opts o64 = opts;
+      o64.inner = BK_PREC_FP64;
+      o64.tol = opts.tol * bnorm / rnorm;
+      o64.max_loads = opts.max_loads - loads;
+      o64.max_refine = std::max(1, opts.max_refine - refinements);
+      bk_info sub;
+      const bk_status ss = solve_impl(c, A, mu, fr, fd, &o64, &sub, false);
+      if (ss != BK_OK && ss != BK_NOT_CONVERGED && ss != BK_BREAKDOWN && ss != BK_STAGNATED) return ss;
+      BK_CK(bk::launch_axpy(d, 1.0, fd, fx, st));
+      loads += sub.loads;
+      refinements += sub.refinements;
+      residual_loads += sub.residual_loads;
+      deflations += sub.deflations;
+      launches += sub.kernel_launches + 1;
+      for (int k = 0; k < 8; ++k) {
+        ms_k[k] += sub.ms_kernel[k];
+        n_k[k] += sub.launches[k];
+      }
+      rnorm *= sub.rel_residual;
+      result = ss;
+    }
+  }
 
   // result back to the caller's x
   BK_CK(cudaMemcpyAsync(x, w.x64, (size_t)d * 8, cudaMemcpyDefault, st));
@@ -608,8 +664,14 @@ bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, 
       info->launches[k] = n_k[k];
     }
     info->kernel_launches = launches;
+    info->fp64_fallback = fallback ? 1 : 0;
   }
   return result;
+}
+
+bk_status bk_solve(bk_ctx* c, const bk_operator* A, double mu, const double* b, double* x, const bk_opts* opts_in,
+                   bk_info* info) {
+  return solve_impl(c, A, mu, b, x, opts_in, info, true);
 }
 
 }  // extern "C"

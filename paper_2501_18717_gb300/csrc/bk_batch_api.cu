@@ -118,6 +118,11 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
   // rule of bk_solve: after a pass that met its target but reduced the FP64 residual by
   // far less, later passes stop at half the reduction it achieved)
   std::vector<double> floor_t(n, 0.0), last_t(n, 0.0), last_r(n, 0.0);
+  // systems that stopped: a pass that lost its recurrence (BK_BREAKDOWN: residual not
+  // finite, or a breakdown that did not reduce it; the next pass would repeat it) or two
+  // passes that reduced the residual less than twofold (BK_STAGNATED), and the count of
+  // such slow passes
+  std::vector<int> failed(n, 0), stag(n, 0);
   bk_status result = BK_OK;
   std::vector<Group*> glist;
   auto cleanup = [&]() {
@@ -301,7 +306,7 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
         const int i = s.index;
         const bool conv = rnorm[i] <= opts.tol * bnorm[i];
         if (conv) status[i] = BK_OK;
-        s.active = (!conv && loads[i] < opts.max_loads) ? 1 : 0;
+        s.active = (!conv && loads[i] < opts.max_loads && !failed[i]) ? 1 : 0;
         nactive += s.active;
         s.rnorm = rnorm[i];
         s.rscale = rnorm[i] > 0 ? 1.0 / rnorm[i] : 0.0;
@@ -380,16 +385,41 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
       BK_CKG(bk::launch_batch_axpy(g->ds, g->cta_sys, g->ncta, st));
     }
     BK_CKG(residuals());
+    bool any_revert = false;
     for (Group* g : glist)
       for (bk::BSys& s : g->hs) {
         const int i = s.index;
-        if (!s.active || last_r[i] <= 0.0) continue;
+        const bool ran = s.active && last_r[i] > 0.0;
+        s.active = 0;
+        if (!ran) continue;
+        // a residual that is not finite, or a breakdown that did not reduce it: the pass
+        // lost its recurrence (the rule of bk_solve)
+        if (!std::isfinite(rnorm[i]) || (hst[i].status == bk::ST_BREAKDOWN && !(rnorm[i] < last_r[i]))) {
+          failed[i] = BK_BREAKDOWN;
+          if (is64) {  // undo x += ||r|| xin (FP32 systems are solved again below)
+            s.active = 1;
+            s.rnorm = -s.rnorm;
+            any_revert = true;
+          }
+          continue;
+        }
         const double achieved = rnorm[i] / last_r[i];
         if (conv_inner[i] && achieved > 4.0 * last_t[i]) floor_t[i] = 0.5 * achieved;
+        if (!(achieved < 0.5) && ++stag[i] >= 2) failed[i] = BK_STAGNATED;
       }
+    if (any_revert) {
+      for (Group* g : glist) {
+        BK_CKG(cudaMemcpyAsync(g->ds, g->hs.data(), sizeof(bk::BSys) * g->hs.size(), cudaMemcpyHostToDevice, st));
+        BK_CKG(bk::launch_batch_axpy(g->ds, g->cta_sys, g->ncta, st));
+      }
+      BK_CKG(residuals());
+    }
   }
   for (int i = 0; i < n; ++i) {
-    if (rnorm[i] <= opts.tol * bnorm[i]) status[i] = BK_OK;
+    if (rnorm[i] <= opts.tol * bnorm[i])
+      status[i] = BK_OK;
+    else if (failed[i])
+      status[i] = failed[i];
     if (status[i] != BK_OK) result = BK_NOT_CONVERGED;
   }
   for (Group* g : glist)
@@ -412,6 +442,51 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
     }
   cleanup();
 #undef BK_CKG
+  if (is64) return result;
+  // FP32 blocks stopped reducing these systems' residuals: they are solved again from
+  // x = 0 in FP64 blocks (the FP32 values promoted in the products), in one nested batch
+  std::vector<int> redo;
+  int max_used = 0;
+  for (int i = 0; i < n; ++i)
+    if (failed[i] && status[i] != BK_OK) {
+      redo.push_back(i);
+      max_used = std::max(max_used, loads[i]);
+    }
+  if (redo.empty() || max_used >= opts.max_loads) return result;
+  const int nr = (int)redo.size();
+  std::vector<bk_operator> ra((size_t)nr);
+  std::vector<double> rmu((size_t)nr);
+  std::vector<const double*> rb((size_t)nr);
+  std::vector<double*> rx((size_t)nr);
+  std::vector<bk_info> ri((size_t)nr);
+  for (int k = 0; k < nr; ++k) {
+    ra[k] = A[redo[k]];
+    rmu[k] = mu[redo[k]];
+    rb[k] = b[redo[k]];
+    rx[k] = x[redo[k]];
+  }
+  bk_opts o64 = opts;
+  o64.inner = BK_PREC_FP64;
+  o64.max_loads = opts.max_loads - max_used;
+  const bk_status rs = bk_solve_batched(c, nr, ra.data(), rmu.data(), rb.data(), rx.data(), &o64, ri.data());
+  if (rs != BK_OK && rs != BK_NOT_CONVERGED) return rs;
+  result = BK_OK;
+  for (int k = 0; k < nr; ++k) status[redo[k]] = ri[k].status;
+  for (int i = 0; i < n; ++i)
+    if (status[i] != BK_OK) result = BK_NOT_CONVERGED;
+  if (infos) {
+    for (int k = 0; k < nr; ++k) {
+      bk_info& f = infos[redo[k]];
+      f.status = ri[k].status;
+      f.loads += ri[k].loads;
+      f.refinements += ri[k].refinements;
+      f.residual_loads += ri[k].residual_loads;
+      f.rel_residual = ri[k].rel_residual;
+      f.deflations += ri[k].deflations;
+      f.fp64_fallback = 1;
+    }
+    for (int i = 0; i < n; ++i) infos[i].ms_total += ri[0].ms_total;
+  }
   return result;
 }
 
@@ -485,10 +560,12 @@ extern "C" bk_status bk_autotune(bk_ctx* c, int32_t n, const bk_operator* A, con
     }
     if (best_k < 0) continue;
     c->tune[kv.first] = candidates[best_k];
-    c->tune_tc[kv.first] = 1;
+    const bool tc_built = bk::padded_width(candidates[best_k] + 1) <= bk::kTcMaxPadded;
+    c->tune_tc[kv.first] = tc_built ? 1 : 0;
     // product kernel of the winning width: the CUDA-core product timed the same way
-    // (FP32 blocks; the tensor-core product is the default where the rows qualify)
-    if (opts.inner == BK_PREC_FP32) {
+    // (FP32 blocks; the tensor-core product is the default where the rows qualify and
+    // the width is one it is built for)
+    if (opts.inner == BK_PREC_FP32 && tc_built) {
       bk_opts o = opts;
       o.sketch = candidates[best_k];
       double t = INFINITY;

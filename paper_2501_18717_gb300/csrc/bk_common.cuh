@@ -34,17 +34,27 @@ struct DevState {
 
 enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_LOADCAP = 3 };
 
+// The recurrence's residual estimate ||c|| starts at 1; the CG residual 2-norm can grow
+// transiently, by at most about sqrt(kappa). An estimate above this bound, or not
+// finite, means the finite-precision recurrence has lost its orthogonality (seen with
+// FP32 blocks wider than about 48 on systems of a few hundred unknowns, where a few
+// loads exhaust the space): the inner solve stops as a breakdown.
+constexpr double kDivergedRes = 1e8;
+
 // Padded block widths the kernels are compiled for (multiples of 4 for the 4x4
-// register blocks of the Gram kernels).
-constexpr int kMaxWidth = 36;
+// register blocks of the Gram kernels). Width 65 (sketch 64) pads to 68.
+constexpr int kMaxWidth = 65;
 inline int padded_width(int m) {
   if (m <= 4) return 4;
   if (m <= 8) return 8;
   if (m <= 16) return 16;
   if (m <= 24) return 24;
   if (m <= 36) return 36;
+  if (m <= 68) return 68;
   return -1;
 }
+// Widest padded block the tensor-core dense products are built for.
+constexpr int kTcMaxPadded = 36;
 // Entries of one Gram partial: upper-triangular 4x4 blocks, 16 entries each.
 inline int gram_entries(int mp) {
   int nb = mp / 4;
@@ -129,6 +139,8 @@ cudaError_t launch_dense_residual(int vals_f64, int64_t d, const void* A, int64_
                                   int nparts, cudaStream_t st);
 // x += a * y (FP64)
 cudaError_t launch_axpy(int64_t d, double a, const double* y, double* x, cudaStream_t st);
+// out = x + a y (out may alias y)
+cudaError_t launch_axpy_out(int64_t d, double a, const double* y, const double* x, double* out, cudaStream_t st);
 // FP64 -> FP32 copy
 cudaError_t launch_to_f32(int64_t n, const double* in, float* out, cudaStream_t st);
 // FP32 -> FP64 copy

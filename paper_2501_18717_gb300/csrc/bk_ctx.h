@@ -22,6 +22,9 @@ enum Slot {
   WS_PT, WS_TCERR,
   // BF16 Gram-form loads: head/tail copies of Z, product workspace
   WS_BF16, WS_BF16W,
+  // single solve: trial iterate and residual of a refinement pass; FP64-block fallback
+  // (iterate, residual, correction kept across the nested solve)
+  WS_XT, WS_RT, WS_FB_X, WS_FB_R, WS_FB_D,
   WS_COUNT
 };
 

@@ -13,7 +13,7 @@
 
 namespace bk {
 
-constexpr int kSmallMax = 64;
+constexpr int kSmallMax = 68;  // widest padded block
 constexpr int kLds = kSmallMax + 1;
 
 struct SmallShared {

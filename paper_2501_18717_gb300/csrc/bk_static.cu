@@ -23,6 +23,7 @@ namespace {
 // partials of every launch on GPUs with up to 182 SMs (4 x 182 x 720 <= 2^19); larger
 // grids are refused with BK_ERR_TOO_LARGE.
 constexpr size_t kStaticParts = (size_t)1 << 19;
+constexpr int kStaticMaxWidth = 36;
 __device__ __align__(256) double g_static_parts[kStaticParts];
 
 constexpr int kMaxDevices = 64;
@@ -72,7 +73,7 @@ extern "C" bk_status bk_block_apply_static(const bk_operator* A, double mu, int3
   // no conversion buffer: the values must already be in the block precision
   if (A->dtype != dtype) return BK_ERR_UNSUPPORTED;
   const int mp = bk::padded_width((int)m);
-  if (mp < 0 || m > bk::kMaxWidth) return BK_ERR_UNSUPPORTED;
+  if (mp < 0 || m > kStaticMaxWidth) return BK_ERR_UNSUPPORTED;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) {
     cudaGetLastError();

@@ -5,7 +5,9 @@
 //
 // Work split: the MP x MP result is cut into 4x4 register blocks; only the blocks on or
 // above the diagonal are formed (NT of them). Thread s owns block s mod NT and the tile
-// rows congruent to s / NT modulo NPH = blockDim / NT.
+// rows congruent to s / NT modulo NPH = blockDim / NT. When there are more blocks than
+// threads (width 68 in 128-thread blocks: 153 blocks), thread s owns blocks s, s +
+// blockDim, ... (BPT = ceil(NT / blockDim) of them) and every row of the tile.
 //
 // Precision: FP64 tiles accumulate in FP64. FP32 tiles multiply and add in FP32 within
 // one tile (at most TM / NPH rows per thread) and carry the running sum across tiles as
@@ -26,7 +28,14 @@ struct GramShape {
   static constexpr int NE = NT * 16;
 };
 
-template <typename T, int MP>
+// Blocks per thread for a kernel launched with NTH threads per block.
+template <int MP, int NTH>
+__host__ __device__ constexpr int gram_bpt() {
+  return GramShape<MP>::NT <= NTH ? 1 : (GramShape<MP>::NT + NTH - 1) / NTH;
+}
+
+// BPT: blocks per thread; the kernel's blocks must have at least ceil(NT / BPT) threads.
+template <typename T, int MP, int BPT = gram_bpt<MP, 128>()>
 struct GramAcc;
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -35,106 +44,147 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-template <int MP>
-struct GramAcc<float, MP> {
+// (i, j) of the t-th upper-triangular 4x4 block
+template <int NB>
+__device__ __forceinline__ void gram_block_ij(int t, int& bi, int& bj) {
+  int tt = t, r = 0;
+  while (tt >= NB - r) {
+    tt -= NB - r;
+    ++r;
+  }
+  bi = r;
+  bj = r + tt;
+}
+
+template <int MP, int BPT>
+struct GramAcc<float, MP, BPT> {
   using S = GramShape<MP>;
-  int t, ph, nph, bi, bj;
+  int t, ph, nph, bi[BPT], bj[BPT], nb;
   bool active;
-  float hi[16], lo[16];
+  float hi[BPT][16], lo[BPT][16];
 
   __device__ void init() {
-    nph = blockDim.x / S::NT;
-    t = threadIdx.x % S::NT;
-    ph = threadIdx.x / S::NT;
-    active = ph < nph;
-    int tt = t, r = 0;
-    while (tt >= S::NB - r) {
-      tt -= S::NB - r;
-      ++r;
+    if (BPT == 1 || S::NT <= (int)blockDim.x) {  // BPT == 1: NT fits the block
+      nph = blockDim.x / S::NT;
+      t = threadIdx.x % S::NT;
+      ph = threadIdx.x / S::NT;
+      active = ph < nph;
+      nb = 1;
+    } else {  // more blocks than threads: blocks t, t + blockDim, ...; all rows
+      nph = 1;
+      t = threadIdx.x;
+      ph = 0;
+      active = true;
+      nb = 0;
+      for (int k = 0; k < BPT; ++k) nb += (t + k * (int)blockDim.x < S::NT) ? 1 : 0;
     }
-    bi = r;
-    bj = r + tt;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) hi[e] = lo[e] = 0.f;
+    for (int k = 0; k < BPT; ++k) {
+      const int b = t + k * (int)blockDim.x;
+      gram_block_ij<S::NB>(b < S::NT ? b : 0, bi[k], bj[k]);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) hi[k][e] = lo[k][e] = 0.f;
+    }
   }
 
   __device__ void tile(const float* sX, const float* sY, int rows) {
     if (!active) return;
-    float acc[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) acc[e] = 0.f;
-    for (int r = ph; r < rows; r += nph) {
-      float4 x = *reinterpret_cast<const float4*>(sX + r * MP + 4 * bi);
-      float4 y = *reinterpret_cast<const float4*>(sY + r * MP + 4 * bj);
-      float xa[4] = {x.x, x.y, x.z, x.w};
-      float yb[4] = {y.x, y.y, y.z, y.w};
+    for (int k = 0; k < BPT; ++k) {
+      if (BPT > 1 && k >= nb) break;
+      float acc[16];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int e = 0; e < 16; ++e) acc[e] = 0.f;
+      for (int r = ph; r < rows; r += nph) {
+        float4 x = *reinterpret_cast<const float4*>(sX + r * MP + 4 * bi[k]);
+        float4 y = *reinterpret_cast<const float4*>(sY + r * MP + 4 * bj[k]);
+        float xa[4] = {x.x, x.y, x.z, x.w};
+        float yb[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a * 4 + b] = fmaf(xa[a], yb[b], acc[a * 4 + b]);
-    }
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      float s, err;
-      two_sum(hi[e], acc[e], s, err);
-      hi[e] = s;
-      lo[e] = __fadd_rn(lo[e], err);
+          for (int b = 0; b < 4; ++b) acc[a * 4 + b] = fmaf(xa[a], yb[b], acc[a * 4 + b]);
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        float s, err;
+        two_sum(hi[k][e], acc[e], s, err);
+        hi[k][e] = s;
+        lo[k][e] = __fadd_rn(lo[k][e], err);
+      }
     }
   }
 
-  __device__ double value(int e) const { return (double)hi[e] + (double)lo[e]; }
+  __device__ double value(int k, int e) const { return (double)hi[k][e] + (double)lo[k][e]; }
 };
 
-template <int MP>
-struct GramAcc<double, MP> {
+template <int MP, int BPT>
+struct GramAcc<double, MP, BPT> {
   using S = GramShape<MP>;
-  int t, ph, nph, bi, bj;
+  int t, ph, nph, bi[BPT], bj[BPT], nb;
   bool active;
-  double hi[16];
+  double hi[BPT][16];
 
   __device__ void init() {
-    nph = blockDim.x / S::NT;
-    t = threadIdx.x % S::NT;
-    ph = threadIdx.x / S::NT;
-    active = ph < nph;
-    int tt = t, r = 0;
-    while (tt >= S::NB - r) {
-      tt -= S::NB - r;
-      ++r;
+    if (BPT == 1 || S::NT <= (int)blockDim.x) {  // BPT == 1: NT fits the block
+      nph = blockDim.x / S::NT;
+      t = threadIdx.x % S::NT;
+      ph = threadIdx.x / S::NT;
+      active = ph < nph;
+      nb = 1;
+    } else {
+      nph = 1;
+      t = threadIdx.x;
+      ph = 0;
+      active = true;
+      nb = 0;
+      for (int k = 0; k < BPT; ++k) nb += (t + k * (int)blockDim.x < S::NT) ? 1 : 0;
     }
-    bi = r;
-    bj = r + tt;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) hi[e] = 0.0;
+    for (int k = 0; k < BPT; ++k) {
+      const int b = t + k * (int)blockDim.x;
+      gram_block_ij<S::NB>(b < S::NT ? b : 0, bi[k], bj[k]);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) hi[k][e] = 0.0;
+    }
   }
 
   __device__ void tile(const double* sX, const double* sY, int rows) {
     if (!active) return;
-    for (int r = ph; r < rows; r += nph) {
-      const double2* px = reinterpret_cast<const double2*>(sX + r * MP + 4 * bi);
-      const double2* py = reinterpret_cast<const double2*>(sY + r * MP + 4 * bj);
-      double2 x01 = px[0], x23 = px[1], y01 = py[0], y23 = py[1];
-      double xa[4] = {x01.x, x01.y, x23.x, x23.y};
-      double yb[4] = {y01.x, y01.y, y23.x, y23.y};
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < BPT; ++k) {
+      if (BPT > 1 && k >= nb) break;
+      for (int r = ph; r < rows; r += nph) {
+        const double2* px = reinterpret_cast<const double2*>(sX + r * MP + 4 * bi[k]);
+        const double2* py = reinterpret_cast<const double2*>(sY + r * MP + 4 * bj[k]);
+        double2 x01 = px[0], x23 = px[1], y01 = py[0], y23 = py[1];
+        double xa[4] = {x01.x, x01.y, x23.x, x23.y};
+        double yb[4] = {y01.x, y01.y, y23.x, y23.y};
 #pragma unroll
-        for (int b = 0; b < 4; ++b) hi[a * 4 + b] = fma(xa[a], yb[b], hi[a * 4 + b]);
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) hi[k][a * 4 + b] = fma(xa[a], yb[b], hi[k][a * 4 + b]);
+      }
     }
   }
 
-  __device__ double value(int e) const { return hi[e]; }
+  __device__ double value(int k, int e) const { return hi[k][e]; }
 };
 
 // Combine the phases of one CTA (fixed order) and write the CTA partial:
 // parts[e * nparts + cta] for e in [0, NE). sred needs nph * NT * 16 doubles and may
 // alias the tile buffers (the caller synchronises before calling).
-template <typename T, int MP>
-__device__ void gram_finish(const GramAcc<T, MP>& g, double* sred, double* parts, int nparts, int cta) {
+template <typename T, int MP, int BPT>
+__device__ void gram_finish(const GramAcc<T, MP, BPT>& g, double* sred, double* parts, int nparts, int cta) {
   using S = GramShape<MP>;
   if (g.active) {
 #pragma unroll
-    for (int e = 0; e < 16; ++e) sred[(g.ph * S::NT + g.t) * 16 + e] = g.value(e);
+    for (int k = 0; k < BPT; ++k) {
+      if (BPT > 1 && k >= g.nb) break;
+      const int b = g.t + k * (int)blockDim.x;  // block index (one block per thread when nph > 0)
+#pragma unroll
+      for (int e = 0; e < 16; ++e) sred[(g.ph * S::NT + b) * 16 + e] = g.value(k, e);
+    }
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < S::NE; idx += blockDim.x) {
@@ -215,12 +265,17 @@ __device__ __forceinline__ void st4(double* p, const double* v) {
   reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
 
+// Phases of the Gram accumulation in a block of `threads` (1 when blocks outnumber threads).
+template <int MP>
+__host__ __device__ constexpr int gram_phases(int threads) {
+  return threads / GramShape<MP>::NT > 0 ? threads / GramShape<MP>::NT : 1;
+}
+
 // Shared bytes a Gram-fused kernel needs: two tiles of TM rows, or the phase buffer.
 template <typename T, int MP>
 inline size_t gram_smem_bytes(int tm, int threads) {
   size_t tiles = 2 * (size_t)tm * MP * sizeof(T);
-  int nph = threads / GramShape<MP>::NT;
-  size_t red = (size_t)nph * GramShape<MP>::NE * sizeof(double);
+  size_t red = (size_t)gram_phases<MP>(threads) * GramShape<MP>::NE * sizeof(double);
   return tiles > red ? tiles : red;
 }
 

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(NTH) k_bop(const BSys* __restrict__ sys, const
   T* Y = static_cast<T*>(S.Y);
   const int64_t d = S.d, lda = S.lda, ld = S.ld;
   const T mu = (T)S.mu;
-  GramAcc<T, MP> g;
+  GramAcc<T, MP, gram_bpt<MP, NTH>()> g;
   g.init();
   const int r = threadIdx.x / CG, cg = threadIdx.x % CG;
   const int nq = (S.m + 3) >> 2;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(TM) k_bupd_r(const BSys* __restrict__ sys, con
   T* R = static_cast<T*>(S.Q);  // W = Q - Y Gi overwrites Q
   const int64_t d = S.d, ld = S.ld;
   const int m = S.m;
-  GramAcc<T, MP> g;
+  GramAcc<T, MP, gram_bpt<MP, TM>()> g;
   g.init();
   const int64_t ntiles = (d + TM - 1) / TM;
   for (int64_t tile = j; tile < ntiles; tile += S.ncta) {
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(TM) k_bgram_r(const BSys* __restrict__ sys, co
   T* sX = reinterpret_cast<T*>(smem_raw);
   const T* R = static_cast<const T*>(S.Q);
   const int64_t d = S.d, ld = S.ld;
-  GramAcc<T, MP> g;
+  GramAcc<T, MP, gram_bpt<MP, TM>()> g;
   g.init();
   const int64_t ntiles = (d + TM - 1) / TM;
   for (int64_t tile = j; tile < ntiles; tile += S.ncta) {
@@ -184,6 +184,11 @@ __global__ void __launch_bounds__(TM) k_bgram_r(const BSys* __restrict__ sys, co
 // ---------------------------------------------------------------- direction update
 // x += P xc; unless the inner solve stopped, Q = W T^{-1} and P = Q + P T^T (P = Q on
 // the start call); the row loop is update_pq_rows.
+template <typename T, int MP>
+constexpr size_t bupd_p_smem() {
+  return MP > 36 ? 2 * (size_t)MP * MP * sizeof(T) : 0;
+}
+
 template <typename T, int MP, int NTH>
 __global__ void __launch_bounds__(NTH) k_bupd_p(const BSys* __restrict__ sys, const int* __restrict__ cta_sys) {
   const BSys S = sys[cta_sys[blockIdx.x]];
@@ -192,9 +197,15 @@ __global__ void __launch_bounds__(NTH) k_bupd_p(const BSys* __restrict__ sys, co
   if (!do_x && !upd) return;
   const bool first = S.st->first;
   const int j = blockIdx.x - S.cta0;
-  __shared__ __align__(16) T sTi[MP * MP];
-  __shared__ __align__(16) T sTT[MP * MP];
+  // above width 36 the two tables are in dynamic shared memory (two FP64 68 x 68
+  // tables exceed the 48 KB of static shared memory)
+  constexpr bool kDyn = MP > 36;
+  __shared__ __align__(16) T sTi_s[kDyn ? 1 : MP * MP];
+  __shared__ __align__(16) T sTT_s[kDyn ? 1 : MP * MP];
   __shared__ __align__(16) T sxc[MP];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sTi = kDyn ? reinterpret_cast<T*>(smem_raw) : sTi_s;
+  T* sTT = kDyn ? reinterpret_cast<T*>(smem_raw) + MP * MP : sTT_s;
   const T* ti = static_cast<const T*>(S.ti_t);
   const T* tt = static_cast<const T*>(S.t_t);
   const T* xc = static_cast<const T*>(S.xc_t);
@@ -276,12 +287,19 @@ __device__ void apply_factor(const SmallShared& sh, int m, int nc, double* Z, bo
 // mode 1 (beta): S = W^T W (reduced from Sp) = T^T T; T^+ and T^T (row-major) for the
 // direction update, c <- T c and the stopping decision on ||c||. The start of an inner solve is a
 // mode-1 call on S = Q^T Q with c = e_1.
+// Zs (MP x (MP + 1)) and cn (MP) are in dynamic shared memory (bsmall_smem bytes).
+template <int MP>
+constexpr size_t bsmall_smem() {
+  return (size_t)(MP * (MP + 1) + MP) * sizeof(double);
+}
+
 template <typename T, int MP>
 __global__ void __launch_bounds__(kBSmall) k_bsmall(BSys* __restrict__ sys, int mode, double rank_tol) {
   BSys& S = sys[blockIdx.x];
   __shared__ SmallShared sh;
-  __shared__ double Zs[MP * (MP + 1)];
-  __shared__ double cn[MP];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Zs = reinterpret_cast<double*>(smem_raw);
+  double* cn = Zs + MP * (MP + 1);
   const int m = S.m;
   DevState* st = S.st;
   if (st->done_a | st->done_b) {
@@ -356,6 +374,9 @@ __global__ void __launch_bounds__(kBSmall) k_bsmall(BSys* __restrict__ sys, int 
     if (conv || st->loads >= st->max_loads) {
       st->done_b = 1;
       st->status = conv ? ST_CONVERGED : ST_LOADCAP;
+    } else if (!(res <= kDivergedRes)) {
+      st->done_b = 1;
+      st->status = ST_BREAKDOWN;
     }
   }
 }
@@ -454,15 +475,27 @@ template <typename T, int MP>
 size_t bop_smem() {
   constexpr int TMD = 16, KC = 64, NTH = 128;
   size_t main = (size_t)(TMD * (KC + 1) + KC * MP + 2 * TMD * MP) * sizeof(T);
-  int nph = NTH / GramShape<MP>::NT;
-  size_t red = (size_t)nph * GramShape<MP>::NE * sizeof(double);
+  size_t red = (size_t)gram_phases<MP>(NTH) * GramShape<MP>::NE * sizeof(double);
   return main > red ? main : red;
+}
+
+// Dynamic shared memory limits of the small solve and the direction update (the small
+// solve's static and dynamic parts together exceed 48 KB).
+template <typename T, int MP>
+cudaError_t small_attrs() {
+  cudaError_t e =
+      cudaFuncSetAttribute(k_bsmall<T, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmall_smem<MP>());
+  if (e == cudaSuccess && bupd_p_smem<T, MP>())
+    e = cudaFuncSetAttribute(k_bupd_p<T, MP, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bupd_p_smem<T, MP>());
+  return e;
 }
 
 template <typename T, typename VA, int MP>
 cudaError_t step_impl(BSys* sys, int nsys, const int* cta_sys, int ncta, double rank_tol, const BatchTc* tc,
                       cudaStream_t st) {
   cudaError_t e;
+  if ((e = small_attrs<T, MP>()) != cudaSuccess) return e;
   if (tc) {
     if ((e = launch_batch_dense_tc(MP, sys, cta_sys, ncta, *tc, st)) != cudaSuccess) return e;
   } else {
@@ -472,7 +505,7 @@ cudaError_t step_impl(BSys* sys, int nsys, const int* cta_sys, int ncta, double 
     k<<<ncta, 128, sm, st>>>(sys, cta_sys);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  k_bsmall<T, MP><<<nsys, kBSmall, 0, st>>>(sys, 0, rank_tol);
+  k_bsmall<T, MP><<<nsys, kBSmall, bsmall_smem<MP>(), st>>>(sys, 0, rank_tol);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {
     auto k = k_bupd_r<T, MP, 128>;
@@ -481,9 +514,9 @@ cudaError_t step_impl(BSys* sys, int nsys, const int* cta_sys, int ncta, double 
     k<<<ncta, 128, sm, st>>>(sys, cta_sys);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  k_bsmall<T, MP><<<nsys, kBSmall, 0, st>>>(sys, 1, rank_tol);
+  k_bsmall<T, MP><<<nsys, kBSmall, bsmall_smem<MP>(), st>>>(sys, 1, rank_tol);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_bupd_p<T, MP, 128><<<ncta, 128, 0, st>>>(sys, cta_sys);
+  k_bupd_p<T, MP, 128><<<ncta, 128, bupd_p_smem<T, MP>(), st>>>(sys, cta_sys);
   return cudaGetLastError();
 }
 
@@ -491,6 +524,7 @@ template <typename T, int MP>
 cudaError_t start_impl(BSys* sys, int nsys, const int* cta_sys, int ncta, uint64_t seed, double rank_tol,
                        cudaStream_t st) {
   cudaError_t e;
+  if ((e = small_attrs<T, MP>()) != cudaSuccess) return e;
   k_bstart<T><<<ncta, 128, 0, st>>>(sys, cta_sys, seed);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   auto k = k_bgram_r<T, MP, 128>;
@@ -498,9 +532,9 @@ cudaError_t start_impl(BSys* sys, int nsys, const int* cta_sys, int ncta, uint64
   if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess) return e;
   k<<<ncta, 128, sm, st>>>(sys, cta_sys);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_bsmall<T, MP><<<nsys, kBSmall, 0, st>>>(sys, 1, rank_tol);
+  k_bsmall<T, MP><<<nsys, kBSmall, bsmall_smem<MP>(), st>>>(sys, 1, rank_tol);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_bupd_p<T, MP, 128><<<ncta, 128, 0, st>>>(sys, cta_sys);
+  k_bupd_p<T, MP, 128><<<ncta, 128, bupd_p_smem<T, MP>(), st>>>(sys, cta_sys);
   return cudaGetLastError();
 }
 
@@ -521,6 +555,7 @@ cudaError_t launch_batch_step(int is_f64, int vals_f64, int mp, BSys* sys, int n
     BK_B(16)
     BK_B(24)
     BK_B(36)
+    BK_B(68)
     default: return cudaErrorInvalidValue;
   }
 #undef BK_B
@@ -538,6 +573,7 @@ cudaError_t launch_batch_start(int is_f64, int mp, BSys* sys, int nsys, const in
     BK_B(16)
     BK_B(24)
     BK_B(36)
+    BK_B(68)
     default: return cudaErrorInvalidValue;
   }
 #undef BK_B

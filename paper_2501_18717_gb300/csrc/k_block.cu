@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(TM) k_gram(int64_t d, const T* __restrict__ X,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sX = reinterpret_cast<T*>(smem_raw);
   T* sY = sX + TM * MP;
-  GramAcc<T, MP> g;
+  GramAcc<T, MP, gram_bpt<MP, TM>()> g;
   g.init();
   int64_t ntiles = (d + TM - 1) / TM;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -249,6 +249,9 @@ __global__ void k_small_beta(int m, int mp, const double* S, double* cvec, T* ti
     if (conv || state->loads >= state->max_loads) {
       state->done_b = 1;
       state->status = conv ? ST_CONVERGED : ST_LOADCAP;
+    } else if (!(res <= kDivergedRes)) {
+      state->done_b = 1;
+      state->status = ST_BREAKDOWN;
     }
   }
 }
@@ -277,10 +280,11 @@ __global__ void k_chol_solve(int m, const double* G, const double* S, double* X,
 // columns of column group cg. The Y tile is staged in shared memory column by column,
 // so each k costs four row values and CPT / 4 broadcast 16-byte alpha chunks for 4 CPT
 // FMAs (at width 36: 7 shared loads per 48 FMAs; one row per thread needed 9 per 36,
-// which left the kernel bound by the shared-memory pipe).
+// which left the kernel bound by the shared-memory pipe). Width 68 (17 chunks of 4)
+// takes 17 column groups of 4 columns (544 threads).
 template <int MP>
 struct UpdRShape {
-  static constexpr int CG = (MP % 12 == 0) ? MP / 12 : ((MP % 8 == 0) ? MP / 8 : 1);
+  static constexpr int CG = (MP % 12 == 0) ? MP / 12 : ((MP % 8 == 0) ? MP / 8 : MP / 4);
   static constexpr int CPT = MP / CG;
   static constexpr int TH = 32 * CG;
   static constexpr int TM = 128;
@@ -292,7 +296,7 @@ struct UpdRSmem {
   static constexpr size_t A_B = ((size_t)MP * MP * sizeof(T) + 15) / 16 * 16;
   static constexpr size_t Y_B = ((size_t)MP * LDY * sizeof(T) + 15) / 16 * 16;
   static constexpr size_t X_B = (size_t)UpdRShape<MP>::TM * MP * sizeof(T);
-  static constexpr size_t RED_B = (size_t)(UpdRShape<MP>::TH / GramShape<MP>::NT) * GramShape<MP>::NE * 8;
+  static constexpr size_t RED_B = (size_t)gram_phases<MP>(UpdRShape<MP>::TH) * GramShape<MP>::NE * 8;
   static constexpr size_t TOTAL = A_B + (Y_B + X_B > RED_B ? Y_B + X_B : RED_B);
 };
 
@@ -310,7 +314,7 @@ __global__ void __launch_bounds__(UpdRShape<MP>::TH)
   T* sX = reinterpret_cast<T*>(smem_raw + SM::A_B + SM::Y_B);  // TM x MP: new R rows
   for (int idx = threadIdx.x; idx < MP * MP; idx += blockDim.x) sA[idx] = alpha_t[idx];
   const int rg = threadIdx.x & 31, cg = threadIdx.x >> 5, c0 = cg * CPT;
-  GramAcc<T, MP> g;
+  GramAcc<T, MP, gram_bpt<MP, U::TH>()> g;
   g.init();
   __syncthreads();
   const int64_t ntiles = (d + TM - 1) / TM;
@@ -396,9 +400,15 @@ __global__ void __launch_bounds__(kUpdThreads, MP < 36 ? (sizeof(T) == 4 ? 3 : 2
   const bool upd = !(state->done_a | state->done_b);
   if (!do_x && !upd) return;
   const bool first = state->first;
-  __shared__ __align__(16) T sTi[MP * MP];
-  __shared__ __align__(16) T sTT[MP * MP];
+  // above width 36 the two tables are in dynamic shared memory (two FP64 68 x 68
+  // tables exceed the 48 KB of static shared memory)
+  constexpr bool kDyn = MP > 36;
+  __shared__ __align__(16) T sTi_s[kDyn ? 1 : MP * MP];
+  __shared__ __align__(16) T sTT_s[kDyn ? 1 : MP * MP];
   __shared__ __align__(16) T sxc[MP];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sTi = kDyn ? reinterpret_cast<T*>(smem_raw) : sTi_s;
+  T* sTT = kDyn ? reinterpret_cast<T*>(smem_raw) + MP * MP : sTT_s;
   for (int idx = threadIdx.x; idx < MP * MP; idx += blockDim.x) {
     sTi[idx] = ti_t[idx];
     sTT[idx] = first ? (T)0 : t_t[idx];
@@ -448,6 +458,11 @@ __global__ void k_init_state(DevState* s, int max_loads, double tol_abs, double*
 __global__ void k_axpy(int64_t d, double a, const double* y, double* x) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = fma(a, y[i], x[i]);
+}
+
+__global__ void k_axpy_out(int64_t d, double a, const double* y, const double* x, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = fma(a, y[i], x[i]);
 }
 
 __global__ void k_to_f32(int64_t n, const double* in, float* out) {
@@ -527,7 +542,12 @@ template <typename T, int MP>
 cudaError_t update_p_impl(int64_t d, int m, void* Q, void* P, int64_t ld, const void* xc_t, const void* ti_t,
                           const void* t_t, double* x, const DevState* state, cudaStream_t st, int device) {
   int grid = capped_grid(d, kUpdThreads, sm_count(device) * (sizeof(T) == 4 ? 4 : 2) * 4);
-  k_update_p<T, MP><<<grid, kUpdThreads, 0, st>>>(d, m, (T*)Q, (T*)P, ld, (const T*)xc_t, (const T*)ti_t,
+  const size_t smem = MP > 36 ? 2 * (size_t)MP * MP * sizeof(T) : 0;
+  if (smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_update_p<T, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_update_p<T, MP><<<grid, kUpdThreads, smem, st>>>(d, m, (T*)Q, (T*)P, ld, (const T*)xc_t, (const T*)ti_t,
                                                   (const T*)t_t, x, state);
   return cudaGetLastError();
 }
@@ -539,6 +559,7 @@ cudaError_t update_p_impl(int64_t d, int m, void* Q, void* P, int64_t ld, const 
     case 16: return F<16>(__VA_ARGS__);             \
     case 24: return F<24>(__VA_ARGS__);             \
     case 36: return F<36>(__VA_ARGS__);             \
+    case 68: return F<68>(__VA_ARGS__);             \
     default: return cudaErrorInvalidValue;          \
   }
 
@@ -676,6 +697,11 @@ cudaError_t launch_init_state(DevState* state, int max_loads, double tol_abs, do
 
 cudaError_t launch_axpy(int64_t d, double a, const double* y, double* x, cudaStream_t st) {
   k_axpy<<<capped_grid(d, 256, 152 * 8), 256, 0, st>>>(d, a, y, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_out(int64_t d, double a, const double* y, const double* x, double* out, cudaStream_t st) {
+  k_axpy_out<<<capped_grid(d, 256, 152 * 8), 256, 0, st>>>(d, a, y, x, out);
   return cudaGetLastError();
 }
 

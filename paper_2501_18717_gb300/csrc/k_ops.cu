@@ -35,7 +35,9 @@ int sm_count_ops(int device) {
 template <int MP>
 __host__ __device__ constexpr int csr_group() { return (MP / 4) % 3 == 0 ? 3 : 2; }
 template <typename T, int MP>
-__host__ __device__ constexpr int csr_blocks() { return sizeof(T) == 4 ? 4 : 2; }
+__host__ __device__ constexpr int csr_blocks() {
+  return MP > 36 ? (sizeof(T) == 4 ? 2 : 1) : (sizeof(T) == 4 ? 4 : 2);
+}
 
 template <typename T, int MP, int TM, int KMAX>
 __global__ void __launch_bounds__(TM, (csr_blocks<T, MP>()))
@@ -48,7 +50,7 @@ __global__ void __launch_bounds__(TM, (csr_blocks<T, MP>()))
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sX = reinterpret_cast<T*>(smem_raw);
   T* sY = sX + TM * MP;
-  GramAcc<T, MP> g;
+  GramAcc<T, MP, gram_bpt<MP, TM>()> g;
   g.init();
   const int t = threadIdx.x;
   const int nq = (m + 3) >> 2;
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(NTH) k_dense_gram(int64_t d, const T* __restri
   T* sP = sA + TMD * (KC + 1);             // KC x MP
   T* sX = sP + KC * MP;                    // TMD x MP tiles for the Gram
   T* sY = sX + TMD * MP;
-  GramAcc<T, MP> g;
+  GramAcc<T, MP, gram_bpt<MP, NTH>()> g;
   g.init();
   int r = threadIdx.x / CG, cg = threadIdx.x % CG;
   const int nq = (m + 3) >> 2;  // panels held in memory
@@ -287,8 +289,7 @@ struct DenseCfg {
   static constexpr int TMD = 16, KC = 64, NTH = 128;
   static size_t smem() {
     size_t main = (size_t)(TMD * (KC + 1) + KC * MP + 2 * TMD * MP) * sizeof(T);
-    int nph = NTH / GramShape<MP>::NT;
-    size_t red = (size_t)nph * GramShape<MP>::NE * sizeof(double);
+    size_t red = (size_t)gram_phases<MP>(NTH) * GramShape<MP>::NE * sizeof(double);
     return main > red ? main : red;
   }
 };
@@ -312,6 +313,7 @@ cudaError_t dense_impl(int64_t d, const void* A, int64_t lda, double mu, const v
     case 16: return F<16>(__VA_ARGS__);    \
     case 24: return F<24>(__VA_ARGS__);    \
     case 36: return F<36>(__VA_ARGS__);    \
+    case 68: return F<68>(__VA_ARGS__);    \
     default: return cudaErrorInvalidValue; \
   }
 
@@ -341,7 +343,8 @@ cudaError_t dense_f(int64_t d, const void* A, int64_t lda, double mu, const void
 int csr_spmm_gram_grid(int is_f64, int mp, int64_t d, int device) {
   int tm = 128;
   int64_t ntiles = (d + tm - 1) / tm;
-  int cap = sm_count_ops(device) * (is_f64 ? 2 : 4);  // resident CTAs per SM (launch bounds)
+  // resident CTAs per SM (the launch bounds of csr_blocks)
+  int cap = sm_count_ops(device) * (mp > 36 ? (is_f64 ? 1 : 2) : (is_f64 ? 2 : 4));
   if (ntiles < 1) ntiles = 1;
   return (int)(ntiles < cap ? ntiles : cap);
 }

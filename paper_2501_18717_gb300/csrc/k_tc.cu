@@ -536,7 +536,7 @@ cudaError_t tc_make_maps(int mp, int64_t d, const float* A, int64_t lda, const f
 
 bool dense_tc_usable(int64_t d, const void* A, int64_t lda, int mp) {
   if (std::getenv("BK_NO_TC")) return false;
-  if (mp > 36 || d < 1 || d > (int64_t)1 << 31) return false;
+  if (mp > kTcMaxPadded || d < 1 || d > (int64_t)1 << 31) return false;
   if ((reinterpret_cast<uintptr_t>(A) & 15) != 0 || (lda & 3) != 0) return false;  // TMA: 16-byte rows
   return encode_fn() != nullptr;
 }

@@ -39,7 +39,7 @@ def test_gaussian_matches_generator(bk, ctx):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("m", [1, 3, 8, 21, 33])
+@pytest.mark.parametrize("m", [1, 3, 8, 21, 33, 37, 65])
 def test_gram(bk, ctx, dtype, m):
     d = 1000  # several 256/128-row tiles and a ragged tail
     ld = 1024
@@ -62,7 +62,7 @@ def test_gram(bk, ctx, dtype, m):
 
 def test_chol_solve(bk, ctx):
     rng = np.random.default_rng(5)
-    for m in [1, 2, 7, 21, 33, 36, 64]:
+    for m in [1, 2, 7, 21, 33, 36, 64, 65]:
         M = rng.standard_normal((m, m))
         G = M @ M.T + m * np.eye(m)
         S = rng.standard_normal((m, m))
@@ -80,7 +80,7 @@ def _block(d, m, seed, npdt):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("m", [1, 5, 21, 33])
+@pytest.mark.parametrize("m", [1, 5, 21, 33, 40, 65])
 def test_block_apply_csr(bk, ctx, dtype, m):
     n = 11  # d = 1331: ragged against the row tiles
     rp, ci, va, d = W.diffusion_csr(W.BASE_SEED + 50, n)
@@ -108,7 +108,7 @@ def test_block_apply_csr(bk, ctx, dtype, m):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("m", [1, 9, 21, 33])
+@pytest.mark.parametrize("m", [1, 9, 21, 33, 65])
 def test_block_apply_dense(bk, ctx, dtype, m):
     d = 333
     npdt = np.float64 if dtype == "f64" else np.float32

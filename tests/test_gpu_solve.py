@@ -54,6 +54,37 @@ def test_iterate_parity_dense(bk, ctx):
         assert err < max(1e-11, 100 * sens), (k, err, sens)
 
 
+@pytest.mark.parametrize("inner", ["fp64", "fp32"])
+def test_iterate_parity_width65(bk, ctx, inner):
+    """The widest block (l = 64, m = 65, padded to 68): after k loads the GPU iterate
+    equals the oracle's block-CG recurrence on the same start block, FP64 blocks to the
+    recurrence's rounding sensitivity, FP32 blocks (FP32-stored values) to FP32 level."""
+    d, l, seed = 700, 64, 4321
+    a = W.dense_spd(W.BASE_SEED + 61, W.decay_spectrum(d, 1e2, 1.0))
+    if inner == "fp32":
+        a = a.astype(np.float32)
+    b = W.normals(W.BASE_SEED + 61, W.STREAM_RHS, d)
+    mu = 1e-2
+    B = W.inner_start_block(b, W.omega(seed, d, l))
+    A = bk.dense_operator(torch.from_numpy(a).to(dev()))
+    bt = torch.from_numpy(b).to(dev())
+    Bp = B * (1 + 1e-14 * np.random.default_rng(1).standard_normal(B.shape))
+    for k in [1, 2, 4]:
+        x = torch.zeros(d, dtype=torch.float64, device=dev())
+        info = bk.solve(ctx, A, mu, bt, x, bk.default_opts(tol=1e-14, inner_tol=1e-15, sketch=l, seed=seed,
+                                                            inner=inner, max_loads=k, max_refine=1), check=False)
+        assert info.loads == k
+        a64 = a.astype(np.float64)
+        ref = bcg.block_cg(a64, mu, B[:, 0], B[:, 1:], tol=0.0, max_loads=k)
+        refp = bcg.block_cg(a64, mu, Bp[:, 0], Bp[:, 1:], tol=0.0, max_loads=k)
+        xr = ref["x"] * np.linalg.norm(b)
+        sens = np.linalg.norm(refp["x"] - ref["x"]) / np.linalg.norm(ref["x"])
+        err = np.linalg.norm(x.cpu().numpy() - xr) / np.linalg.norm(xr)
+        # FP32 blocks: unit roundoff 6e-8 amplified like a 1e-14 perturbation is by sens
+        bound = max(1e-11, 100 * sens) if inner == "fp64" else max(1e-5, 100 * sens * 6e-8 / 1e-14)
+        assert err < bound, (k, err, sens)
+
+
 def test_dense_fp64_workload(bk, ctx):
     """The dense FP64 workload (d = 2000, lambda_i = 1e4 i^-2 + 1e-2, mu = 1e-3, l = 20):
     relative residual <= 1e-10 recomputed by the oracle in FP64."""
@@ -73,7 +104,7 @@ def test_dense_fp64_workload(bk, ctx):
 
 
 @pytest.mark.parametrize("inner,tol", [("fp64", 1e-10), ("fp32", 1e-8)])
-@pytest.mark.parametrize("n,l", [(16, 32), (20, 8), (9, 0)])
+@pytest.mark.parametrize("n,l", [(16, 32), (20, 8), (9, 0), (14, 64)])
 def test_csr_solve_small(bk, ctx, inner, tol, n, l):
     rp, ci, va, b = W.diffusion_workload(W.BASE_SEED + 70 + n, n=n)
     mu = 1e-4
@@ -150,8 +181,8 @@ def test_edge_cases(bk, ctx):
     with pytest.raises(bk.BKError) as e:
         bk.solve(ctx, A, -1.0, b, x)
     assert e.value.status == bk.BK_ERR_ARG
-    # blocks wider than the compiled widths (m <= 36) on a system large enough to use them
+    # blocks wider than the compiled widths (m <= 65) on a system large enough to use them
     big = np.diag(np.arange(1.0, 101.0))
     with pytest.raises(bk.BKError) as e:
-        bk.solve(ctx, bk.dense_operator(big), 0.0, np.ones(100), np.zeros(100), bk.default_opts(sketch=40))
+        bk.solve(ctx, bk.dense_operator(big), 0.0, np.ones(100), np.zeros(100), bk.default_opts(sketch=65))
     assert e.value.status == bk.BK_ERR_UNSUPPORTED

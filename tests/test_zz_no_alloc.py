@@ -94,3 +94,5 @@ def test_static_rejects_what_it_cannot_do_without_allocating():
     # the same argument rules as bk_block_apply: a non-finite shift is refused
     assert bk.block_apply_static(A, float("inf"), Pt, Y, G, 9, ld) == bk.BK_ERR_ARG
     assert bk.block_apply_static(A, float("nan"), Pt, Y, G, 9, ld) == bk.BK_ERR_ARG
+    # blocks wider than 36 (the fixed scratch array's limit) are refused before any launch
+    assert bk.block_apply_static(A, 0.0, Pt, Y, G, 40, ld) == bk.BK_ERR_UNSUPPORTED
