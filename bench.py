@@ -417,8 +417,8 @@ def run_batched(args, world, rank, local, dev):
             "config": {"workload": f"batched_{n}_dense_logU500-16000_fp32_outliers1e2-1e5",
                        "sum_d2_bytes_fp32": sum(4.0 * d * d for d in ds), "tol": TOL,
                        "autotune": {"candidates": cands, "table_log2d": table, "seconds": tune_s,
-                                    "note": "a candidate whose block width the kernels are not built for "
-                                            "(64: width 65) is skipped; product = block-product kernel"},
+                                    "note": "every candidate's block width is built (64: width 65, padded 68); "
+                                            "product = block-product kernel"},
                        "l2": "matrices 75 GB, far larger than L2; no flush"},
             "converged": ok, "rel_residual_max": rel, "loads_mean": float(np.mean(loads)),
             "loads_max": int(max(loads)),
