@@ -443,3 +443,47 @@ def test_shrink_one_column_block_is_cg(s):
     for j in [0, 2, 6]:
         ref, _ = spla.cg(a + mu * np.eye(d), b, x0=np.zeros(d), maxiter=s + j, rtol=0.0, atol=0.0)
         assert rel(xs[j], ref) < 1e-10, (s, j)
+
+
+# ---- accurate dense products (oracle/accurate.py) against exact rational arithmetic
+def _exact_rowsum(a_row, x):
+    from fractions import Fraction
+    return float(sum(Fraction(float(a)) * Fraction(float(v)) for a, v in zip(a_row, x)))
+
+
+def test_accurate_split_is_exact_and_short():
+    from oracle import accurate
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(1000) * np.exp2(rng.integers(-300, 300, 1000))
+    h, t = accurate.split_head_tail(x)
+    assert np.array_equal(h + t, x)
+    # the head has at most 26 significant bits: scaled to [2^25, 2^26) it is an integer
+    m, _ = np.frexp(h)
+    assert np.all(m * 2.0 ** 26 == np.round(m * 2.0 ** 26))
+
+
+@pytest.mark.parametrize("case", ["gaussian", "cancelling", "wide_range"])
+def test_accurate_matvec_against_fractions(case):
+    """Rows of 300 FP32 values times FP64 x: within 2e-15 sum |a x| of the exact
+    rational sum; the cancelling case (sum near 0 with large terms) and exponents
+    spread over 2^-60 .. 2^60 are where an ordinary dot product loses digits."""
+    from oracle import accurate
+    rng = np.random.default_rng({"gaussian": 1, "cancelling": 2, "wide_range": 3}[case])
+    d = 300
+    a = rng.standard_normal((6, d)).astype(np.float32)
+    x = rng.standard_normal(d)
+    if case == "cancelling":
+        # x orthogonal to each row up to rounding, in FP64
+        for i in range(6):
+            a64 = a[i].astype(np.float64)
+            x = x - (a64 @ x) / (a64 @ a64) * a64
+    if case == "wide_range":
+        x = x * np.exp2(rng.integers(-60, 60, d))
+        a = (a * np.exp2(rng.integers(-30, 30, (6, d)))).astype(np.float32)
+    A = np.zeros((d, d), dtype=np.float32)
+    A[:6] = a
+    y = accurate.matvec(A, x)[:6]
+    scale = accurate.abs_products(A, x[:, None])[:6, 0]
+    for i in range(6):
+        exact = _exact_rowsum(a[i], x)
+        assert abs(y[i] - exact) <= 2e-15 * scale[i], (i, y[i], exact)
