@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--sample-d", type=int, default=40000)
     ap.add_argument("--sample-m", type=int, default=256)
     ap.add_argument("--sample-loads", type=int, default=16)
-    ap.add_argument("--sample-inner", default="f32x2", choices=["f32x2", "fp32", "fp64"])
+    ap.add_argument("--sample-inner", default="ozaki", choices=["ozaki", "f32x2", "fp32", "fp64"])
     ap.add_argument("--sample-nugget", type=float, default=None)
     ap.add_argument("--sample-operator", default="stored", choices=["stored", "rbf"])
     ap.add_argument("--dense-d", type=int, default=16384)
@@ -96,6 +96,17 @@ def algorithmic_bytes(d, nnz, m):
         "update_r": 3 * blk,                               # read Y, Q; write W (over Q)
         "update_p": 4 * blk + 2 * d * 8,                   # read W, P; write Q, P; x read+write (FP64)
     }
+
+
+def measured_bf16_peak(sustained=True):
+    """Measured dense BF16 TFLOP/s (sustained: for a kernel timed inside a long call)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            j = json.load(fh)
+        k = "bf16_tflops_sustained" if sustained and "bf16_tflops_sustained" in j else "bf16_tflops"
+        return float(j[k]), "measured " + k
+    return (1700.0 if sustained else 1900.0), "fallback"
 
 
 def measured_peaks():
@@ -856,6 +867,20 @@ def run_sample(args, world, rank, local, dev):
         torch.cuda.synchronize(dev)
     isqrt = {"value": m / (e0.elapsed_time(e1) / 1e3), "unit": "samples/s", "ms": e0.elapsed_time(e1),
              "loads": iinfo.loads, "last_change": iinfo.rel_residual, "status": iinfo.status}
+    other = None
+    if args.sample_inner == "ozaki" and not onfly:
+        # the compensated FP32-pair loads on the same problem, for comparison (one profiled
+        # call after the timed ones), and how far its samples are from this mode's
+        call(opts())
+        S_oz = S.clone()
+        oo = bk.default_opts(tol=1e-4, inner="f32x2", check_every=4, max_loads=args.sample_loads, profile=1)
+        oinfo = call(oo)
+        j = bk.KERNEL_CLASSES.index("operator")
+        other = {"inner": "f32x2", "ms_total": oinfo.ms_total, "loads": oinfo.loads,
+                 "value": m / (oinfo.ms_total / 1e3), "unit": "samples/s",
+                 "operator_avg_ms": oinfo.ms_kernel[j] / max(oinfo.launches[j], 1),
+                 "rel_diff_of_samples": float(torch.linalg.norm(S - S_oz) / torch.linalg.norm(S_oz)),
+                 "note": "one call with profiling events (ms_total includes them)"}
     names = bk.KERNEL_CLASSES
     groups = {}
     for k in ("operator", "orth"):
@@ -870,7 +895,12 @@ def run_sample(args, world, rank, local, dev):
     # compensated FP32-pair products issue about 11 FP32 instructions per multiply-add
     # (12 with both operands split, on the fly)
     issue = 12.0 if onfly else (11.0 if args.sample_inner == "f32x2" else 1.0)
+    oz = args.sample_inner == "ozaki" and not onfly
+    # the Ozaki product runs 28 BF16 digit products (digit pairs i + j <= 6 of 7 digits),
+    # each 2 d^2 m flop, per load
+    oz_pairs = 28
     peak_hbm, peak_src = measured_peaks()
+    bf16_peak, bf16_src = measured_bf16_peak(sustained=True)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the FP64 oracle's block-Lanczos (full reorthogonalisation) on the stored K
@@ -901,7 +931,7 @@ def run_sample(args, world, rank, local, dev):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
             "dtype": "f64 blocks, " + ("compensated f32-pair" if args.sample_inner == "f32x2" or onfly
-                                       else args.sample_inner)
+                                       else ("Ozaki-split bf16 tensor-core" if oz else args.sample_inner))
                      + (" products of K formed on the fly in f64" if onfly else " products of the f32-stored K")
                      + ", f64 Gram/band solves", "data": "synthetic",
             "config": {"workload": f"rbf_sample_d{d}_m{m}_ls0.2_nugget{args.sample_nugget:g}_"
@@ -913,17 +943,25 @@ def run_sample(args, world, rank, local, dev):
                               else f"K {4.0 * d * d / 1e9:.1f} GB, larger than L2; no flush")},
             "loads": [i.loads for i in infos], "last_change": [i.rel_residual for i in infos],
             "status": [i.status for i in infos], "groups": groups,
-            "roofline": {"bound": "alu", "kernel": ("on-the-fly kernel load K P (k_rbf, f32 pairs)" if onfly
-                                                    else f"dense load K P (k_tsm nn, {args.sample_inner})"),
-                         "achieved": op_tf, "peak": peak_tf / issue, "unit": "TFLOP/s",
-                         "frac": (op_tf * issue / peak_tf) if op_tf else None,
-                         "traffic": None,
-                         "peak_source": f"FP32 pipe: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz"
-                                        f" / {issue:.0f} instructions per multiply-add",
-                         "hbm_equiv": {"achieved_gbs": 4.0 * d * d / (groups['operator']['avg_ms'] / 1e3) / 1e9
-                                       if groups["operator"]["calls"] else None, "peak": peak_hbm,
-                                       "peak_source": peak_src}},
-            "isqrt": isqrt, "clocks": clocks, "cpu_baseline": cpu,
+            "roofline": ({"bound": "tensor", "kernel": "dense load K P (k_ozgemm, Ozaki split: 28 BF16 digit "
+                                                       "products with FP32 accumulation)",
+                          "achieved": op_tf * oz_pairs if op_tf else None, "peak": bf16_peak, "unit": "TFLOP/s",
+                          "frac": (op_tf * oz_pairs / bf16_peak) if op_tf else None, "traffic": None,
+                          "peak_source": bf16_src, "fp64_accurate_tflops": op_tf,
+                          "hbm_equiv": {"achieved_gbs": 4.0 * d * d / (groups['operator']['avg_ms'] / 1e3) / 1e9
+                                        if groups["operator"]["calls"] else None, "peak": peak_hbm,
+                                        "peak_source": peak_src}} if oz else
+                         {"bound": "alu", "kernel": ("on-the-fly kernel load K P (k_rbf, f32 pairs)" if onfly
+                                                     else f"dense load K P (k_tsm nn, {args.sample_inner})"),
+                          "achieved": op_tf, "peak": peak_tf / issue, "unit": "TFLOP/s",
+                          "frac": (op_tf * issue / peak_tf) if op_tf else None,
+                          "traffic": None,
+                          "peak_source": f"FP32 pipe: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz"
+                                         f" / {issue:.0f} instructions per multiply-add",
+                          "hbm_equiv": {"achieved_gbs": 4.0 * d * d / (groups['operator']['avg_ms'] / 1e3) / 1e9
+                                        if groups["operator"]["calls"] else None, "peak": peak_hbm,
+                                        "peak_source": peak_src}}),
+            "isqrt": isqrt, "other_inner": other, "clocks": clocks, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -73,8 +73,20 @@ typedef enum { BK_F64 = 0, BK_F32 = 1 } bk_dtype;
  *   product is the sum of the three head/tail products, about 2^-16 of
  *   sum |z_ik x_k|. The refinement residual stays FP64-accurate (compensated
  *   products of the stored Z). bk_ridge_path only, with at most 128 block columns;
- *   other entry points and operator kinds return BK_ERR_UNSUPPORTED. */
-typedef enum { BK_PREC_FP64 = 0, BK_PREC_FP32 = 1, BK_PREC_F32X2 = 2, BK_PREC_BF16 = 3 } bk_prec;
+ *   other entry points and operator kinds return BK_ERR_UNSUPPORTED.
+ *   BK_PREC_OZAKI: as BK_PREC_F32X2, except that the block products of a stored dense
+ *   FP32 operator run on the BF16 tensor cores through an error-free splitting (Ozaki,
+ *   Ogita and Oishi, 2012; see bk_apply_ozaki for the digits and the error bound).
+ *   The digits of the operator (7 planes of BF16, 14 d^2 bytes) are made once per
+ *   call. bk_sample and bk_sample_isqrt with a BK_DENSE FP32 operator only; other
+ *   entry points and operators return BK_ERR_UNSUPPORTED. */
+typedef enum {
+  BK_PREC_FP64 = 0,
+  BK_PREC_FP32 = 1,
+  BK_PREC_F32X2 = 2,
+  BK_PREC_BF16 = 3,
+  BK_PREC_OZAKI = 4
+} bk_prec;
 
 /* The matrix A (without the shift mu).
  *   BK_DENSE: vals is rows x cols row-major with leading dimension ld, rows = cols = d.
@@ -401,6 +413,27 @@ bk_status bk_sqrt_quadrature(double lo, double hi, int32_t n, double* z2, double
  * bk_solve / bk_sample. */
 bk_status bk_apply(bk_ctx* ctx, const bk_operator* A, double mu, int32_t L, const double* X, int64_t ldx,
                    double* Y, int64_t ldy);
+
+/* Y = A X + mu X in FP64 for a dense FP32-stored A (BK_DENSE, dtype BK_F32; host or
+ * device arrays as in bk_apply), on the BF16 tensor cores by an error-free splitting
+ * in the manner of Ozaki, Ogita and Oishi (2012), the product the BK_PREC_OZAKI mode
+ * uses for its loads. The paper prescribes no product algorithm; this is a GB300
+ * implementation of its FP64-accurate matrix-load (Sec. 1.2, Sec. 5).
+ * Each row of A and each column of X is cut into blocks of 512 consecutive elements;
+ * a block whose largest magnitude is below 2^e is written as 2^e sum_i a_i 2^-(6+7i)
+ * with 7 integer digits |a_i| <= 64 (exact in BF16), which keeps every value to
+ * 2^-49 of 2^e. The digit products with i + j <= 6 are accumulated per block on the
+ * tensor cores, where every partial sum is an integer below 2^24 and so exact; the
+ * blocks are added in unevaluated FP32 pairs. Error of entry i of Y: at most about
+ * 2^-45 sum_k 2^eA(i,k) 2^eX(k), where 2^eA(i,k) and 2^eX(k) bound the blocks that
+ * a_ik and x_k fall in; this equals 2^-45 sum_k |a_ik x_k| up to the spread of the
+ * magnitudes within a block (a factor 4 when they lie within a factor 2 of its
+ * largest), not for blocks of very uneven magnitudes. The digits of A (7 d^2 BF16 values, 14 d^2 bytes, in the context
+ * workspace) are made at every call; the Lanczos drivers make them once per call.
+ * Y and X have leading dimensions ldy, ldx >= d and L columns (L <= 4096). Returns
+ * BK_ERR_UNSUPPORTED for other operators, BK_TIMEOUT if a pipeline wait gave up. */
+bk_status bk_apply_ozaki(bk_ctx* ctx, const bk_operator* A, double mu, int32_t L, const double* X, int64_t ldx,
+                         double* Y, int64_t ldy);
 
 /* One block product with its Gram matrix (one "matrix-load", Sec. 1.2):
  *   Y = A P + mu P  and  G = P^T Y  (m x m, FP64, row-major).

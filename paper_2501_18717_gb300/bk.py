@@ -24,7 +24,7 @@ BK_OK, BK_ERR_ARG, BK_ERR_CUDA, BK_ERR_OOM, BK_NOT_CONVERGED, BK_BREAKDOWN, BK_S
     BK_ERR_UNSUPPORTED, BK_ERR_TOO_LARGE = range(10)
 BK_DENSE, BK_CSR, BK_GRAM, BK_RBF = 0, 1, 2, 3
 BK_F64, BK_F32 = 0, 1
-BK_PREC_FP64, BK_PREC_FP32, BK_PREC_F32X2, BK_PREC_BF16 = 0, 1, 2, 3
+BK_PREC_FP64, BK_PREC_FP32, BK_PREC_F32X2, BK_PREC_BF16, BK_PREC_OZAKI = 0, 1, 2, 3, 4
 
 EXPORTS = ("bk_default_opts", "bk_create", "bk_destroy", "bk_set_stream", "bk_status_string", "bk_last_error",
            "bk_solve",
@@ -97,6 +97,7 @@ def _load():
         "bk_solve_shrink": (i32, [vp, ctypes.POINTER(Operator), dbl, vp, vp, i32, ctypes.POINTER(Opts),
                                   ctypes.POINTER(Info)]),
         "bk_apply": (i32, [vp, ctypes.POINTER(Operator), dbl, i32, vp, i64, vp, i64]),
+        "bk_apply_ozaki": (i32, [vp, ctypes.POINTER(Operator), dbl, i32, vp, i64, vp, i64]),
         "bk_autotune_save": (i32, [vp, ctypes.c_char_p]),
         "bk_autotune_load": (i32, [vp, ctypes.c_char_p]),
     }
@@ -248,7 +249,8 @@ def default_opts(**kw) -> Opts:
     _lib.bk_default_opts(ctypes.byref(o))
     for k, v in kw.items():
         if k == "inner" and isinstance(v, str):
-            v = {"fp64": BK_PREC_FP64, "fp32": BK_PREC_FP32, "f32x2": BK_PREC_F32X2, "bf16": BK_PREC_BF16}[v]
+            v = {"fp64": BK_PREC_FP64, "fp32": BK_PREC_FP32, "f32x2": BK_PREC_F32X2, "bf16": BK_PREC_BF16,
+                 "ozaki": BK_PREC_OZAKI}[v]
         setattr(o, k, v)
     return o
 
@@ -343,10 +345,12 @@ def solve_shrink(ctx: Context, A: OperatorRef, mu: float, b, x, s_lock: int = 3,
     return info
 
 
-def apply(ctx: Context, A: OperatorRef, mu: float, X, Y, ldx: int | None = None, ldy: int | None = None) -> None:
+def apply(ctx: Context, A: OperatorRef, mu: float, X, Y, ldx: int | None = None, ldy: int | None = None,
+          ozaki: bool = False) -> None:
     """bk_apply: Y = A X + mu X in FP64. X and Y are column-major (a Fortran-ordered
     NumPy array or a transposed contiguous torch tensor) with the operator's d rows
-    first in each column; the leading dimensions default to the column strides."""
+    first in each column; the leading dimensions default to the column strides.
+    ozaki=True calls bk_apply_ozaki (dense FP32 A on the BF16 tensor cores)."""
     def cols(a):
         if len(a.shape) == 1:
             return 1, int(a.shape[0])
@@ -356,9 +360,10 @@ def apply(ctx: Context, A: OperatorRef, mu: float, X, Y, ldx: int | None = None,
     _, sy = cols(Y)
     px, kx = _ptr(X)
     py, ky = _ptr(Y)
-    s = _lib.bk_apply(ctx.handle, ctypes.byref(A.op), float(mu), L, px, int(ldx or sx), py, int(ldy or sy))
+    fn = _lib.bk_apply_ozaki if ozaki else _lib.bk_apply
+    s = fn(ctx.handle, ctypes.byref(A.op), float(mu), L, px, int(ldx or sx), py, int(ldy or sy))
     if s != BK_OK:
-        raise BKError(s, "bk_apply", ctx.last_error())
+        raise BKError(s, "bk_apply_ozaki" if ozaki else "bk_apply", ctx.last_error())
 
 
 def block_apply(ctx: Context, A: OperatorRef, mu: float, P, Y, G, m: int, ld: int, dtype=None) -> None:

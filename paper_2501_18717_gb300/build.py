@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libbk.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["bk_api.cu", "k_ops.cu", "k_block.cu", "k_rng.cu", "bk_static.cu", "k_gemm.cu", "k_krylov.cu",
-           "bk_krylov_api.cu", "k_batch.cu", "bk_batch_api.cu", "k_tc.cu", "k_tsm.cu", "k_pcg.cu", "k_rbf.cu", "k_bf16.cu"]
+           "bk_krylov_api.cu", "k_batch.cu", "bk_batch_api.cu", "k_tc.cu", "k_tsm.cu", "k_pcg.cu", "k_rbf.cu", "k_bf16.cu",
+           "k_ozaki.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

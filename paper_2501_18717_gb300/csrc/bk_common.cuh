@@ -130,6 +130,17 @@ cudaError_t launch_omega(int is_f64, int64_t d, int l, int64_t ld, uint64_t seed
 cudaError_t launch_gaussian(uint64_t seed, uint32_t stream, int64_t n, int64_t offset, double* out,
                             cudaStream_t st);
 
+// FP64-accurate dense products Y = A X (A: d x d FP32 row-major, lda; X, Y: d x N FP64
+// column-major) by an Ozaki split on the BF16 tensor cores (k_ozaki.cu). The digits of
+// A are made once per operator into `abuf` (ozaki_a_bytes); each product splits X
+// into `xbuf` (ozaki_x_bytes). *err is set if a pipeline wait gave up.
+bool ozaki_usable(int64_t d, int N);
+size_t ozaki_a_bytes(int64_t d);
+size_t ozaki_x_bytes(int64_t d, int N);
+cudaError_t launch_ozaki_split_a(int64_t d, const float* A, int64_t lda, void* abuf, int sms, cudaStream_t st);
+cudaError_t launch_ozaki_apply(int64_t d, int N, const void* abuf, const double* X, int64_t ldx, double* Y,
+                               int64_t ldy, void* xbuf, long long wait_cycles, int* err, int sms, cudaStream_t st);
+
 // FP64 residual r = b - (A x + mu x) and per-CTA partials of ||r||^2.
 cudaError_t launch_csr_residual(int vals_f64, int64_t d, const int* rowptr, const int* colidx,
                                 const void* vals, double mu, const double* x, const double* b, double* r,

@@ -135,6 +135,11 @@ struct Lanczos {
   void* bwork = nullptr;
   size_t bwork_bytes = 0;
   int* berr = nullptr;
+  // FP64 blocks of a dense FP32 operator through the Ozaki split on the BF16 tensor
+  // cores (k_ozaki.cu): the operator's digits, the block's workspace, the timeout flag
+  const void* oza = nullptr;
+  void* ozx = nullptr;
+  int* ozerr = nullptr;
   int t = 0;      // blocks in T_t
   int loads = 0;  // operator applications
   double rank_tol = 1e-12;
@@ -191,6 +196,8 @@ struct Lanczos {
     cudaError_t e;
     const int af = op.vals_f64;  // 1: FP64 values, 0: FP32 values
     if (!is64 && af) return cudaErrorInvalidValue;  // FP32 runs use FP32 values
+    if (is64 && oza && op.kind == BK_DENSE && !af)
+      return bk::launch_ozaki_apply(d, nc, oza, (const double*)X, ldx, (double*)Y, ldy, ozx, 0, ozerr, c->sms, st);
     if (!is64 && bz && op.kind == BK_GRAM)
       return bk::launch_bf16_gram_apply(op.nrows, d, nc, bz, (const float*)X, ldx, (float*)Y, ldy, 1.0, 0.0, bwork,
                                         bwork_bytes, 0, berr, c->sms, st);
@@ -742,12 +749,16 @@ bk_status sample_driver(bk_ctx* c, const bk_operator* Kop, double nugget, int32_
   else
     bk_default_opts(&opts);
   if (!(opts.tol > 0.0) || opts.max_loads < 1 || opts.check_every < 1) return BK_ERR_ARG;
-  if (opts.inner != BK_PREC_FP64 && opts.inner != BK_PREC_FP32 && opts.inner != BK_PREC_F32X2)
+  if (opts.inner != BK_PREC_FP64 && opts.inner != BK_PREC_FP32 && opts.inner != BK_PREC_F32X2 &&
+      opts.inner != BK_PREC_OZAKI)
     return BK_ERR_UNSUPPORTED;
   const int is64 = opts.inner != BK_PREC_FP32;
+  const bool oz = opts.inner == BK_PREC_OZAKI;
   const int64_t d = o.d;
   if (m > d) return BK_ERR_ARG;
   if (o.kind == BK_RBF && !is64) return BK_ERR_UNSUPPORTED;
+  // the Ozaki split is built for stored dense FP32 operators
+  if (oz && (o.kind != BK_DENSE || Kop->dtype != BK_F32 || !bk::ozaki_usable(d, m))) return BK_ERR_UNSUPPORTED;
   BK_CK(cudaSetDevice(c->device));
   cudaStream_t st = c->stream;
   cudaEvent_t ev0, ev1;
@@ -766,7 +777,19 @@ bk_status sample_driver(bk_ctx* c, const bk_operator* Kop, double nugget, int32_
   Lanczos lz;
   BK_CK(lz.init(c, o, is64, m, tmax));
   lz.prof = &prof;
-  lz.df = opts.inner == BK_PREC_F32X2;
+  lz.df = opts.inner == BK_PREC_F32X2 || oz;
+  int* ozerr = nullptr;
+  if (oz) {  // digits of K once per call; the loads then run on the tensor cores
+    void *oza = nullptr, *ozx = nullptr;
+    BK_CK(ws_get(c, WS_OZ_A, bk::ozaki_a_bytes(d), &oza));
+    BK_CK(ws_get(c, WS_OZ_X, bk::ozaki_x_bytes(d, m) + 256, &ozx));
+    ozerr = (int*)((char*)ozx + bk::ozaki_x_bytes(d, m));
+    BK_CK(cudaMemsetAsync(ozerr, 0, sizeof(int), st));
+    BK_CK(bk::launch_ozaki_split_a(d, (const float*)o.vals, o.ld, oza, c->sms, st));
+    lz.oza = oza;
+    lz.ozx = ozx;
+    lz.ozerr = ozerr;
+  }
   BK_CK(bk::launch_copy_cols(1, is64, d, m, Bd, d, lz.W, lz.ldq, st));
   BK_CK(lz.start(lz.W));
 
@@ -856,6 +879,16 @@ bk_status sample_driver(bk_ctx* c, const bk_operator* Kop, double nugget, int32_
     if (last) break;
   }
   BK_CK(cudaMemcpyAsync(S, Sd, (size_t)d * m * 8, cudaMemcpyDefault, st));
+  if (ozerr) {  // a tensor-core load whose pipeline wait gave up left an invalid block
+    int herr = 0;
+    BK_CK(cudaMemcpyAsync(c->hparts, ozerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BK_CK(cudaStreamSynchronize(st));
+    std::memcpy(&herr, c->hparts, sizeof(int));
+    if (herr) {
+      std::snprintf(c->last_error, sizeof(c->last_error), "tensor-core pipeline wait timed out");
+      result = BK_TIMEOUT;
+    }
+  }
   BK_CK(cudaEventRecord(ev1, st));
   BK_CK(cudaEventSynchronize(ev1));
   float ms = 0.f;
@@ -1410,6 +1443,48 @@ extern "C" bk_status bk_solve_shrink(bk_ctx* c, const bk_operator* A, double mu,
     info->ms_total = ms;
   }
   return result;
+}
+
+extern "C" bk_status bk_apply_ozaki(bk_ctx* c, const bk_operator* A, double mu, int32_t L, const double* X,
+                                    int64_t ldx, double* Y, int64_t ldy) {
+  if (!c || !X || !Y || L < 1 || !std::isfinite(mu)) return BK_ERR_ARG;
+  err_ctx() = c;
+  c->last_error[0] = 0;
+  LzOp o;
+  bk_status s = check_pcg_operator(A, &o);
+  if (s != BK_OK) return s;
+  const int64_t d = o.d;
+  if (ldx < d || ldy < d) return BK_ERR_ARG;
+  if (A->kind != BK_DENSE || A->dtype != BK_F32 || !bk::ozaki_usable(d, L)) return BK_ERR_UNSUPPORTED;
+  BK_CK(cudaSetDevice(c->device));
+  cudaStream_t st = c->stream;
+  BK_CK(stage_pcg_operator(c, A, &o));
+  const size_t xbytes = ((size_t)(L - 1) * ldx + d) * 8;
+  const double* Xd = nullptr;
+  BK_CK(stage_in(c, WS_TMP_IN, X, xbytes, (const void**)&Xd));
+  double* Yd = Y;
+  const bool direct = is_device_ptr(Y) && ldy == ldx;
+  if (!direct) BK_CK(ws_get(c, WS_TMP_OUT, xbytes, (void**)&Yd));
+  void *oza = nullptr, *ozx = nullptr;
+  BK_CK(ws_get(c, WS_OZ_A, bk::ozaki_a_bytes(d), &oza));
+  BK_CK(ws_get(c, WS_OZ_X, bk::ozaki_x_bytes(d, L) + 256, &ozx));
+  int* err = (int*)((char*)ozx + bk::ozaki_x_bytes(d, L));
+  BK_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  BK_CK(bk::launch_ozaki_split_a(d, (const float*)o.vals, o.ld, oza, c->sms, st));
+  BK_CK(bk::launch_ozaki_apply(d, L, oza, Xd, ldx, Yd, ldx, ozx, 0, err, c->sms, st));
+  if (mu != 0.0)
+    for (int j = 0; j < L; ++j) BK_CK(bk::launch_axpy(d, mu, Xd + (size_t)j * ldx, Yd + (size_t)j * ldx, st));
+  if (!direct)
+    BK_CK(cudaMemcpy2DAsync(Y, (size_t)ldy * 8, Yd, (size_t)ldx * 8, (size_t)d * 8, L, cudaMemcpyDefault, st));
+  int herr = 0;
+  BK_CK(cudaMemcpyAsync(c->hparts, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  BK_CK(cudaStreamSynchronize(st));
+  std::memcpy(&herr, c->hparts, sizeof(int));
+  if (herr) {
+    std::snprintf(c->last_error, sizeof(c->last_error), "tensor-core pipeline wait timed out");
+    return BK_TIMEOUT;
+  }
+  return BK_OK;
 }
 
 extern "C" bk_status bk_apply(bk_ctx* c, const bk_operator* A, double mu, int32_t L, const double* X, int64_t ldx,

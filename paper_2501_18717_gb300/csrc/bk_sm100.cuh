@@ -211,4 +211,10 @@ __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 }  // namespace sm100
+
+// 2D BF16 tensor map (inner extent x, outer extent y, row pitch in elements) read in
+// boxes of 64 x box_y with the 128-byte swizzle; elements outside the tensor read as
+// zero (k_bf16.cu).
+cudaError_t make_map_bf16(CUtensorMap* map, const void* ptr, int64_t x, int64_t y, int64_t pitch, int box_y);
+
 }  // namespace bk

@@ -337,6 +337,8 @@ __global__ void k_xsplit(int64_t d, int N, int NP, const float* __restrict__ X, 
   }
 }
 
+}  // namespace
+
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_bf16_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -366,6 +368,8 @@ cudaError_t make_map_bf16(CUtensorMap* map, const void* ptr, int64_t x, int64_t 
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
+
+namespace {
 
 int64_t up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
