@@ -71,8 +71,12 @@ typedef enum { BK_F64 = 0, BK_F32 = 1 } bk_dtype;
  *   accumulation. Z is split once per call into a BF16 head and tail (a row-major and
  *   a transposed copy, 4 n d bytes each) and the block likewise at every product; a
  *   product is the sum of the three head/tail products, about 2^-16 of
- *   sum |z_ik x_k|. The refinement residual stays FP64-accurate (compensated
- *   products of the stored Z). bk_ridge_path only, with at most 128 block columns;
+ *   sum |z_ik x_k|. The refinement residual stays FP64-accurate: its products with
+ *   the stored Z run on the BF16 tensor cores too, through the error-free digit
+ *   splitting of bk_apply_ozaki (digits of Z and Z^T made once per call, 28 n d
+ *   bytes), under the same accuracy guard as the compensated FP32-pair products
+ *   (and in FP64 GEMMs once a pass stops reducing the residual). bk_ridge_path
+ *   only, with at most 128 block columns;
  *   other entry points and operator kinds return BK_ERR_UNSUPPORTED.
  *   BK_PREC_OZAKI: as BK_PREC_F32X2, except that the block products of a stored dense
  *   FP32 operator run on the BF16 tensor cores through an error-free splitting (Ozaki,
@@ -414,10 +418,11 @@ bk_status bk_sqrt_quadrature(double lo, double hi, int32_t n, double* z2, double
 bk_status bk_apply(bk_ctx* ctx, const bk_operator* A, double mu, int32_t L, const double* X, int64_t ldx,
                    double* Y, int64_t ldy);
 
-/* Y = A X + mu X in FP64 for a dense FP32-stored A (BK_DENSE, dtype BK_F32; host or
- * device arrays as in bk_apply), on the BF16 tensor cores by an error-free splitting
- * in the manner of Ozaki, Ogita and Oishi (2012), the product the BK_PREC_OZAKI mode
- * uses for its loads. The paper prescribes no product algorithm; this is a GB300
+/* Y = A X + mu X in FP64 for a dense FP32-stored A (BK_DENSE, dtype BK_F32) or a Gram-
+ * form A = Z^T Z (BK_GRAM, FP32 or FP64 Z: Y = Z^T (Z X) + mu X, both products split;
+ * host or device arrays as in bk_apply), on the BF16 tensor cores by an error-free
+ * splitting in the manner of Ozaki, Ogita and Oishi (2012): the product of the
+ * BK_PREC_OZAKI loads and of the BK_PREC_BF16 refinement residuals. The paper prescribes no product algorithm; this is a GB300
  * implementation of its FP64-accurate matrix-load (Sec. 1.2, Sec. 5).
  * Each row of A and each column of X is cut into blocks of 512 consecutive elements;
  * a block whose largest magnitude is below 2^e is written as 2^e sum_i a_i 2^-(6+7i)
@@ -428,8 +433,9 @@ bk_status bk_apply(bk_ctx* ctx, const bk_operator* A, double mu, int32_t L, cons
  * 2^-45 sum_k 2^eA(i,k) 2^eX(k), where 2^eA(i,k) and 2^eX(k) bound the blocks that
  * a_ik and x_k fall in; this equals 2^-45 sum_k |a_ik x_k| up to the spread of the
  * magnitudes within a block (a factor 4 when they lie within a factor 2 of its
- * largest), not for blocks of very uneven magnitudes. The digits of A (7 d^2 BF16 values, 14 d^2 bytes, in the context
- * workspace) are made at every call; the Lanczos drivers make them once per call.
+ * largest), not for blocks of very uneven magnitudes. The digits of A (7 d^2 BF16
+ * values, 14 d^2 bytes; for Z, of Z and Z^T, 28 n d bytes; in the context workspace)
+ * are made at every call; the drivers make them once per call.
  * Y and X have leading dimensions ldy, ldx >= d and L columns (L <= 4096). Returns
  * BK_ERR_UNSUPPORTED for other operators, BK_TIMEOUT if a pipeline wait gave up. */
 bk_status bk_apply_ozaki(bk_ctx* ctx, const bk_operator* A, double mu, int32_t L, const double* X, int64_t ldx,

@@ -136,10 +136,21 @@ cudaError_t launch_gaussian(uint64_t seed, uint32_t stream, int64_t n, int64_t o
 // into `xbuf` (ozaki_x_bytes). *err is set if a pipeline wait gave up.
 bool ozaki_usable(int64_t d, int N);
 size_t ozaki_a_bytes(int64_t d);
-size_t ozaki_x_bytes(int64_t d, int N);
+size_t ozaki_x_bytes(int64_t d, int N, int sms);
 cudaError_t launch_ozaki_split_a(int64_t d, const float* A, int64_t lda, void* abuf, int sms, cudaStream_t st);
 cudaError_t launch_ozaki_apply(int64_t d, int N, const void* abuf, const double* X, int64_t ldx, double* Y,
                                int64_t ldy, void* xbuf, long long wait_cycles, int* err, int sms, cudaStream_t st);
+// Gram form A = Z^T Z (Z: n x d row-major, FP32 or FP64, ldz): the digits of Z and of Z^T
+// go into `zbuf` (ozaki_gram_bytes) once per operator; a product Y = Z^T (Z X) uses
+// `work` (ozaki_gram_work_bytes).
+bool ozaki_gram_usable(int64_t n, int64_t d, int N);
+size_t ozaki_gram_bytes(int64_t n, int64_t d);
+size_t ozaki_gram_work_bytes(int64_t n, int64_t d, int N, int sms);
+cudaError_t launch_ozaki_split_gram(int64_t n, int64_t d, int z_f64, const void* Z, int64_t ldz, void* zbuf, int sms,
+                                    cudaStream_t st);
+cudaError_t launch_ozaki_gram_apply(int64_t n, int64_t d, int N, const void* zbuf, const double* X, int64_t ldx,
+                                    double* Y, int64_t ldy, void* work, long long wait_cycles, int* err, int sms,
+                                    cudaStream_t st);
 
 // FP64 residual r = b - (A x + mu x) and per-CTA partials of ||r||^2.
 cudaError_t launch_csr_residual(int vals_f64, int64_t d, const int* rowptr, const int* colidx,

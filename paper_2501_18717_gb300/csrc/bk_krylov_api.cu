@@ -534,6 +534,18 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
     BK_CK(cudaMemsetAsync(bzerr, 0, sizeof(int), st));
     BK_CK(bk::launch_bf16_gram_split(o.nrows, d, (const float*)o.vals, o.ld, bzc, st));
   }
+  // BF16 runs also take their FP64-accurate residual products to the tensor cores: the
+  // Ozaki-split digits of the stored Z and Z^T, made once per call
+  void *ozz = nullptr, *ozw = nullptr;
+  int* ozerr = nullptr;
+  if (bf16 && o64.kind == BK_GRAM && bk::ozaki_gram_usable(o64.nrows, d, L)) {
+    const size_t wb = bk::ozaki_gram_work_bytes(o64.nrows, d, L, c->sms);
+    BK_CK(ws_get(c, WS_OZ_A, bk::ozaki_gram_bytes(o64.nrows, d), &ozz));
+    BK_CK(ws_get(c, WS_OZ_X, wb + 256, &ozw));
+    ozerr = (int*)((char*)ozw + wb);
+    BK_CK(cudaMemsetAsync(ozerr, 0, sizeof(int), st));
+    BK_CK(bk::launch_ozaki_split_gram(o64.nrows, d, o64.vals_f64, o64.vals, o64.ld, ozz, c->sms, st));
+  }
   const double* bd = nullptr;
   BK_CK(stage_in(c, WS_B64, b, (size_t)d * 8, (const void**)&bd));
   double* dmu = nullptr;
@@ -679,7 +691,10 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
     const double prev_worst = worst;
     for (int attempt = 0; attempt < 2; ++attempt) {
       prof.begin();
-      BK_CK(apply_fp64(c, o64, Xd, ldx, L, AX, Vw, df_ok));
+      if (ozz && df_ok)
+        BK_CK(bk::launch_ozaki_gram_apply(o64.nrows, d, L, ozz, Xd, ldx, AX, ldx, ozw, 0, ozerr, c->sms, st));
+      else
+        BK_CK(apply_fp64(c, o64, Xd, ldx, L, AX, Vw, df_ok));
       prof.end(BK_K_RESIDUAL);
       BK_CK(bk::launch_shift_residual(d, L, bd, AX, Xd, ldx, dmu, Rres, norms, st));
       residual_loads += 1;
@@ -692,6 +707,16 @@ extern "C" bk_status bk_ridge_path(bk_ctx* c, const bk_operator* A, int32_t L, c
       df_ok = false;  // recompute this residual in FP64
     }
     if (worst <= opts.tol) result = BK_OK;
+  }
+  if (ozerr) {  // an Ozaki-split residual product whose pipeline wait gave up
+    int herr = 0;
+    BK_CK(cudaMemcpyAsync(c->hparts, ozerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BK_CK(cudaStreamSynchronize(st));
+    std::memcpy(&herr, c->hparts, sizeof(int));
+    if (herr) {
+      std::snprintf(c->last_error, sizeof(c->last_error), "tensor-core pipeline wait timed out");
+      result = BK_TIMEOUT;
+    }
   }
   if (bzerr) {  // a BF16 product whose pipeline wait gave up left an invalid load
     BK_CK(cudaMemcpyAsync(c->hparts, bzerr, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -782,8 +807,8 @@ bk_status sample_driver(bk_ctx* c, const bk_operator* Kop, double nugget, int32_
   if (oz) {  // digits of K once per call; the loads then run on the tensor cores
     void *oza = nullptr, *ozx = nullptr;
     BK_CK(ws_get(c, WS_OZ_A, bk::ozaki_a_bytes(d), &oza));
-    BK_CK(ws_get(c, WS_OZ_X, bk::ozaki_x_bytes(d, m) + 256, &ozx));
-    ozerr = (int*)((char*)ozx + bk::ozaki_x_bytes(d, m));
+    BK_CK(ws_get(c, WS_OZ_X, bk::ozaki_x_bytes(d, m, c->sms) + 256, &ozx));
+    ozerr = (int*)((char*)ozx + bk::ozaki_x_bytes(d, m, c->sms));
     BK_CK(cudaMemsetAsync(ozerr, 0, sizeof(int), st));
     BK_CK(bk::launch_ozaki_split_a(d, (const float*)o.vals, o.ld, oza, c->sms, st));
     lz.oza = oza;
@@ -1455,7 +1480,10 @@ extern "C" bk_status bk_apply_ozaki(bk_ctx* c, const bk_operator* A, double mu, 
   if (s != BK_OK) return s;
   const int64_t d = o.d;
   if (ldx < d || ldy < d) return BK_ERR_ARG;
-  if (A->kind != BK_DENSE || A->dtype != BK_F32 || !bk::ozaki_usable(d, L)) return BK_ERR_UNSUPPORTED;
+  const bool gram = A->kind == BK_GRAM;
+  if (gram ? !bk::ozaki_gram_usable(o.nrows, d, L)
+           : (A->kind != BK_DENSE || A->dtype != BK_F32 || !bk::ozaki_usable(d, L)))
+    return BK_ERR_UNSUPPORTED;
   BK_CK(cudaSetDevice(c->device));
   cudaStream_t st = c->stream;
   BK_CK(stage_pcg_operator(c, A, &o));
@@ -1466,12 +1494,19 @@ extern "C" bk_status bk_apply_ozaki(bk_ctx* c, const bk_operator* A, double mu, 
   const bool direct = is_device_ptr(Y) && ldy == ldx;
   if (!direct) BK_CK(ws_get(c, WS_TMP_OUT, xbytes, (void**)&Yd));
   void *oza = nullptr, *ozx = nullptr;
-  BK_CK(ws_get(c, WS_OZ_A, bk::ozaki_a_bytes(d), &oza));
-  BK_CK(ws_get(c, WS_OZ_X, bk::ozaki_x_bytes(d, L) + 256, &ozx));
-  int* err = (int*)((char*)ozx + bk::ozaki_x_bytes(d, L));
+  const size_t ab = gram ? bk::ozaki_gram_bytes(o.nrows, d) : bk::ozaki_a_bytes(d);
+  const size_t xb = gram ? bk::ozaki_gram_work_bytes(o.nrows, d, L, c->sms) : bk::ozaki_x_bytes(d, L, c->sms);
+  BK_CK(ws_get(c, WS_OZ_A, ab, &oza));
+  BK_CK(ws_get(c, WS_OZ_X, xb + 256, &ozx));
+  int* err = (int*)((char*)ozx + xb);
   BK_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
-  BK_CK(bk::launch_ozaki_split_a(d, (const float*)o.vals, o.ld, oza, c->sms, st));
-  BK_CK(bk::launch_ozaki_apply(d, L, oza, Xd, ldx, Yd, ldx, ozx, 0, err, c->sms, st));
+  if (gram) {
+    BK_CK(bk::launch_ozaki_split_gram(o.nrows, d, o.vals_f64, o.vals, o.ld, oza, c->sms, st));
+    BK_CK(bk::launch_ozaki_gram_apply(o.nrows, d, L, oza, Xd, ldx, Yd, ldx, ozx, 0, err, c->sms, st));
+  } else {
+    BK_CK(bk::launch_ozaki_split_a(d, (const float*)o.vals, o.ld, oza, c->sms, st));
+    BK_CK(bk::launch_ozaki_apply(d, L, oza, Xd, ldx, Yd, ldx, ozx, 0, err, c->sms, st));
+  }
   if (mu != 0.0)
     for (int j = 0; j < L; ++j) BK_CK(bk::launch_axpy(d, mu, Xd + (size_t)j * ldx, Yd + (size_t)j * ldx, st));
   if (!direct)

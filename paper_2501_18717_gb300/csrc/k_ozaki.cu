@@ -73,6 +73,35 @@ static_assert(kOzDigits * kOzNP <= (int)kOzTmemCols, "accumulators in tensor mem
 // (r < R, k < Kd); the digits go to dig[(i Rpad + r) ldk + k] (rows R .. Rpad - 1 are
 // written as zeros), the exponent to eblk[r nkb + kb] (kOzNoBlock for an all-zero
 // block).
+// The digits of one (row, K block) from the warp's values v[u] = element k0 + lane + 32 u.
+template <typename T>
+__device__ __forceinline__ void oz_digits(const T (&v)[kOzKB / 32], int lane, int64_t r, int64_t R, int64_t Rpad,
+                                          int64_t Kd, int64_t kb, __nv_bfloat16* __restrict__ dig, int64_t ldk,
+                                          int* __restrict__ eblk, int64_t nkb) {
+  const int64_t k0 = kb * kOzKB;
+  T amax = 0;
+#pragma unroll
+  for (int u = 0; u < kOzKB / 32; ++u) amax = fmax(amax, fabs(v[u]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  int e = 0;
+  if (amax > 0) frexp(amax, &e);  // amax = f 2^e, f in [0.5, 1): |v| < 2^e
+#pragma unroll
+  for (int u = 0; u < kOzKB / 32; ++u) {
+    const int64_t k = k0 + lane + 32 * u;
+    if (k >= Kd) continue;
+    T rem = amax > 0 ? ldexp(v[u], -e) : (T)0;  // in (-1, 1), exact
+#pragma unroll
+    for (int i = 0; i < kOzDigits; ++i) {
+      const int sh = 6 + 7 * i;
+      const T dgt = rint(ldexp(rem, sh));  // |dgt| <= 64
+      rem = rem - ldexp(dgt, -sh);         // exact: what the digit leaves
+      dig[((int64_t)i * Rpad + r) * ldk + k] = __float2bfloat16_rn((float)dgt);
+    }
+  }
+  if (lane == 0 && r < R) eblk[r * nkb + kb] = amax > 0 ? e : kOzNoBlock;
+}
+
 template <typename T>
 __global__ void k_oz_split(int64_t R, int64_t Rpad, int64_t Kd, const T* __restrict__ src, int64_t ld,
                            __nv_bfloat16* __restrict__ dig, int64_t ldk, int* __restrict__ eblk, int64_t nkb) {
@@ -82,31 +111,41 @@ __global__ void k_oz_split(int64_t R, int64_t Rpad, int64_t Kd, const T* __restr
     const int64_t r = w / nkb, kb = w - r * nkb;
     const int64_t k0 = kb * kOzKB;
     T v[kOzKB / 32];
-    T amax = 0;
 #pragma unroll
     for (int u = 0; u < kOzKB / 32; ++u) {
       const int64_t k = k0 + lane + 32 * u;
       v[u] = (r < R && k < Kd) ? src[r * ld + k] : (T)0;
-      amax = fmax(amax, fabs(v[u]));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    int e = 0;
-    if (amax > 0) frexp(amax, &e);  // amax = f 2^e, f in [0.5, 1): |v| < 2^e
+    oz_digits<T>(v, lane, r, R, Rpad, Kd, kb, dig, ldk, eblk, nkb);
+  }
+}
+
+// The same split of the transposed source: element k of row r is src[k ld + r] (the
+// columns of a row-major matrix). A block of 32 warps stages 32 rows x one K block
+// through shared memory (coalesced reads along r), then warp w splits row r0 + w.
+constexpr int kOzTRows = 32;
+template <typename T>
+__global__ void __launch_bounds__(1024) k_oz_split_t(int64_t R, int64_t Rpad, int64_t Kd, const T* __restrict__ src,
+                                                     int64_t ld, __nv_bfloat16* __restrict__ dig, int64_t ldk,
+                                                     int* __restrict__ eblk, int64_t nkb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);  // [kOzKB][kOzTRows + 1]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t rtiles = Rpad / kOzTRows;
+  for (int64_t b = blockIdx.x; b < rtiles * nkb; b += gridDim.x) {
+    const int64_t r0 = (b / nkb) * kOzTRows, kb = b % nkb, k0 = kb * kOzKB;
 #pragma unroll
     for (int u = 0; u < kOzKB / 32; ++u) {
-      const int64_t k = k0 + lane + 32 * u;
-      if (k >= Kd) continue;
-      T rem = amax > 0 ? ldexp(v[u], -e) : (T)0;  // in (-1, 1), exact
-#pragma unroll
-      for (int i = 0; i < kOzDigits; ++i) {
-        const int sh = 6 + 7 * i;
-        const T dgt = rint(ldexp(rem, sh));        // |dgt| <= 64
-        rem = rem - ldexp(dgt, -sh);               // exact: what the digit leaves
-        dig[((int64_t)i * Rpad + r) * ldk + k] = __float2bfloat16_rn((float)dgt);
-      }
+      const int kk = w + 32 * u;
+      const int64_t r = r0 + lane, k = k0 + kk;
+      tile[kk * (kOzTRows + 1) + lane] = (r < R && k < Kd) ? src[k * ld + r] : (T)0;
     }
-    if (lane == 0 && r < R) eblk[r * nkb + kb] = amax > 0 ? e : kOzNoBlock;
+    __syncthreads();
+    T v[kOzKB / 32];
+#pragma unroll
+    for (int u = 0; u < kOzKB / 32; ++u) v[u] = tile[(lane + 32 * u) * (kOzTRows + 1) + w];
+    oz_digits<T>(v, lane, r0 + w, R, Rpad, Kd, kb, dig, ldk, eblk, nkb);
+    __syncthreads();
   }
 }
 
@@ -164,8 +203,9 @@ struct OzArgs {
   const int* ex_rel;   // [kb Cpad + c]
   const int* ea_max;   // [r]
   const int* ex_max;   // [c]
-  double* Y;           // column-major, ldy
+  double* Y;           // column-major, ldy; with nkc > 1 the partial of chunk kc starts at column kc N
   int64_t ldy;
+  int64_t nkc, kbc;    // K chunks (split-K) and K blocks per chunk
   long long wait;
   int* err;
 };
@@ -189,8 +229,17 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   volatile long long* s_cons_a = s_cons_x + 1;                                                // A tiles seen
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t mtiles = a.Rpad / 128, ntiles = a.Cpad / kOzNP;
-  const int64_t items = mtiles * ntiles;
   const int64_t nks = (a.K + 63) / 64;
+  const int64_t tiles = mtiles * ntiles;
+  const int64_t items = tiles * a.nkc;
+  // item it: K chunk it / tiles (its K blocks [kb0, kb1), stages [ks0, ks1)), then row
+  // tile and column tile
+  auto krange = [&](int64_t it, int64_t& kb0, int64_t& kb1, int64_t& ks0, int64_t& ks1) {
+    kb0 = (it / tiles) * a.kbc;
+    kb1 = kb0 + a.kbc < a.nkb ? kb0 + a.kbc : a.nkb;
+    ks0 = kb0 * kOzStagesPerBlock;
+    ks1 = kb1 * kOzStagesPerBlock < nks ? kb1 * kOzStagesPerBlock : nks;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
@@ -222,8 +271,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       tma_prefetch_desc(&mapX);
       long long gx = 0, ga = 0;
       for (int64_t it = blockIdx.x; it < items && !*s_abort; it += gridDim.x) {
-        const int64_t mt = it / ntiles, nt = it % ntiles;
-        for (int64_t ks = 0; ks < nks && !*s_abort; ++ks, ++gx) {
+        const int64_t mt = (it % tiles) / ntiles, nt = it % ntiles;
+        int64_t kb0, kb1, ks0, ks1;
+        krange(it, kb0, kb1, ks0, ks1);
+        for (int64_t ks = ks0; ks < ks1 && !*s_abort; ++ks, ++gx) {
           const int xs = (int)(gx & 1);
           if (gx >= 2 && !mbar_wait(xempty + xs, (uint32_t)((gx >> 1) - 1) & 1, a.wait)) {
             *s_abort = 1;
@@ -254,13 +305,15 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       long long gx = 0, ga = 0, per = 0;
       bool ok = true;
       for (int64_t it = blockIdx.x; it < items && ok && !*s_abort; it += gridDim.x) {
-        for (int64_t p0 = 0; p0 < nks && ok && !*s_abort; p0 += kOzStagesPerBlock, ++per) {
+        int64_t kb0, kb1, ks0, ks1;
+        krange(it, kb0, kb1, ks0, ks1);
+        for (int64_t p0 = ks0; p0 < ks1 && ok && !*s_abort; p0 += kOzStagesPerBlock, ++per) {
           if (per >= 1 && !mbar_wait(acce, (uint32_t)(per - 1) & 1, a.wait)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const int64_t p1 = p0 + kOzStagesPerBlock < nks ? p0 + kOzStagesPerBlock : nks;
+          const int64_t p1 = p0 + kOzStagesPerBlock < ks1 ? p0 + kOzStagesPerBlock : ks1;
           for (int64_t ks = p0; ks < p1 && ok; ++ks, ++gx) {
             const int xs = (int)(gx & 1);
             if (!mbar_wait(xfull + xs, (uint32_t)(gx >> 1) & 1, a.wait)) {
@@ -308,13 +361,15 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     bool ok = true;
     for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
       if (__any_sync(0xffffffffu, *s_abort != 0)) break;
-      const int64_t mt = it / ntiles, nt = it % ntiles;
+      const int64_t mt = (it % tiles) / ntiles, nt = it % ntiles;
+      int64_t kb0, kb1, ks0, ks1;
+      krange(it, kb0, kb1, ks0, ks1);
       const int64_t r = mt * 128 + row;
       const int64_t cbase = nt * kOzNP + hf * 32;
       float H[32], L[32];
 #pragma unroll
       for (int c = 0; c < 32; ++c) H[c] = L[c] = 0.f;
-      for (int64_t kb = 0; kb * kOzStagesPerBlock < nks; ++kb, ++per) {
+      for (int64_t kb = kb0; kb < kb1; ++kb, ++per) {
         if (!__all_sync(0xffffffffu, mbar_wait(accf, (uint32_t)per & 1, a.wait))) {
           ok = false;
           break;
@@ -357,7 +412,9 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int64_t col = cbase + c;
-          if (col < a.N) a.Y[col * a.ldy + r] = ldexp((double)H[c] + (double)L[c], eam + a.ex_max[col] - 12);
+          if (col < a.N)
+            a.Y[((it / tiles) * (a.nkc > 1 ? a.N : 0) + col) * a.ldy + r] =
+                ldexp((double)H[c] + (double)L[c], eam + a.ex_max[col] - 12);
         }
       }
     }
@@ -387,6 +444,19 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 }
 
 }  // namespace
+
+// Y[c ldy + r] = sum over chunks of part[(kc N + c) M + r], chunks in order
+__global__ void k_oz_sum(int64_t M, int N, int64_t nkc, const double* __restrict__ part, double* __restrict__ Y,
+                         int64_t ldy) {
+  const int64_t total = M * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = idx / M, r = idx - c * M;
+    double s = 0.0;
+    for (int64_t k = 0; k < nkc; ++k) s += part[(k * N + c) * M + r];
+    Y[c * ldy + r] = s;
+  }
+}
 
 // ---------------------------------------------------------------- host side
 namespace {
@@ -424,67 +494,165 @@ OzOperand oz_operand(int64_t R, int64_t Rpad, int64_t K, void* buf) {
   o.emax = reinterpret_cast<int*>(p);
   return o;
 }
+// the operand of the left factor (rows padded to 128) and of the right factor (to 64)
+OzOperand oz_left(int64_t R, int64_t K, void* buf) { return oz_operand(R, oz_up(R, 128), K, buf); }
+OzOperand oz_right(int64_t R, int64_t K, void* buf) { return oz_operand(R, oz_up(R, kOzNP), K, buf); }
+size_t oz_left_bytes(int64_t R, int64_t K) { return oz_operand_bytes(oz_up(R, 128), K); }
+size_t oz_right_bytes(int64_t R, int64_t K) { return oz_operand_bytes(oz_up(R, kOzNP), K); }
 
+// Digits of a source whose row r, element k is src[r ld + k] (transposed: src[k ld + r]);
+// relative exponents by row then block (left factor) or by block then row (right).
 template <typename T>
-cudaError_t oz_split(const OzOperand& o, const T* src, int64_t ld, int64_t rs, int64_t ks, int sms, cudaStream_t st) {
-  const int64_t warps = o.Rpad * o.nkb;
-  int64_t grid = (warps + 7) / 8;
-  if (grid > (int64_t)sms * 16) grid = (int64_t)sms * 16;
-  k_oz_split<T><<<(int)grid, 256, 0, st>>>(o.R, o.Rpad, o.K, src, ld, o.dig, o.ldk, o.eblk, o.nkb);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+cudaError_t oz_split(const OzOperand& o, const T* src, int64_t ld, bool transposed, bool right, int sms,
+                     cudaStream_t st) {
+  cudaError_t e;
+  if (!transposed) {
+    const int64_t warps = o.Rpad * o.nkb;
+    int64_t grid = (warps + 7) / 8;
+    if (grid > (int64_t)sms * 16) grid = (int64_t)sms * 16;
+    k_oz_split<T><<<(int)grid, 256, 0, st>>>(o.R, o.Rpad, o.K, src, ld, o.dig, o.ldk, o.eblk, o.nkb);
+  } else {
+    const size_t smem = (size_t)kOzKB * (kOzTRows + 1) * sizeof(T);
+    if ((e = cudaFuncSetAttribute(k_oz_split_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return e;
+    int64_t grid = (o.Rpad / kOzTRows) * o.nkb;
+    if (grid > (int64_t)sms * 4) grid = (int64_t)sms * 4;
+    k_oz_split_t<T><<<(int)grid, 1024, smem, st>>>(o.R, o.Rpad, o.K, src, ld, o.dig, o.ldk, o.eblk, o.nkb);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int64_t g2 = (o.Rpad + 7) / 8;
   if (g2 > (int64_t)sms * 16) g2 = (int64_t)sms * 16;
-  k_oz_rel<<<(int)g2, 256, 0, st>>>(o.R, o.Rpad, o.nkb, o.eblk, o.erel, rs, ks, o.emax);
+  k_oz_rel<<<(int)g2, 256, 0, st>>>(o.R, o.Rpad, o.nkb, o.eblk, o.erel, right ? 1 : o.nkb, right ? o.Rpad : 1,
+                                    o.emax);
+  return cudaGetLastError();
+}
+
+// Split-K plan: with fewer output tiles than two per SM, items also cut K into chunks
+// of whole K blocks (at least two per SM in all); the partials are summed in chunk order.
+void oz_plan(int64_t M, int64_t N, int64_t K, int sms, int64_t* nkc, int64_t* kbc) {
+  const int64_t tiles = (oz_up(M, 128) / 128) * (oz_up(N, kOzNP) / kOzNP);
+  const int64_t nkb = (K + kOzKB - 1) / kOzKB;
+  int64_t want = tiles >= 2 * (int64_t)sms ? 1 : (2 * (int64_t)sms + tiles - 1) / tiles;
+  if (want > nkb) want = nkb;
+  if (want < 1) want = 1;
+  *kbc = (nkb + want - 1) / want;
+  *nkc = (nkb + *kbc - 1) / *kbc;
+}
+size_t oz_part_bytes(int64_t M, int64_t N, int64_t K, int sms) {
+  int64_t nkc, kbc;
+  oz_plan(M, N, K, sms, &nkc, &kbc);
+  return nkc > 1 ? oz_al((size_t)nkc * N * M * 8) : 0;
+}
+
+// Y (A.R x X.R, column-major ldy) = A X^T over the common K; part holds
+// oz_part_bytes(A.R, X.R, K, sms) for the split-K partials
+cudaError_t oz_gemm(const OzOperand& A, const OzOperand& X, double* Y, int64_t ldy, double* part,
+                    long long wait_cycles, int* err, int sms, cudaStream_t st) {
+  if (A.K != X.K) return cudaErrorInvalidValue;
+  CUtensorMap ma, mx;
+  cudaError_t e;
+  if ((e = make_map_bf16(&ma, A.dig, A.K, (int64_t)kOzDigits * A.Rpad, A.ldk, 128)) != cudaSuccess) return e;
+  if ((e = make_map_bf16(&mx, X.dig, X.K, (int64_t)kOzDigits * X.Rpad, X.ldk, kOzNP)) != cudaSuccess) return e;
+  OzArgs args;
+  args.M = A.R;
+  args.K = A.K;
+  args.N = (int)X.R;
+  args.Rpad = A.Rpad;
+  args.Cpad = X.Rpad;
+  args.nkb = A.nkb;
+  args.ea_rel = A.erel;
+  args.ex_rel = X.erel;
+  args.ea_max = A.emax;
+  args.ex_max = X.emax;
+  oz_plan(A.R, X.R, A.K, sms, &args.nkc, &args.kbc);
+  if (args.nkc > 1 && !part) return cudaErrorInvalidValue;
+  args.Y = args.nkc > 1 ? part : Y;
+  args.ldy = args.nkc > 1 ? A.R : ldy;
+  args.wait = wait_cycles > 0 ? wait_cycles : kWaitCycles;
+  args.err = err;
+  if ((e = cudaFuncSetAttribute(k_ozgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem)) != cudaSuccess)
+    return e;
+  const int64_t items = (A.Rpad / 128) * (X.Rpad / kOzNP) * args.nkc;
+  const int grid = (int)(items < sms ? items : sms);
+  k_ozgemm<<<grid, kOzThreads, kOzSmem, st>>>(ma, mx, args);
+  if ((e = cudaGetLastError()) != cudaSuccess || args.nkc == 1) return e;
+  const int64_t total = A.R * X.R;
+  int64_t g = (total + 255) / 256;
+  if (g > (int64_t)sms * 8) g = (int64_t)sms * 8;
+  k_oz_sum<<<(int)g, 256, 0, st>>>(A.R, (int)X.R, args.nkc, part, Y, ldy);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 bool ozaki_usable(int64_t d, int N) {
-  // TMA coordinates are 32-bit: the digit planes of A stack 7 x Rpad rows
+  // TMA coordinates are 32-bit: the digit planes of the left factor stack 7 x Rpad rows
   return d >= 1 && N >= 1 && N <= 4096 && (int64_t)kOzDigits * oz_up(d, 128) < ((int64_t)1 << 31);
 }
-size_t ozaki_a_bytes(int64_t d) { return oz_operand_bytes(oz_up(d, 128), d); }
-size_t ozaki_x_bytes(int64_t d, int N) { return oz_operand_bytes(oz_up(N, kOzNP), d); }
+size_t ozaki_a_bytes(int64_t d) { return oz_left_bytes(d, d); }
+size_t ozaki_x_bytes(int64_t d, int N, int sms) { return oz_al(oz_right_bytes(N, d)) + oz_part_bytes(d, N, d, sms); }
 
 cudaError_t launch_ozaki_split_a(int64_t d, const float* A, int64_t lda, void* abuf, int sms, cudaStream_t st) {
-  const OzOperand o = oz_operand(d, oz_up(d, 128), d, abuf);
-  return oz_split<float>(o, A, lda, o.nkb, 1, sms, st);
+  return oz_split<float>(oz_left(d, d, abuf), A, lda, false, false, sms, st);
 }
 
 cudaError_t launch_ozaki_apply(int64_t d, int N, const void* abuf, const double* X, int64_t ldx, double* Y,
                                int64_t ldy, void* xbuf, long long wait_cycles, int* err, int sms, cudaStream_t st) {
   if (!ozaki_usable(d, N)) return cudaErrorInvalidValue;
-  const OzOperand oa = oz_operand(d, oz_up(d, 128), d, const_cast<void*>(abuf));
-  const OzOperand ox = oz_operand(N, oz_up(N, kOzNP), d, xbuf);
-  // X column c is row c of the split (elements X[c ldx + k]); exponents by block, then column
-  cudaError_t e = oz_split<double>(ox, X, ldx, 1, ox.Rpad, sms, st);
+  const OzOperand oa = oz_left(d, d, const_cast<void*>(abuf));
+  const OzOperand ox = oz_right(N, d, xbuf);
+  double* part = reinterpret_cast<double*>(static_cast<char*>(xbuf) + oz_al(oz_right_bytes(N, d)));
+  // column c of X is row c of the right factor (elements X[c ldx + k])
+  cudaError_t e = oz_split<double>(ox, X, ldx, false, true, sms, st);
   if (e != cudaSuccess) return e;
-  CUtensorMap ma, mx;
-  if ((e = make_map_bf16(&ma, oa.dig, d, (int64_t)kOzDigits * oa.Rpad, oa.ldk, 128)) != cudaSuccess) return e;
-  if ((e = make_map_bf16(&mx, ox.dig, d, (int64_t)kOzDigits * ox.Rpad, ox.ldk, kOzNP)) != cudaSuccess) return e;
-  OzArgs args;
-  args.M = d;
-  args.K = d;
-  args.N = N;
-  args.Rpad = oa.Rpad;
-  args.Cpad = ox.Rpad;
-  args.nkb = oa.nkb;
-  args.ea_rel = oa.erel;
-  args.ex_rel = ox.erel;
-  args.ea_max = oa.emax;
-  args.ex_max = ox.emax;
-  args.Y = Y;
-  args.ldy = ldy;
-  args.wait = wait_cycles > 0 ? wait_cycles : kWaitCycles;
-  args.err = err;
-  if ((e = cudaFuncSetAttribute(k_ozgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem)) != cudaSuccess)
-    return e;
-  const int64_t items = (oa.Rpad / 128) * (ox.Rpad / kOzNP);
-  const int grid = (int)(items < sms ? items : sms);
-  k_ozgemm<<<grid, kOzThreads, kOzSmem, st>>>(ma, mx, args);
-  return cudaGetLastError();
+  return oz_gemm(oa, ox, Y, ldy, part, wait_cycles, err, sms, st);
+}
+
+// Gram form A = Z^T Z (Z: n x d row-major): the digits of Z (rows of Z) and of Z^T
+// (columns of Z), made once per operator.
+bool ozaki_gram_usable(int64_t n, int64_t d, int N) { return ozaki_usable(n, N) && ozaki_usable(d, N); }
+size_t ozaki_gram_bytes(int64_t n, int64_t d) { return oz_al(oz_left_bytes(n, d)) + oz_left_bytes(d, n); }
+size_t oz_gram_part_bytes(int64_t n, int64_t d, int N, int sms) {
+  const size_t a = oz_part_bytes(n, N, d, sms), b = oz_part_bytes(d, N, n, sms);
+  return a > b ? a : b;
+}
+size_t ozaki_gram_work_bytes(int64_t n, int64_t d, int N, int sms) {
+  return oz_al(oz_right_bytes(N, d)) + oz_al(oz_right_bytes(N, n)) + oz_al((size_t)n * N * 8) +
+         oz_gram_part_bytes(n, d, N, sms);
+}
+
+cudaError_t launch_ozaki_split_gram(int64_t n, int64_t d, int z_f64, const void* Z, int64_t ldz, void* zbuf, int sms,
+                                    cudaStream_t st) {
+  const OzOperand oz = oz_left(n, d, zbuf);
+  const OzOperand ot = oz_left(d, n, static_cast<char*>(zbuf) + oz_al(oz_left_bytes(n, d)));
+  cudaError_t e = z_f64 ? oz_split<double>(oz, (const double*)Z, ldz, false, false, sms, st)
+                        : oz_split<float>(oz, (const float*)Z, ldz, false, false, sms, st);
+  if (e != cudaSuccess) return e;
+  return z_f64 ? oz_split<double>(ot, (const double*)Z, ldz, true, false, sms, st)
+               : oz_split<float>(ot, (const float*)Z, ldz, true, false, sms, st);
+}
+
+cudaError_t launch_ozaki_gram_apply(int64_t n, int64_t d, int N, const void* zbuf, const double* X, int64_t ldx,
+                                    double* Y, int64_t ldy, void* work, long long wait_cycles, int* err, int sms,
+                                    cudaStream_t st) {
+  if (!ozaki_gram_usable(n, d, N)) return cudaErrorInvalidValue;
+  char* zb = static_cast<char*>(const_cast<void*>(zbuf));
+  const OzOperand oz = oz_left(n, d, zb);
+  const OzOperand ot = oz_left(d, n, zb + oz_al(oz_left_bytes(n, d)));
+  char* w = static_cast<char*>(work);
+  const OzOperand ox = oz_right(N, d, w);
+  w += oz_al(oz_right_bytes(N, d));
+  const OzOperand ov = oz_right(N, n, w);
+  w += oz_al(oz_right_bytes(N, n));
+  double* V = reinterpret_cast<double*>(w);  // n x N column-major
+  w += oz_al((size_t)n * N * 8);
+  double* part = reinterpret_cast<double*>(w);
+  cudaError_t e = oz_split<double>(ox, X, ldx, false, true, sms, st);
+  if (e == cudaSuccess) e = oz_gemm(oz, ox, V, n, part, wait_cycles, err, sms, st);      // V = Z X
+  if (e == cudaSuccess) e = oz_split<double>(ov, V, n, false, true, sms, st);
+  if (e == cudaSuccess) e = oz_gemm(ot, ov, Y, ldy, part, wait_cycles, err, sms, st);    // Y = Z^T V
+  return e;
 }
 
 }  // namespace bk

@@ -152,3 +152,20 @@ def test_sampling_ozaki_mode(bk, ctx, fn):
         tol = 1e-13 * lam[-1] / lam[0]
     err = np.linalg.norm(S - ref) / np.linalg.norm(ref)
     assert err <= tol, (err, tol, info.as_dict())
+
+
+def test_ozaki_gram_form_matches_accurate_product(bk, ctx):
+    """Z^T (Z X) for the ridge configuration's Z shape (here 5003 x 300: ragged row
+    tiles of Z^T and K blocks of both products), 4 columns, mu 0.5, against the
+    oracle's accurate products (V = Z X, then Z^T V): within 2^-40 of
+    sum_i |z_ik| (|Z| |X|)_i, the scale of the two rounded products."""
+    n, d, L = 5003, 300, 4
+    rng = np.random.default_rng(21)
+    Z = W.ridge_workload(W.BASE_SEED + 22, n, d, 1e-3)[0].astype(np.float32)
+    X = rng.standard_normal((d, L))
+    Y = np.zeros((d, L), order="F")
+    bk.apply(ctx, bk.gram_operator(Z), 0.5, np.asfortranarray(X), Y, ozaki=True)
+    V = np.stack([accurate.matvec(Z, X[:, j]) for j in range(L)], axis=1)
+    ref = np.stack([accurate.matvec(np.ascontiguousarray(Z.T), V[:, j]) for j in range(L)], axis=1) + 0.5 * X
+    scale = np.abs(Z.astype(np.float64)).T @ (np.abs(Z.astype(np.float64)) @ np.abs(X))
+    assert np.all(np.abs(Y - ref) <= 2.0 ** -40 * scale), np.max(np.abs(Y - ref) / scale)
