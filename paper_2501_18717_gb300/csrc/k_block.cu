@@ -419,6 +419,32 @@ __global__ void __launch_bounds__(kUpdThreads, MP < 36 ? (sizeof(T) == 4 ? 3 : 2
                         ld, sTi, sTT, sxc, do_x, upd, x);
 }
 
+// FP32 direction update at widths up to 36 with each thread's next row in flight
+// (update_pq_rows_async: a two-stage cp.async ring of 16-byte panel slots in dynamic
+// shared memory, 72 KB at width 36); persistent grid of two CTAs per SM.
+template <int MP>
+__global__ void __launch_bounds__(kUpdThreads, 2)
+    k_update_p_async(int64_t d, int m, float* Q, float* P, int64_t ld, const float* __restrict__ xc_t,
+                     const float* __restrict__ ti_t, const float* __restrict__ t_t, double* x,
+                     const DevState* state) {
+  const bool do_x = state->pending_x;
+  const bool upd = !(state->done_a | state->done_b);
+  if (!do_x && !upd) return;
+  const bool first = state->first;
+  __shared__ __align__(16) float sTi[MP * MP];
+  __shared__ __align__(16) float sTT[MP * MP];
+  __shared__ __align__(16) float sxc[MP];
+  extern __shared__ __align__(16) float4 ring[];
+  for (int idx = threadIdx.x; idx < MP * MP; idx += blockDim.x) {
+    sTi[idx] = ti_t[idx];
+    sTT[idx] = first ? 0.f : t_t[idx];
+  }
+  for (int idx = threadIdx.x; idx < MP; idx += blockDim.x) sxc[idx] = do_x ? xc_t[idx] : 0.f;
+  __syncthreads();
+  update_pq_rows_async<MP>(blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, d, m, Q,
+                           P, ld, sTi, sTT, sxc, do_x, upd, x, ring);
+}
+
 // ------------------------------------------------------------------ start block, helpers
 // Q = [r * scale, Omega] on panels (the Omega buffer is a full panel block whose column
 // 0 and padding columns are zero), x = 0. P is formed by the first k_update_p.
@@ -541,15 +567,26 @@ cudaError_t update_r_impl(int64_t d, int m, const void* Y, void* R, int64_t ld, 
 template <typename T, int MP>
 cudaError_t update_p_impl(int64_t d, int m, void* Q, void* P, int64_t ld, const void* xc_t, const void* ti_t,
                           const void* t_t, double* x, const DevState* state, cudaStream_t st, int device) {
-  int grid = capped_grid(d, kUpdThreads, sm_count(device) * (sizeof(T) == 4 ? 4 : 2) * 4);
-  const size_t smem = MP > 36 ? 2 * (size_t)MP * MP * sizeof(T) : 0;
-  if (smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_update_p<T, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if constexpr (sizeof(T) == 4 && MP <= 36) {
+    const size_t ring = (size_t)2 * 2 * (MP / 4) * kUpdThreads * 16;
+    auto k = k_update_p_async<MP>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
     if (e != cudaSuccess) return e;
+    const int grid = capped_grid(d, kUpdThreads, sm_count(device) * 2);
+    k<<<grid, kUpdThreads, ring, st>>>(d, m, (float*)Q, (float*)P, ld, (const float*)xc_t, (const float*)ti_t,
+                                       (const float*)t_t, x, state);
+    return cudaGetLastError();
+  } else {
+    int grid = capped_grid(d, kUpdThreads, sm_count(device) * (sizeof(T) == 4 ? 4 : 2) * 4);
+    const size_t smem = MP > 36 ? 2 * (size_t)MP * MP * sizeof(T) : 0;
+    if (smem) {
+      cudaError_t e = cudaFuncSetAttribute(k_update_p<T, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_update_p<T, MP><<<grid, kUpdThreads, smem, st>>>(d, m, (T*)Q, (T*)P, ld, (const T*)xc_t, (const T*)ti_t,
+                                                    (const T*)t_t, x, state);
+    return cudaGetLastError();
   }
-  k_update_p<T, MP><<<grid, kUpdThreads, smem, st>>>(d, m, (T*)Q, (T*)P, ld, (const T*)xc_t, (const T*)ti_t,
-                                                  (const T*)t_t, x, state);
-  return cudaGetLastError();
 }
 
 #define BK_DISPATCH_MP(mp, F, ...)                  \
