@@ -147,9 +147,9 @@ __global__ void k_three_term(int m, int first, const double* __restrict__ A, con
 
 // Shifted banded Cholesky solves (T + mu_j I) Z_j = E_j, E_j = the nrhs columns of rhs
 // starting at column rhs_col[j] (rhs: n x ncol column-major, ld n). Two kernels:
-//   k_band_factor: one CTA per shift j factors T + mu_j I (band storage, bw
-//     subdiagonals) into work: L x (bw + 2) x n doubles (the factor and the reciprocal
-//     diagonal). A diagonal entry that is exactly zero (a dropped Lanczos direction) is
+//   k_band_factor (bw > 112, blocked) / k_band_factor_smem (bw <= 112): one CTA per
+//     shift j factors T + mu_j I (band storage, bw subdiagonals) into work: L x
+//     (bw + 2) x n doubles (the factor and the reciprocal diagonal). A diagonal entry that is exactly zero (a dropped Lanczos direction) is
 //     replaced by 1 so the dropped direction decouples. A pivot that is not positive
 //     drops its direction the same way (its solution component is zero) and sets
 //     flags[j] = 1: T + mu_j I was not positive definite.
@@ -157,10 +157,21 @@ __global__ void k_three_term(int m, int first, const double* __restrict__ A, con
 //     slice of the right-hand sides, so that many right-hand sides spread over many SMs.
 // Z_j is n x nrhs column-major at Z + j * n * nrhs. Cost O(n bw^2) per shift to factor,
 // O(n bw nrhs) to substitute (Thm. cost).
+// Wide bands (bw > 112): blocked right-looking factorisation. A panel of kBandNB
+// columns (rows c0 .. c0 + kBandNB + bw - 1, column-major in shared memory) is factored
+// column by column; its update of the window that follows, a rank-kBandNB symmetric
+// update of the band entries (i, c), c0 + kBandNB <= c <= i, runs in 4 x 4 register tiles
+// over the panel, so each band entry is read and written once per panel instead of once
+// per column (the column-by-column update in global memory was latency bound at
+// bw = 256). Same storage, pivots and dropped directions as k_band_factor_smem.
+constexpr int kBandNB = 32;
 __global__ void __launch_bounds__(256) k_band_factor(int n, int bw, const double* __restrict__ band, int ldb,
                                                      const double* __restrict__ mus, double* work, int* flags) {
+  extern __shared__ __align__(16) double pan[];  // [kBandNB][PR], column q at pan + q PR
   const int j = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+  // panel rows: the band's rows padded to a multiple of 4, plus one spare 4-row tile for
+  // the window tiles that start at the 4-aligned row below the window (all zeros)
+  const int PR = ((kBandNB + bw + 3) & ~3) + 4;
   double* Lb = work + (size_t)j * (bw + 2) * n;
   double* invL = Lb + (size_t)(bw + 1) * n;
   const double mu = mus[j];
@@ -175,36 +186,88 @@ __global__ void __launch_bounds__(256) k_band_factor(int n, int bw, const double
   }
   if (tid == 0) s_bad = 0;
   __syncthreads();
-  // factorisation, column by column: L(c, c) = sqrt(pivot) formed by one thread
-  for (int c = 0; c < n; ++c) {
-    if (tid == 0) {
-      const double x = Lb[c];
-      if (!(x > 0.0)) {
-        // not positive: drop this direction (unit pivot, zero column), as the block
-        // solves drop dependent columns; the solve continues on the others
-        s_bad = 1;
-        s_inv = 0.0;
-        Lb[c] = 1.0;
-      } else {
-        const double r = rsqrt_nr(x);
-        Lb[c] = x * r;
-        s_inv = r;
-      }
-      invL[c] = s_inv;
+  for (int c0 = 0; c0 < n; c0 += kBandNB) {
+    const int nb = min(kBandNB, n - c0);
+    const int rows = min(nb + bw, n - c0);  // panel rows c0 .. c0 + rows - 1
+    // panel in: pan[q][r] = L(c0 + r, c0 + q) inside the band, 0 elsewhere
+    for (int idx = tid; idx < kBandNB * PR; idx += nth) {
+      const int q = idx / PR, r = idx - q * PR, off = r - q;
+      pan[idx] = (q < nb && r < rows && off >= 0 && off <= bw) ? Lb[(size_t)off * n + c0 + q] : 0.0;
     }
     __syncthreads();
-    const double inv = s_inv;
-    const int w = min(bw, n - 1 - c);
-    for (int r = 1 + tid; r <= w; r += nth) Lb[(size_t)r * n + c] *= inv;
-    __syncthreads();
-    if (inv == 0.0) continue;  // dropped: its zero column changes nothing below
-    // trailing window T(c+a, c+b) -= L(c+a, c) L(c+b, c), 1 <= b <= a <= w:
-    // warps over a, lanes over b
-    for (int a = 1 + warp; a <= w; a += nw) {
-      const double la = Lb[(size_t)a * n + c];
-      for (int b = 1 + lane; b <= a; b += 32) {
-        double* t = Lb + (size_t)(a - b) * n + (c + b);
-        *t = fma(-la, Lb[(size_t)b * n + c], *t);
+    for (int q = 0; q < nb; ++q) {
+      double* col = pan + q * PR;
+      if (tid == 0) {
+        const double x = col[q];
+        if (!(x > 0.0)) {  // not positive: drop this direction (unit pivot, zero column)
+          s_bad = 1;
+          s_inv = 0.0;
+          col[q] = 1.0;
+        } else {
+          const double r = rsqrt_nr(x);
+          col[q] = x * r;
+          s_inv = r;
+        }
+        invL[c0 + q] = s_inv;
+      }
+      __syncthreads();
+      const double inv = s_inv;
+      for (int r = q + 1 + tid; r < rows; r += nth) col[r] *= inv;
+      __syncthreads();
+      if (inv != 0.0 && q + 1 < nb) {
+        // the panel's later columns k: L(r, k) -= L(r, q) L(k, q), r >= k
+        const int nk = nb - 1 - q;
+        for (int idx = tid; idx < nk * rows; idx += nth) {
+          const int k = q + 1 + idx / rows, r = idx - (idx / rows) * rows;
+          if (r >= k) pan[k * PR + r] = fma(-col[r], col[k], pan[k * PR + r]);
+        }
+        __syncthreads();
+      }
+    }
+    // panel out
+    for (int idx = tid; idx < kBandNB * PR; idx += nth) {
+      const int q = idx / PR, r = idx - q * PR, off = r - q;
+      if (q < nb && r < rows && off >= 0 && off <= bw) Lb[(size_t)off * n + c0 + q] = pan[idx];
+    }
+    // window update: band entries (i, c), nb <= c - c0 <= i - c0 < rows, minus the
+    // panel's rank-nb product; 4 x 4 tiles of the lower triangle, a thread per tile
+    // tiles start at the 4-aligned row wb <= nb (aligned 16-byte loads); entries above
+    // the window (rows < nb) are skipped
+    const int wb = nb & ~3, wn = rows - wb;
+    if (rows > nb) {
+      const int t4 = (wn + 3) / 4;
+      const int ntiles = t4 * (t4 + 1) / 2;
+      for (int t = tid; t < ntiles; t += nth) {
+        int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+        while (ti * (ti + 1) / 2 > t) --ti;
+        while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+        const int tc = t - ti * (ti + 1) / 2;
+        const int ib = wb + 4 * ti, cb = wb + 4 * tc;  // panel rows of the tile (< PR - 3)
+        double acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+        for (int q = 0; q < nb; ++q) {
+          const double2* pa = reinterpret_cast<const double2*>(pan + q * PR + ib);
+          const double2* pc = reinterpret_cast<const double2*>(pan + q * PR + cb);
+          const double2 a01 = pa[0], a23 = pa[1], c01 = pc[0], c23 = pc[1];
+          const double a[4] = {a01.x, a01.y, a23.x, a23.y}, cc[4] = {c01.x, c01.y, c23.x, c23.y};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], cc[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int ri = ib + u, rc = cb + v;
+            if (rc >= nb && ri < rows && ri >= rc && ri - rc <= bw) {
+              double* e = Lb + (size_t)(ri - rc) * n + c0 + rc;
+              *e -= acc[u][v];
+            }
+          }
       }
     }
     __syncthreads();
@@ -494,7 +557,11 @@ cudaError_t launch_band_solve(int n, int bw, const double* band, int ldb, int L,
       return e;
     k_band_factor_smem<<<L, 256, smem, st>>>(n, bw, band, ldb, mus, work, flags);
   } else {
-    k_band_factor<<<L, 256, 0, st>>>(n, bw, band, ldb, mus, work, flags);
+    const size_t smem = (size_t)kBandNB * (((kBandNB + bw + 3) & ~3) + 4) * 8;
+    if ((e = cudaFuncSetAttribute(k_band_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return e;
+    k_band_factor<<<L, 256, smem, st>>>(n, bw, band, ldb, mus, work, flags);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
