@@ -931,7 +931,8 @@ def run_sample(args, world, rank, local, dev):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
             "dtype": "f64 blocks, " + ("compensated f32-pair" if args.sample_inner == "f32x2" or onfly
-                                       else ("Ozaki-split bf16 tensor-core" if oz else args.sample_inner))
+                                       else ("Ozaki-split bf16 tensor-core (loads and basis)" if oz
+                                             else args.sample_inner))
                      + (" products of K formed on the fly in f64" if onfly else " products of the f32-stored K")
                      + ", f64 Gram/band solves", "data": "synthetic",
             "config": {"workload": f"rbf_sample_d{d}_m{m}_ls0.2_nugget{args.sample_nugget:g}_"

@@ -78,11 +78,13 @@ typedef enum { BK_F64 = 0, BK_F32 = 1 } bk_dtype;
  *   (and in FP64 GEMMs once a pass stops reducing the residual). bk_ridge_path
  *   only, with at most 128 block columns;
  *   other entry points and operator kinds return BK_ERR_UNSUPPORTED.
- *   BK_PREC_OZAKI: as BK_PREC_F32X2, except that the block products of a stored dense
- *   FP32 operator run on the BF16 tensor cores through an error-free splitting (Ozaki,
- *   Ogita and Oishi, 2012; see bk_apply_ozaki for the digits and the error bound).
- *   The digits of the operator (7 planes of BF16, 14 d^2 bytes) are made once per
- *   call. bk_sample and bk_sample_isqrt with a BK_DENSE FP32 operator only; other
+ *   BK_PREC_OZAKI: FP64 blocks; the block products of a stored dense FP32 operator and
+ *   the FP64 basis products (the Grams that give T_t, the reorthogonalisation, the
+ *   three-term step, Q = W R^{-1}) run on the BF16 tensor cores through an error-free
+ *   splitting (Ozaki, Ogita and Oishi, 2012; see bk_apply_ozaki for the digits and the
+ *   error bound: 2^-45 of the block bounds, the order of an FP64 GEMM's rounding over
+ *   K = d). The digits of the operator (7 planes of BF16, 14 d^2 bytes) are made once
+ *   per call, those of each basis product's operands at the product. bk_sample and bk_sample_isqrt with a BK_DENSE FP32 operator only; other
  *   entry points and operators return BK_ERR_UNSUPPORTED. */
 typedef enum {
   BK_PREC_FP64 = 0,

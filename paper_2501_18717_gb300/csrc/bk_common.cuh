@@ -143,6 +143,13 @@ cudaError_t launch_ozaki_apply(int64_t d, int N, const void* abuf, const double*
 // Gram form A = Z^T Z (Z: n x d row-major, FP32 or FP64, ldz): the digits of Z and of Z^T
 // go into `zbuf` (ozaki_gram_bytes) once per operator; a product Y = Z^T (Z X) uses
 // `work` (ozaki_gram_work_bytes).
+// General FP64 product C = alpha A B + beta C by the Ozaki split (strides as in
+// launch_gemm; each operand contiguous along K or along its other index).
+bool ozaki_gemm_usable(int64_t M, int64_t N, int64_t K, int64_t sai, int64_t sak, int64_t sbk, int64_t sbj);
+size_t ozaki_gemm_work_bytes(int64_t M, int64_t N, int64_t K, int sms);
+cudaError_t launch_ozaki_gemm(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai,
+                              int64_t sak, const double* B, int64_t sbk, int64_t sbj, double beta, double* C,
+                              int64_t ldc, void* work, long long wait_cycles, int* err, int sms, cudaStream_t st);
 bool ozaki_gram_usable(int64_t n, int64_t d, int N);
 size_t ozaki_gram_bytes(int64_t n, int64_t d);
 size_t ozaki_gram_work_bytes(int64_t n, int64_t d, int N, int sms);

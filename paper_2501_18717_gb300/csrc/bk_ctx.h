@@ -26,7 +26,7 @@ enum Slot {
   // (iterate, residual, correction kept across the nested solve)
   WS_XT, WS_RT, WS_FB_X, WS_FB_R, WS_FB_D,
   // Ozaki-split products: digits and exponents of the operator, of the block
-  WS_OZ_A, WS_OZ_X,
+  WS_OZ_A, WS_OZ_X, WS_OZ_G,
   WS_COUNT
 };
 

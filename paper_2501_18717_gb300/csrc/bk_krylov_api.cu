@@ -140,6 +140,7 @@ struct Lanczos {
   const void* oza = nullptr;
   void* ozx = nullptr;
   int* ozerr = nullptr;
+  bool ozb = false;  // FP64 basis products (Grams, reorthogonalisation, Q = W R^{-1}) split too
   int t = 0;      // blocks in T_t
   int loads = 0;  // operator applications
   double rank_tol = 1e-12;
@@ -241,7 +242,10 @@ struct Lanczos {
   // three-term step, Q = W R^{-1}) use the double-float GEMM, about 2^-44 relative
   // (CholQR2's second pass restores orthogonality); the Grams that give the entries of
   // T_t (allow_dd = false) stay in FP64, since the shifted solves and the square root
-  // resolve T_t's smallest eigenvalues. FP64 runs use the FP64 GEMM throughout.
+  // resolve T_t's smallest eigenvalues. FP64 runs use the FP64 GEMM throughout. In an
+  // Ozaki run (ozb) every FP64 basis product, the Grams of T_t included, goes through
+  // the Ozaki split: 2^-45 of the block bounds, the order of an FP64 GEMM's rounding
+  // over K = d (about sqrt(d) u).
   cudaError_t gemm_k(int out64, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int a_f64, int64_t sai,
                      int64_t sak, const void* B, int64_t sbk, int64_t sbj, double beta, void* C, int64_t ldc,
                      bool allow_dd = true) {
@@ -250,6 +254,13 @@ struct Lanczos {
     if (wb) {
       cudaError_t e = ws_get(c, WS_SPLIT, wb, &wk);
       if (e != cudaSuccess) return e;
+    }
+    if (ozb && is64 && out64 && a_f64 == 1 && bk::ozaki_gemm_usable(M, N, K, sai, sak, sbk, sbj)) {
+      void* ow = nullptr;
+      cudaError_t e = ws_get(c, WS_OZ_G, bk::ozaki_gemm_work_bytes(M, N, K, c->sms), &ow);
+      if (e != cudaSuccess) return e;
+      return bk::launch_ozaki_gemm(M, N, K, alpha, (const double*)A, sai, sak, (const double*)B, sbk, sbj, beta,
+                                   (double*)C, ldc, ow, 0, ozerr, c->sms, st);
     }
     if (allow_dd && df && is64 && out64 && a_f64 == 1)
       return bk::launch_gemm_dd(M, N, K, alpha, (const double*)A, sai, sak, (const double*)B, sbk, sbj, beta,
@@ -814,6 +825,7 @@ bk_status sample_driver(bk_ctx* c, const bk_operator* Kop, double nugget, int32_
     lz.oza = oza;
     lz.ozx = ozx;
     lz.ozerr = ozerr;
+    lz.ozb = true;
   }
   BK_CK(bk::launch_copy_cols(1, is64, d, m, Bd, d, lz.W, lz.ldq, st));
   BK_CK(lz.start(lz.W));

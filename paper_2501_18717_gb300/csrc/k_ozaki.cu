@@ -102,6 +102,67 @@ __device__ __forceinline__ void oz_digits(const T (&v)[kOzKB / 32], int lane, in
   if (lane == 0 && r < R) eblk[r * nkb + kb] = amax > 0 ? e : kOzNoBlock;
 }
 
+// FP64 values by integer arithmetic (FP64 instructions run at 1/58 of the FP32 rate
+// here): the block bound from the bit patterns (|v| orders like its pattern), then
+// N = round(v 2^(48 - e)) from the mantissa by a rounding shift (|N| <= 2^48, so
+// |v 2^-e - N 2^-48| <= 2^-49, the bound of the FP32 path), and balanced base-128
+// digits of N from the bottom: a_i = ((N + 64) mod 128) - 64, N <- (N - a_i) / 128, with
+// N = sum_i a_i 2^(42 - 7 i), i.e. v 2^-e ~= sum_i a_i 2^-(6 + 7 i), |a_i| <= 64.
+template <>
+__device__ __forceinline__ void oz_digits<double>(const double (&v)[kOzKB / 32], int lane, int64_t r, int64_t R,
+                                                  int64_t Rpad, int64_t Kd, int64_t kb,
+                                                  __nv_bfloat16* __restrict__ dig, int64_t ldk,
+                                                  int* __restrict__ eblk, int64_t nkb) {
+  const int64_t k0 = kb * kOzKB;
+  unsigned long long amax = 0;
+#pragma unroll
+  for (int u = 0; u < kOzKB / 32; ++u) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v[u]) & 0x7fffffffffffffffull;
+    amax = b > amax ? b : amax;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long x = __shfl_xor_sync(0xffffffffu, amax, o);
+    amax = x > amax ? x : amax;
+  }
+  int e = 0;
+  if (amax) frexp(__longlong_as_double((long long)amax), &e);  // |v| < 2^e
+#pragma unroll
+  for (int u = 0; u < kOzKB / 32; ++u) {
+    const int64_t k = k0 + lane + 32 * u;
+    if (k >= Kd) continue;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v[u]);
+    const int ev = (int)((b >> 52) & 0x7ff);
+    unsigned long long mant = b & 0xfffffffffffffull;
+    int E = -1074;  // value = mant 2^E
+    if (ev) {
+      mant |= 1ull << 52;
+      E = ev - 1075;
+    }
+    const int sh = E + 48 - e;
+    long long N;
+    if (!amax || !mant)
+      N = 0;
+    else if (sh >= 0)
+      N = (long long)(mant << sh);  // only for subnormal blocks; |N| < 2^48
+    else if (-sh > 63)
+      N = 0;
+    else
+      N = (long long)((mant + (1ull << (-sh - 1))) >> (-sh));
+    if (b >> 63) N = -N;
+    int a[kOzDigits];
+#pragma unroll
+    for (int i = kOzDigits - 1; i > 0; --i) {
+      a[i] = (int)((N + 64) & 127) - 64;
+      N = (N - a[i]) >> 7;
+    }
+    a[0] = (int)N;
+#pragma unroll
+    for (int i = 0; i < kOzDigits; ++i) dig[((int64_t)i * Rpad + r) * ldk + k] = __float2bfloat16_rn((float)a[i]);
+  }
+  if (lane == 0 && r < R) eblk[r * nkb + kb] = amax ? e : kOzNoBlock;
+}
+
 template <typename T>
 __global__ void k_oz_split(int64_t R, int64_t Rpad, int64_t Kd, const T* __restrict__ src, int64_t ld,
                            __nv_bfloat16* __restrict__ dig, int64_t ldk, int* __restrict__ eblk, int64_t nkb) {
@@ -458,6 +519,18 @@ __global__ void k_oz_sum(int64_t M, int N, int64_t nkc, const double* __restrict
   }
 }
 
+// C = alpha Y + beta C (Y: M x N column-major, ld M; C: ldc); C is not read when beta = 0
+__global__ void k_oz_axpby(int64_t M, int N, double alpha, const double* __restrict__ Y, double beta, double* C,
+                           int64_t ldc) {
+  const int64_t total = M * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = idx / M, r = idx - c * M;
+    double* o = C + c * ldc + r;
+    *o = beta == 0.0 ? alpha * Y[idx] : fma(alpha, Y[idx], beta * *o);
+  }
+}
+
 // ---------------------------------------------------------------- host side
 namespace {
 
@@ -653,6 +726,43 @@ cudaError_t launch_ozaki_gram_apply(int64_t n, int64_t d, int N, const void* zbu
   if (e == cudaSuccess) e = oz_split<double>(ov, V, n, false, true, sms, st);
   if (e == cudaSuccess) e = oz_gemm(ot, ov, Y, ldy, part, wait_cycles, err, sms, st);    // Y = Z^T V
   return e;
+}
+
+// General FP64 product C = alpha A B + beta C (A: M x K with element (i, k) at
+// A[i sai + k sak], B: K x N with element (k, j) at B[k sbk + j sbj]) through the Ozaki
+// split; each operand must be contiguous along K (sak = 1, sbk = 1) or along the other
+// index (sai = 1, sbj = 1: the transposed split).
+bool ozaki_gemm_usable(int64_t M, int64_t N, int64_t K, int64_t sai, int64_t sak, int64_t sbk, int64_t sbj) {
+  return M >= 1 && N >= 1 && N <= 4096 && K >= 1 && (sak == 1 || sai == 1) && (sbk == 1 || sbj == 1) &&
+         (int64_t)kOzDigits * oz_up(M, 128) < ((int64_t)1 << 31);
+}
+size_t ozaki_gemm_work_bytes(int64_t M, int64_t N, int64_t K, int sms) {
+  return oz_al(oz_left_bytes(M, K)) + oz_al(oz_right_bytes(N, K)) + oz_part_bytes(M, N, K, sms) +
+         oz_al((size_t)M * N * 8);
+}
+cudaError_t launch_ozaki_gemm(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai,
+                              int64_t sak, const double* B, int64_t sbk, int64_t sbj, double beta, double* C,
+                              int64_t ldc, void* work, long long wait_cycles, int* err, int sms, cudaStream_t st) {
+  if (!ozaki_gemm_usable(M, N, K, sai, sak, sbk, sbj)) return cudaErrorInvalidValue;
+  char* w = static_cast<char*>(work);
+  const OzOperand oa = oz_left(M, K, w);
+  w += oz_al(oz_left_bytes(M, K));
+  const OzOperand ob = oz_right(N, K, w);
+  w += oz_al(oz_right_bytes(N, K));
+  double* part = reinterpret_cast<double*>(w);
+  w += oz_part_bytes(M, N, K, sms);
+  double* Y = reinterpret_cast<double*>(w);  // M x N column-major
+  cudaError_t e = sak == 1 ? oz_split<double>(oa, A, sai, false, false, sms, st)
+                           : oz_split<double>(oa, A, sak, true, false, sms, st);
+  if (e == cudaSuccess)
+    e = sbk == 1 ? oz_split<double>(ob, B, sbj, false, true, sms, st)
+                 : oz_split<double>(ob, B, sbk, true, true, sms, st);
+  if (e == cudaSuccess) e = oz_gemm(oa, ob, Y, M, part, wait_cycles, err, sms, st);
+  if (e != cudaSuccess) return e;
+  int64_t g = (M * N + 255) / 256;
+  if (g > (int64_t)sms * 8) g = (int64_t)sms * 8;
+  k_oz_axpby<<<(int)g, 256, 0, st>>>(M, (int)N, alpha, Y, beta, C, ldc);
+  return cudaGetLastError();
 }
 
 }  // namespace bk
