@@ -260,8 +260,10 @@ cudaError_t launch_rbf_apply(int64_t d, int N, const double* pts, int64_t ldp, d
                              const float* Xl, int64_t ldx, double* Y, int64_t ldy, cudaStream_t st);
 // ---- block-Lanczos drivers (k_krylov.cu)
 cudaError_t launch_e1r0(int n, int mb, const double* R0, double* rhs, cudaStream_t st);
+// CholQR step: R (upper, row-major) with Wb = Q R and Rinv = R^+ of the scaled Gram G
+// (m <= 256; work: m x m doubles, scratch: 2 m doubles, keep: m flags, rank: kept count)
 cudaError_t launch_chol_inv(int m, const double* G, double rank_tol, double* work, double* R, double* Rinv,
-                            int* keep, int* rank, cudaStream_t st);
+                            int* keep, int* rank, double* scratch, cudaStream_t st);
 cudaError_t launch_band_put(int ldb, int bw, int m, int k, const double* A, const double* B, double* band,
                             cudaStream_t st);
 // M = [B^T; A] (2m x m column-major, block precision) for the three-term recurrence

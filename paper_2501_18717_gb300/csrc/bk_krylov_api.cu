@@ -127,6 +127,7 @@ struct Lanczos {
   double *G = nullptr, *R1 = nullptr, *R2 = nullptr, *Ri1 = nullptr, *Ri2 = nullptr, *work = nullptr;
   double *Ak = nullptr, *Bk = nullptr, *R0 = nullptr, *band = nullptr;
   int *keep = nullptr, *rank = nullptr;
+  double* ci_scratch = nullptr;
   Prof* prof = nullptr;  // optional event timing
   int df = 0;            // FP64 blocks: FP32 values through the compensated products
   // FP32 blocks of a Gram-form operator on BF16 tensor cores (k_bf16.cu): the BF16
@@ -184,6 +185,7 @@ struct Lanczos {
     Rt = (void*)(R0 + mm);  // m x m in the block precision
     keep = (int*)(R0 + 2 * mm);
     rank = keep + m + 8;
+    ci_scratch = R0 + 2 * mm + m + 16;  // 2 m doubles after keep and rank
     if ((e = ws_get(c, WS_LBAND, (size_t)(m + 1) * ncol_max * 8, (void**)&band)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(band, 0, (size_t)(m + 1) * ncol_max * 8, st)) != cudaSuccess) return e;
     t = 0;
@@ -279,7 +281,8 @@ struct Lanczos {
       double* Ri = pass == 0 ? Ri1 : Ri2;
       if ((e = gemm_k(1, m, m, d, 1.0, src, gaf, ldq, 1, src, 1, ldq, 0.0, G, m, false)) != cudaSuccess)
         return e;
-      if ((e = bk::launch_chol_inv(m, G, rank_tol, work, R, Ri, keep, rank, st)) != cudaSuccess) return e;
+      if ((e = bk::launch_chol_inv(m, G, rank_tol, work, R, Ri, keep, rank, ci_scratch, st)) != cudaSuccess)
+        return e;
       // Qout = src * Ri (Ri row-major: element (k, j) at Ri[k m + j])
       if (is64) {
         e = gemm_k(1, d, m, m, 1.0, src, 1, 1, ldq, Ri, m, 1, 0.0, Qout, ldq);

@@ -1,6 +1,7 @@
 // Kernels of the block-Lanczos drivers (ridge path and Gaussian sampling):
-//   k_chol_inv      Cholesky with dropped dependent columns and the inverse factor of an
-//                   m x m FP64 Gram (m <= 256), for the CholQR orthogonalisation of a block
+//   k_ci_*          Cholesky with dropped dependent columns and the inverse factor of an
+//                   m x m FP64 Gram (m <= 256), for the CholQR orthogonalisation of a block:
+//                   scaling, panel factorisations and trailing updates, inverse, R
 //   k_band_*        the banded block-tridiagonal T_t (Sec. 3.2, Thm. cost): assembly
 //                   from the Lanczos blocks, shifted Cholesky solves for many shifts in
 //                   one launch (one CTA per shift), and the banded product T_t Y
@@ -24,7 +25,6 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
   return r;
 }
 
-constexpr int kCholThreads = 1024;
 
 // One CTA. G (m x m, row-major, FP64) = W^T W of a block W. Writes
 //   R     (m x m, row-major, upper): W = Q R on the kept columns (R rows of dropped
@@ -34,81 +34,147 @@ constexpr int kCholThreads = 1024;
 // with the factorisation done on D^{-1/2} G D^{-1/2} (D = diag G), dropping a column
 // whose scaled pivot is <= rank_tol. work: m * m doubles of scratch (global).
 // Returns the number of kept columns in *rank.
-__global__ void __launch_bounds__(kCholThreads) k_chol_inv(int m, const double* __restrict__ G, double rank_tol,
-                                                          double* work, double* R, double* Rinv, int* keep,
-                                                          int* rank) {
-  const int tid = threadIdx.x;
-  __shared__ double s_rs[256];     // D^{-1/2}
-  __shared__ double s_invd[256];   // 1 / L[k][k] (0 for dropped)
-  __shared__ int s_keep[256];
-  __shared__ int s_rank;
-  double* L = work;  // m x m row-major, lower triangle used
-  for (int i = tid; i < m; i += kCholThreads) {
-    const double g = G[i * m + i];
-    s_rs[i] = (g > 0.0 && isfinite(g)) ? rsqrt_nr(g) : 0.0;
+// CholQR factor and inverse (m <= 256) in parallel pieces: the scaled Gram, then per
+// panel of kCiNB columns a one-CTA panel factorisation in shared memory and a many-CTA
+// update of the trailing lower triangle in 4 x 4 register tiles, then the inverse
+// factor one warp per column and the upper factor R. The matrix lives in `work` (m x m
+// row-major, lower triangle used); rs (D^{-1/2}) and invd (1 / L[k][k], 0 for dropped
+// columns) in `scratch` (2 m doubles).
+constexpr int kCiNB = 32;
+
+__device__ __forceinline__ double ci_rs(double g) { return (g > 0.0 && isfinite(g)) ? rsqrt_nr(g) : 0.0; }
+
+__global__ void k_ci_scale(int m, const double* __restrict__ G, double* L, double* rs, int* rank) {
+  const int64_t mm = (int64_t)m * m;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < mm;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / m), c = (int)(idx - (int64_t)r * m);
+    L[idx] = G[idx] * ci_rs(G[(int64_t)r * m + r]) * ci_rs(G[(int64_t)c * m + c]);
+    if (idx < m) rs[idx] = ci_rs(G[idx * m + idx]);
   }
-  if (tid == 0) s_rank = 0;
-  __syncthreads();
-  for (int idx = tid; idx < m * m; idx += kCholThreads) {
-    const int r = idx / m, c = idx - r * m;
-    L[idx] = G[idx] * s_rs[r] * s_rs[c];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *rank = 0;
+}
+
+// Columns c0 .. c0 + nb - 1 (rows c0 .. m - 1) of the scaled matrix, column-major in
+// shared memory: a pivot at or below rank_tol, or a zero diagonal of G, drops its column
+// (zero column, invd 0, keep 0), which then changes nothing below.
+__global__ void __launch_bounds__(256) k_ci_panel(int m, int c0, double* L, const double* __restrict__ rs,
+                                                  double rank_tol, double* invd, int* keep, int* rank) {
+  extern __shared__ __align__(16) double pan[];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int nb = min(kCiNB, m - c0), rows = m - c0, PR = ((m + 3) & ~3) + 4;
+  __shared__ double s_inv;
+  for (int idx = tid; idx < kCiNB * PR; idx += nth) {
+    const int q = idx / PR, r = idx - q * PR;
+    pan[idx] = (q < nb && r < rows && r >= q) ? L[(int64_t)(c0 + r) * m + c0 + q] : 0.0;
   }
   __syncthreads();
-  for (int k = 0; k < m; ++k) {
+  for (int q = 0; q < nb; ++q) {
+    double* col = pan + q * PR;
     if (tid == 0) {
-      const double x = L[k * m + k];
-      const bool kp = (s_rs[k] > 0.0) && (x > rank_tol);
+      const double x = col[q];
+      const bool kp = rs[c0 + q] > 0.0 && x > rank_tol;
       const double r = kp ? rsqrt_nr(x) : 0.0;
-      L[k * m + k] = kp ? x * r : 0.0;
-      s_invd[k] = r;
-      s_keep[k] = kp;
-      s_rank += kp;
+      col[q] = kp ? x * r : 0.0;
+      invd[c0 + q] = r;
+      keep[c0 + q] = kp;
+      if (kp) atomicAdd(rank, 1);
+      s_inv = r;
     }
     __syncthreads();
-    const double inv = s_invd[k];
-    for (int i = k + 1 + tid; i < m; i += kCholThreads) L[i * m + k] *= inv;
+    const double inv = s_inv;
+    for (int r = q + 1 + tid; r < rows; r += nth) col[r] *= inv;
     __syncthreads();
-    if (inv != 0.0) {
-      const int nt = m - k - 1;
-      for (int idx = tid; idx < nt * nt; idx += kCholThreads) {
-        const int i = k + 1 + idx / nt, j = k + 1 + idx % nt;
-        if (j <= i) L[i * m + j] = fma(-L[i * m + k], L[j * m + k], L[i * m + j]);
+    if (inv != 0.0 && q + 1 < nb) {
+      const int nk = nb - 1 - q;
+      for (int idx = tid; idx < nk * rows; idx += nth) {
+        const int k = q + 1 + idx / rows, r = idx - (idx / rows) * rows;
+        if (r >= k) pan[k * PR + r] = fma(-col[r], col[k], pan[k * PR + r]);
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
-  // R = L^T D^{1/2}: R[i][j] = L[j][i] / rs[j] for j >= i (upper)
-  for (int idx = tid; idx < m * m; idx += kCholThreads) {
-    const int i = idx / m, j = idx - i * m;
-    double v = 0.0;
-    if (j >= i && s_keep[i] && s_rs[j] > 0.0) v = L[j * m + i] / s_rs[j];
-    R[idx] = v;
+  for (int idx = tid; idx < kCiNB * PR; idx += nth) {
+    const int q = idx / PR, r = idx - q * PR;
+    if (q < nb && r < rows && r >= q) L[(int64_t)(c0 + r) * m + c0 + q] = pan[idx];
   }
-  // Rinv = D^{-1/2} L^{-T}: column c of L^{-T} is row c of L^{-1}; L^{-1} by forward
-  // substitution, one unit vector per thread group (columns c in parallel)
-  __syncthreads();
-  for (int c = tid; c < m; c += kCholThreads) {
-    // column c of L^{-1}: solve L y = e_c (kept indices only), write Rinv[j][c] later
-    for (int j = 0; j < m; ++j) Rinv[j * m + c] = 0.0;
-    if (!s_keep[c]) continue;
-    // y_j for j >= c
+}
+
+// L[i][j] -= sum_q L[i][c0 + q] L[j][c0 + q] for c0 + nb <= j <= i < m, a 4 x 4 tile per thread
+__global__ void __launch_bounds__(256) k_ci_syrk(int m, int c0, int nb, double* L) {
+  const int w0 = c0 + nb, wn = m - w0;
+  const int t4 = (wn + 3) / 4, ntiles = t4 * (t4 + 1) / 2;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+    int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while (ti * (ti + 1) / 2 > t) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    const int tc = t - ti * (ti + 1) / 2;
+    const int ib = w0 + 4 * ti, cb = w0 + 4 * tc;
+    double acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int q = 0; q < nb; ++q) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = ib + u < m ? L[(int64_t)(ib + u) * m + c0 + q] : 0.0;
+        b[u] = cb + u < m ? L[(int64_t)(cb + u) * m + c0 + q] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int i = ib + u, j = cb + v;
+        if (i < m && j <= i) L[(int64_t)i * m + j] -= acc[u][v];
+      }
+  }
+}
+
+// Row c of Rinv = D^{-1/2} L^{-T}: rs[c] (L^{-1})[j][c], j >= c, from column c of L^{-1}
+// by forward substitution over the kept indices (a warp per column, lanes over the dot
+// products; dropped indices stay zero).
+__global__ void __launch_bounds__(256) k_ci_inv(int m, const double* __restrict__ L, const double* __restrict__ rs,
+                                                const double* __restrict__ invd, const int* __restrict__ keep,
+                                                double* Rinv) {
+  __shared__ double ys[8][256];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + w;
+  if (c >= m) return;
+  double* y = ys[w];
+  for (int j = lane; j < m; j += 32) y[j] = 0.0;
+  __syncwarp();
+  if (keep[c]) {
     for (int j = c; j < m; ++j) {
-      if (!s_keep[j]) continue;
-      double s = (j == c) ? 1.0 : 0.0;
-      for (int l = c; l < j; ++l) s = fma(-L[j * m + l], Rinv[l * m + c], s);  // Rinv[l][c] holds y_l
-      Rinv[j * m + c] = s * s_invd[j];
+      if (!keep[j]) continue;  // uniform across the warp
+      double s = 0.0;
+      for (int l = c + lane; l < j; l += 32) s = fma(L[(int64_t)j * m + l], y[l], s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      const double val = ((j == c ? 1.0 : 0.0) - s) * invd[j];
+      __syncwarp();
+      if (lane == 0) y[j] = val;
+      __syncwarp();
     }
   }
-  __syncthreads();
-  // now Rinv[j][c] = (L^{-1})[j][c]; Rinv_final[i][j] = rs[i] * (L^{-1})[j][i] (upper)
-  for (int idx = tid; idx < m * m; idx += kCholThreads) {
-    const int i = idx / m, j = idx - i * m;
-    work[idx] = (j >= i) ? s_rs[i] * Rinv[j * m + i] : 0.0;
+  for (int j = lane; j < m; j += 32) Rinv[(int64_t)c * m + j] = (j >= c) ? rs[c] * y[j] : 0.0;
+}
+
+// R = L^T D^{1/2}: R[i][j] = L[j][i] / rs[j] for j >= i on the kept columns
+__global__ void k_ci_r(int m, const double* __restrict__ L, const double* __restrict__ rs,
+                       const int* __restrict__ keep, double* R) {
+  const int64_t mm = (int64_t)m * m;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < mm;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / m), j = (int)(idx - (int64_t)i * m);
+    R[idx] = (j >= i && keep[i] && rs[j] > 0.0) ? L[(int64_t)j * m + i] / rs[j] : 0.0;
   }
-  __syncthreads();
-  for (int idx = tid; idx < m * m; idx += kCholThreads) Rinv[idx] = work[idx];
-  for (int i = tid; i < m; i += kCholThreads) keep[i] = s_keep[i];
-  if (tid == 0) *rank = s_rank;
 }
 
 // Band storage of the symmetric block-tridiagonal T (half-bandwidth bw, row stride ldb
@@ -523,9 +589,30 @@ cudaError_t launch_e1r0(int n, int mb, const double* R0, double* rhs, cudaStream
 }
 
 cudaError_t launch_chol_inv(int m, const double* G, double rank_tol, double* work, double* R, double* Rinv,
-                            int* keep, int* rank, cudaStream_t st) {
+                            int* keep, int* rank, double* scratch, cudaStream_t st) {
   if (m < 1 || m > 256) return cudaErrorInvalidValue;
-  k_chol_inv<<<1, kCholThreads, 0, st>>>(m, G, rank_tol, work, R, Rinv, keep, rank);
+  double* rs = scratch;
+  double* invd = scratch + m;
+  const int gmm = (int)std::min<int64_t>(((int64_t)m * m + 255) / 256, 1024);
+  k_ci_scale<<<gmm, 256, 0, st>>>(m, G, work, rs, rank);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)kCiNB * (((m + 3) & ~3) + 4) * 8;
+  if ((e = cudaFuncSetAttribute(k_ci_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  for (int c0 = 0; c0 < m; c0 += kCiNB) {
+    const int nb = std::min(kCiNB, m - c0);
+    k_ci_panel<<<1, 256, smem, st>>>(m, c0, work, rs, rank_tol, invd, keep, rank);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (c0 + nb < m) {
+      const int t4 = (m - c0 - nb + 3) / 4, ntiles = t4 * (t4 + 1) / 2;
+      k_ci_syrk<<<(ntiles + 255) / 256, 256, 0, st>>>(m, c0, nb, work);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  k_ci_inv<<<(m + 7) / 8, 256, 0, st>>>(m, work, rs, invd, keep, Rinv);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_ci_r<<<gmm, 256, 0, st>>>(m, work, rs, keep, R);
   return cudaGetLastError();
 }
 
