@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--sample-inner", default="ozaki", choices=["ozaki", "f32x2", "fp32", "fp64"])
     ap.add_argument("--sample-nugget", type=float, default=None)
     ap.add_argument("--sample-operator", default="stored", choices=["stored", "rbf"])
+    ap.add_argument("--sample-only", action="store_true",
+                    help="sampling leg: only the timed calls (no profiled, inverse-square-root or other-mode call)")
     ap.add_argument("--dense-d", type=int, default=16384)
     ap.add_argument("--dense-m", type=int, default=33)
     ap.add_argument("--batch", type=int, default=512)
@@ -857,6 +859,14 @@ def run_sample(args, world, rank, local, dev):
         ev1.record(stream)
         torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1) / args.steps
+    if args.sample_only:
+        if rank == 0:
+            print(json.dumps({"metric": "samples/s, (K + nugget I)^{1/2} B by block-Lanczos quadrature (32 shifts)",
+                              "value": world * m / (ms / 1e3), "unit": "samples/s", "ms_per_step": ms,
+                              "steps": args.steps, "loads": [i.loads for i in infos],
+                              "inner": args.sample_inner, "note": "--sample-only: timed calls only"}), flush=True)
+        ctx.close()
+        return 0
     pinfo = call(opts(profile=1))
     # the inverse square root on the same basis, shifts and weights (one timed call)
     with torch.cuda.stream(stream):

@@ -890,14 +890,22 @@ bk_status sample_driver(bk_ctx* c, const bk_operator* Kop, double nugget, int32_
     }
     // Ybar = sum_j w_j Y_j; S = Q_t (T_t + nugget) Ybar + Q_{t+1} B_t E_t^T Ybar
     BK_CK(bk::launch_combine_shifts(n, m, N, Z, dw, Ybar, st));
+    // the basis products of the combination (d x m from the d x n basis) go through the
+    // Ozaki split in Ozaki runs, FP64 GEMMs otherwise
+    auto basis_gemm = [&](int64_t M_, int64_t N_, int64_t K_, const void* A_, int64_t sai, int64_t sak,
+                          const double* B_, int64_t sbk, int64_t sbj, double beta_, double* C_,
+                          int64_t ldc_) -> cudaError_t {
+      if (oz) return lz.gemm_k(1, M_, N_, K_, 1.0, A_, is64, sai, sak, B_, sbk, sbj, beta_, C_, ldc_, false);
+      return bk::launch_gemm(1, M_, N_, K_, 1.0, A_, is64, sai, sak, B_, sbk, sbj, beta_, C_, ldc_, st);
+    };
     if (inverse) {
-      BK_CK(bk::launch_gemm(1, d, m, n, 1.0, lz.Q, is64, 1, lz.ldq, Ybar, 1, n, 0.0, Sd, d, st));
+      BK_CK(basis_gemm(d, m, n, lz.Q, 1, lz.ldq, Ybar, 1, n, 0.0, Sd, d));
     } else {
       BK_CK(bk::launch_band_mult(n, m, lz.band, lz.ldb(), nugget, Ybar, m, M1, st));
-      BK_CK(bk::launch_gemm(1, d, m, n, 1.0, lz.Q, is64, 1, lz.ldq, M1, 1, n, 0.0, Sd, d, st));
+      BK_CK(basis_gemm(d, m, n, lz.Q, 1, lz.ldq, M1, 1, n, 0.0, Sd, d));
       // small = B_t (rows n-m.. of Ybar): B_t row-major m x m, Ybar rows n-m..n-1 (ld n)
       BK_CK(bk::launch_gemm(1, m, m, m, 1.0, lz.Bk, 1, m, 1, Ybar + (n - m), 1, n, 0.0, small, m, st));
-      BK_CK(bk::launch_gemm(1, d, m, m, 1.0, lz.qblock(lz.t), is64, 1, lz.ldq, small, 1, m, 1.0, Sd, d, st));
+      BK_CK(basis_gemm(d, m, m, lz.qblock(lz.t), 1, lz.ldq, small, 1, m, 1.0, Sd, d));
     }
     // relative change against the previous check (a-posteriori stopping, Sec. 4 remark)
     int np = bk::residual_parts(d * m);
