@@ -374,11 +374,14 @@ bk_status bk_solve_batched(bk_ctx* ctx, int32_t n, const bk_operator* A, const d
 /* Chooses the sketch size per size bucket (floor(log2 d)) from timed calibration
  * solves and stores the table in the context; bk_solve_batched uses it when
  * opts->sketch = -1. A candidate whose block width the kernels are not built for
- * (bk_solve_batched: BK_ERR_UNSUPPORTED) is skipped. With FP32 blocks the bucket's
- * block-product kernel is chosen too: for the winning sketch, the CUDA-core product
- * (16-row x 64-column tiles through shared memory) is timed against the tensor-core
- * product (128-row tiles, TMA ring, split TF32) and the faster one is kept. The calibration systems of each bucket are solved together with
- * bk_solve_batched, repeated in one batch until it streams about 1 GB of matrix per
+ * (bk_solve_batched: BK_ERR_UNSUPPORTED) is skipped. For the winning sketch the
+ * bucket's block-product kernel and tile shape are chosen too: the default (the
+ * tensor-core product, 128-row tiles, TMA ring, split TF32, for FP32 blocks at widths
+ * it is built for; else the CUDA-core product with 16-row x 64-column tiles through
+ * shared memory) is timed against the other choices (the CUDA-core product with 16-row
+ * and with 32-row tiles) and the fastest is kept. The calibration systems of each
+ * bucket are solved together with bk_solve_batched, repeated in one batch until it
+ * streams about 1 GB of matrix per
  * block product (at most 64 copies), so the timing reflects throughput inside a large
  * batch; each candidate is timed as the best of three solves after a warm one, and
  * the fastest candidate that converges on every system wins. Calibrate on systems
@@ -388,8 +391,9 @@ bk_status bk_autotune(bk_ctx* ctx, int32_t n, const bk_operator* A, const double
                       const int32_t* candidates, int32_t ncand, const bk_opts* opts, int32_t* chosen);
 
 /* The autotune table of a context as a text file (one line per size bucket:
- * floor(log2 d), sketch, product kernel 1 = tensor-core / 0 = CUDA-core), so that a
- * calibration can be reused by later contexts and processes. bk_autotune_load replaces
+ * floor(log2 d), sketch, product kernel 1 = tensor-core, 0 = CUDA-core with 16-row
+ * tiles, 2 = CUDA-core with 32-row tiles), so that a calibration can be reused by
+ * later contexts and processes. bk_autotune_load replaces
  * the context's table with the file's; it returns BK_ERR_ARG (table unchanged) for a
  * file it cannot open or a malformed line. Host-only calls. */
 bk_status bk_autotune_save(const bk_ctx* ctx, const char* path);

@@ -479,7 +479,7 @@ def autotune_table(ctx: Context, path: str) -> dict:
             if line.startswith("#") or not line.strip():
                 continue
             bkt, sk, tc = (int(v) for v in line.split())
-            table[bkt] = (sk, "tensor" if tc else "cuda")
+            table[bkt] = (sk, {0: "cuda", 1: "tensor", 2: "cuda32"}[tc])
     return table
 
 

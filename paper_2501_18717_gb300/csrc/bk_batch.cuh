@@ -49,9 +49,10 @@ cudaError_t launch_batch_dense_tc(int mp, BSys* sys, const int* cta_sys, int nct
 cudaError_t tc_make_maps(int mp, int64_t d, const float* A, int64_t lda, const float* pt, void* out);
 
 // One block-CG step for every system of a group with padded width mp (tc: the group's
-// tensor-core product, or null for the FFMA product).
+// tensor-core product, or null for the FFMA product, whose row tiles are tile_rows = 16
+// or 32 rows per thread block).
 cudaError_t launch_batch_step(int is_f64, int vals_f64, int mp, BSys* sys, int nsys, const int* cta_sys, int ncta,
-                              double rank_tol, const BatchTc* tc, cudaStream_t st);
+                              double rank_tol, const BatchTc* tc, int tile_rows, cudaStream_t st);
 // Start blocks of the active systems (Q = [r/||r||, Omega/sqrt(d)] normalised, P = Q,
 // c = T e_1); resets their control blocks.
 cudaError_t launch_batch_start(int is_f64, int mp, BSys* sys, int nsys, const int* cta_sys, int ncta, uint64_t seed,

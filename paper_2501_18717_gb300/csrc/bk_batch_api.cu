@@ -29,8 +29,10 @@ struct Group {
   int* cta_sys = nullptr;    // device copy of hcta
   int ncta = 0;
   cudaGraphExec_t gexec = nullptr;
-  // tensor-core block product (all systems of the group qualify)
+  // tensor-core block product (all systems of the group qualify); otherwise the FFMA
+  // product with row tiles of tile_rows rows
   bool tc = false;
+  int tile_rows = 16;
   std::vector<int> htile;        // tile_sys then tile_row
   std::vector<CUtensorMap> hmaps;  // two per system
   bk::BatchTc btc;
@@ -85,7 +87,8 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
   if (infos) std::memset(infos, 0, sizeof(bk_info) * n);
 
   // block width per system: fixed sketch, or the autotune table (nearest size bucket)
-  // and the block-product kernel per system (1: tensor cores where usable, 0: CUDA cores)
+  // and the block-product kernel per system (kernel codes: 1 tensor cores where usable,
+  // 0 CUDA cores with 16-row tiles, 2 CUDA cores with 32-row tiles)
   std::vector<int> ms(n), want_tc(n, 1);
   for (int i = 0; i < n; ++i) {
     int l = opts.sketch;
@@ -104,9 +107,9 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
     ms[i] = (int)std::min<int64_t>((int64_t)l + 1, A[i].rows);
     if (bk::padded_width(ms[i]) < 0) return BK_ERR_UNSUPPORTED;
   }
-  // groups by padded width and product kernel (key 2 mp + kernel)
+  // groups by padded width and product kernel (key 4 mp + kernel code)
   std::map<int, Group> groups;
-  for (int i = 0; i < n; ++i) groups[2 * bk::padded_width(ms[i]) + want_tc[i]].members.push_back(i);
+  for (int i = 0; i < n; ++i) groups[4 * bk::padded_width(ms[i]) + want_tc[i]].members.push_back(i);
 
   const size_t es = is64 ? 8 : 4;
   const size_t vs = vals_f64 ? 8 : 4;
@@ -142,11 +145,12 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
   int total_cta = 0;
   for (auto& kv : groups) {
     Group& g = kv.second;
-    g.mp = kv.first / 2;
+    g.mp = kv.first / 4;
     glist.push_back(&g);
+    g.tile_rows = (kv.first & 3) == 2 ? 32 : 16;
     // the tensor-core product needs FP32 values with 16-byte aligned rows (host values
     // are staged to 256-byte aligned buffers with the caller's lda)
-    g.tc = !is64 && (kv.first & 1);
+    g.tc = !is64 && (kv.first & 3) == 1;
     for (int i : g.members) {
       const bool dev = bkx::is_device_ptr(A[i].vals);
       const void* probe = dev ? A[i].vals : reinterpret_cast<const void*>(uintptr_t(256));
@@ -334,7 +338,7 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
             cudaError_t ce = cudaSuccess;
             for (int it = 0; it < opts.check_every && ce == cudaSuccess; ++it)
               ce = bk::launch_batch_step(is64, vals_f64, g->mp, g->ds, (int)g->hs.size(), g->cta_sys, g->ncta,
-                                         rank_tol, g->tc ? &g->btc : nullptr, st);
+                                         rank_tol, g->tc ? &g->btc : nullptr, g->tile_rows, st);
             cudaError_t ee = cudaStreamEndCapture(st, &graph);
             BK_CKG(ce);
             BK_CKG(ee);
@@ -346,7 +350,7 @@ extern "C" bk_status bk_solve_batched(bk_ctx* c, int32_t n, const bk_operator* A
         } else {
           for (int it = 0; it < opts.check_every; ++it)
             BK_CKG(bk::launch_batch_step(is64, vals_f64, g->mp, g->ds, (int)g->hs.size(), g->cta_sys, g->ncta,
-                                         rank_tol, g->tc ? &g->btc : nullptr, st));
+                                         rank_tol, g->tc ? &g->btc : nullptr, g->tile_rows, st));
         }
       }
       BK_CKG(cudaMemcpyAsync(hst.data(), dstates, sizeof(bk::DevState) * n, cudaMemcpyDeviceToHost, st));
@@ -560,16 +564,18 @@ extern "C" bk_status bk_autotune(bk_ctx* c, int32_t n, const bk_operator* A, con
     }
     if (best_k < 0) continue;
     c->tune[kv.first] = candidates[best_k];
-    const bool tc_built = bk::padded_width(candidates[best_k] + 1) <= bk::kTcMaxPadded;
-    c->tune_tc[kv.first] = tc_built ? 1 : 0;
-    // product kernel of the winning width: the CUDA-core product timed the same way
-    // (FP32 blocks; the tensor-core product is the default where the rows qualify and
-    // the width is one it is built for)
-    if (opts.inner == BK_PREC_FP32 && tc_built) {
+    // product kernel and tile shape of the winning width: the default (tensor cores for
+    // FP32 blocks where the width is one they are built for, else 16-row FFMA tiles)
+    // against the other kernels, timed the same way
+    const bool tc_built = opts.inner == BK_PREC_FP32 && bk::padded_width(candidates[best_k] + 1) <= bk::kTcMaxPadded;
+    const int def = tc_built ? 1 : 0;
+    c->tune_tc[kv.first] = def;
+    for (int kern : {0, 1, 2}) {
+      if (kern == def || (kern == 1 && !tc_built)) continue;
       bk_opts o = opts;
       o.sketch = candidates[best_k];
       double t = INFINITY;
-      c->force_tc = 0;
+      c->force_tc = kern;
       for (int rep = 0; rep < 4; ++rep) {
         bk_status s = bk_solve_batched(c, nb, ops.data(), mus.data(), bs.data(), xp.data(), &o, infos.data());
         if (s != BK_OK) {
@@ -583,7 +589,10 @@ extern "C" bk_status bk_autotune(bk_ctx* c, int32_t n, const bk_operator* A, con
         if (rep > 0) t = std::min(t, (double)infos[0].ms_total);
       }
       c->force_tc = -1;
-      if (t < best_t) c->tune_tc[kv.first] = 0;
+      if (t < best_t) {
+        best_t = t;
+        c->tune_tc[kv.first] = kern;
+      }
     }
   }
   if (chosen)
@@ -598,7 +607,8 @@ extern "C" bk_status bk_autotune_save(const bk_ctx* c, const char* path) {
   if (!c || !path) return BK_ERR_ARG;
   FILE* f = std::fopen(path, "w");
   if (!f) return BK_ERR_ARG;
-  std::fprintf(f, "# bk autotune table: floor(log2 d) sketch product(1 tensor-core, 0 cuda-core)\n");
+  std::fprintf(f, "# bk autotune table: floor(log2 d) sketch product(1 tensor-core, 0 cuda-core 16-row tiles, "
+                 "2 cuda-core 32-row tiles)\n");
   for (auto& kv : c->tune) {
     auto it = c->tune_tc.find(kv.first);
     std::fprintf(f, "%d %d %d\n", kv.first, kv.second, it == c->tune_tc.end() ? 1 : it->second);
@@ -617,7 +627,7 @@ extern "C" bk_status bk_autotune_load(bk_ctx* c, const char* path) {
   while (std::fgets(line, sizeof(line), f)) {
     if (line[0] == '#' || line[0] == '\n') continue;
     int bkt = 0, sk = 0, tc = 1;
-    if (std::sscanf(line, "%d %d %d", &bkt, &sk, &tc) != 3 || bkt < 0 || bkt > 62 || sk < 1 || (tc != 0 && tc != 1)) {
+    if (std::sscanf(line, "%d %d %d", &bkt, &sk, &tc) != 3 || bkt < 0 || bkt > 62 || sk < 1 || tc < 0 || tc > 2) {
       st = BK_ERR_ARG;
       break;
     }

@@ -471,9 +471,9 @@ __global__ void __launch_bounds__(256) k_bresid(BSys* __restrict__ sys, const in
   }
 }
 
-template <typename T, int MP>
+template <typename T, int MP, int TMD>
 size_t bop_smem() {
-  constexpr int TMD = 16, KC = 64, NTH = 128;
+  constexpr int KC = 64, NTH = 128;
   size_t main = (size_t)(TMD * (KC + 1) + KC * MP + 2 * TMD * MP) * sizeof(T);
   size_t red = (size_t)gram_phases<MP>(NTH) * GramShape<MP>::NE * sizeof(double);
   return main > red ? main : red;
@@ -491,20 +491,28 @@ cudaError_t small_attrs() {
   return e;
 }
 
+template <typename T, typename VA, int MP, int TMD>
+cudaError_t bop_launch(BSys* sys, const int* cta_sys, int ncta, cudaStream_t st) {
+  auto k = k_bop<T, VA, MP, TMD, 64, 128>;
+  const size_t sm = bop_smem<T, MP, TMD>();
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k<<<ncta, 128, sm, st>>>(sys, cta_sys);
+  return cudaGetLastError();
+}
+
 template <typename T, typename VA, int MP>
 cudaError_t step_impl(BSys* sys, int nsys, const int* cta_sys, int ncta, double rank_tol, const BatchTc* tc,
-                      cudaStream_t st) {
+                      int tile_rows, cudaStream_t st) {
   cudaError_t e;
   if ((e = small_attrs<T, MP>()) != cudaSuccess) return e;
-  if (tc) {
-    if ((e = launch_batch_dense_tc(MP, sys, cta_sys, ncta, *tc, st)) != cudaSuccess) return e;
-  } else {
-    auto k = k_bop<T, VA, MP, 16, 64, 128>;
-    size_t sm = bop_smem<T, MP>();
-    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess) return e;
-    k<<<ncta, 128, sm, st>>>(sys, cta_sys);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  if (tc)
+    e = launch_batch_dense_tc(MP, sys, cta_sys, ncta, *tc, st);
+  else if (tile_rows == 32)
+    e = bop_launch<T, VA, MP, 32>(sys, cta_sys, ncta, st);
+  else
+    e = bop_launch<T, VA, MP, 16>(sys, cta_sys, ncta, st);
+  if (e != cudaSuccess) return e;
   k_bsmall<T, MP><<<nsys, kBSmall, bsmall_smem<MP>(), st>>>(sys, 0, rank_tol);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {
@@ -541,14 +549,17 @@ cudaError_t start_impl(BSys* sys, int nsys, const int* cta_sys, int ncta, uint64
 }  // namespace
 
 cudaError_t launch_batch_step(int is_f64, int vals_f64, int mp, BSys* sys, int nsys, const int* cta_sys, int ncta,
-                              double rank_tol, const BatchTc* tc, cudaStream_t st) {
+                              double rank_tol, const BatchTc* tc, int tile_rows, cudaStream_t st) {
   if (!is_f64 && vals_f64) return cudaErrorInvalidValue;  // FP32 blocks take FP32 values
   if (tc && is_f64) return cudaErrorInvalidValue;          // the tensor-core product is FP32
-#define BK_B(MPV)                                                                                           \
-  case MPV:                                                                                                 \
-    return is_f64 ? (vals_f64 ? step_impl<double, double, MPV>(sys, nsys, cta_sys, ncta, rank_tol, nullptr, st) \
-                              : step_impl<double, float, MPV>(sys, nsys, cta_sys, ncta, rank_tol, nullptr, st))  \
-                  : step_impl<float, float, MPV>(sys, nsys, cta_sys, ncta, rank_tol, tc, st);
+  if (tile_rows != 16 && tile_rows != 32) return cudaErrorInvalidValue;
+#define BK_B(MPV)                                                                                        \
+  case MPV:                                                                                              \
+    return is_f64 ? (vals_f64 ? step_impl<double, double, MPV>(sys, nsys, cta_sys, ncta, rank_tol, nullptr, \
+                                                               tile_rows, st)                            \
+                              : step_impl<double, float, MPV>(sys, nsys, cta_sys, ncta, rank_tol, nullptr,  \
+                                                              tile_rows, st))                             \
+                  : step_impl<float, float, MPV>(sys, nsys, cta_sys, ncta, rank_tol, tc, tile_rows, st);
   switch (mp) {
     BK_B(4)
     BK_B(8)

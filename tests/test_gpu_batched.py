@@ -141,6 +141,31 @@ def test_fp32_width65_falls_back_to_fp64_blocks(bk, ctx):
     assert infos[6].loads < 1000, infos[6].as_dict()
 
 
+@pytest.mark.parametrize("inner,tol", [("fp32", 1e-8), ("fp64", 1e-10)])
+def test_batched_product_tile_shapes(bk, ctx, tmp_path, inner, tol):
+    """The three block-product choices of the autotune table (tensor cores, CUDA cores
+    with 16-row and with 32-row tiles) loaded for one bucket each: every system meets
+    tol in the oracle's FP64 residual, and the two CUDA-core tile shapes give the same
+    solutions to the forward error that residual allows (kappa <= 1e5: 2 kappa tol)."""
+    seed = W.BASE_SEED + 45
+    ds, mats, bs = make_batch(seed, 6, 300, 1200)
+    xs = {}
+    for kern in (0, 1, 2):
+        (tmp_path / "t.txt").write_text("".join(f"{b} 16 {kern}\n" for b in range(8, 12)))
+        with bk.Context(0) as c2:
+            bk.autotune_load(c2, tmp_path / "t.txt")
+            x = [np.zeros(d) for d in ds]
+            infos = bk.solve_batched(c2, bk.Batch(mats, np.zeros(len(ds)), bs, x),
+                                     bk.default_opts(tol=tol, sketch=-1, seed=3, inner=inner,
+                                                     inner_tol=1e-5 if inner == "fp32" else 1e-6))
+        for i in range(len(ds)):
+            assert infos[i].status == bk.BK_OK, (kern, i, infos[i].as_dict())
+            assert rel_res(mats[i], x[i], bs[i]) <= tol, (kern, i)
+        xs[kern] = x
+    for i in range(len(ds)):
+        assert np.linalg.norm(xs[0][i] - xs[2][i]) <= 2e5 * tol * np.linalg.norm(xs[0][i]), i
+
+
 def test_batched_host_and_device_agree(bk, ctx):
     seed = W.BASE_SEED + 41
     ds, mats, bs = make_batch(seed, 4, 300, 600)
@@ -196,7 +221,7 @@ def test_autotune_table(bk, ctx, tmp_path):
     chosen = bk.autotune(ctx, cal, [8, 16, 32, 64, 80], bk.default_opts(tol=1e-8, inner="fp32", inner_tol=1e-5))
     assert set(chosen.tolist()) <= {8, 16, 32, 64}
     table = bk.autotune_table(ctx, tmp_path / "tune.txt")
-    assert table and all(sk in (8, 16, 32, 64) and kern in ("tensor", "cuda") for sk, kern in table.values())
+    assert table and all(sk in (8, 16, 32, 64) and kern in ("tensor", "cuda", "cuda32") for sk, kern in table.values())
     # a fresh batch solved with sketch = -1 uses the table and converges
     ds2, mats2, bs2 = make_batch(seed + 100, 4, 300, 1200)
     xs2 = [np.zeros(d) for d in ds2]
