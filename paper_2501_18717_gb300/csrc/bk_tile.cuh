@@ -28,6 +28,12 @@ struct GramShape {
   static constexpr int NE = NT * 16;
 };
 
+// Phases of the Gram accumulation in a block of `threads` (1 when blocks outnumber threads).
+template <int MP>
+__host__ __device__ constexpr int gram_phases(int threads) {
+  return threads / GramShape<MP>::NT > 0 ? threads / GramShape<MP>::NT : 1;
+}
+
 // Blocks per thread for a kernel launched with NTH threads per block.
 template <int MP, int NTH>
 __host__ __device__ constexpr int gram_bpt() {
@@ -115,6 +121,39 @@ struct GramAcc<float, MP, BPT> {
     }
   }
 
+  // tile() for a block of exactly NPH phases (one Gram block per thread) and a tile of
+  // ROWS rows: the same rows in the same order, with a compile-time stride so the row
+  // loop unrolls and the next rows' loads issue ahead of the multiply-adds.
+  template <int ROWS, int NPH>
+  __device__ void tile_fixed(const float* sX, const float* sY) {
+    static_assert(BPT == 1, "one Gram block per thread");
+    if (!active) return;
+    constexpr int IT = ROWS / NPH;
+    float acc[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[e] = 0.f;
+    auto row = [&](int r) {
+      float4 x = *reinterpret_cast<const float4*>(sX + r * MP + 4 * bi[0]);
+      float4 y = *reinterpret_cast<const float4*>(sY + r * MP + 4 * bj[0]);
+      float xa[4] = {x.x, x.y, x.z, x.w};
+      float yb[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a * 4 + b] = fmaf(xa[a], yb[b], acc[a * 4 + b]);
+    };
+#pragma unroll 8
+    for (int it = 0; it < IT; ++it) row(ph + it * NPH);
+    if (ph < ROWS - IT * NPH) row(ph + IT * NPH);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      float s, err;
+      two_sum(hi[0][e], acc[e], s, err);
+      hi[0][e] = s;
+      lo[0][e] = __fadd_rn(lo[0][e], err);
+    }
+  }
+
   __device__ double value(int k, int e) const { return (double)hi[k][e] + (double)lo[k][e]; }
 };
 
@@ -170,6 +209,16 @@ struct GramAcc<double, MP, BPT> {
 
   __device__ double value(int k, int e) const { return hi[k][e]; }
 };
+
+// One tile of ROWS rows in a block of NTH threads: FP32 Grams with one block per thread
+// take the fixed-stride loop, the others the general one (same rows, same order).
+template <int ROWS, int NTH, typename T, int MP, int BPT>
+__device__ __forceinline__ void gram_tile(GramAcc<T, MP, BPT>& g, const T* sX, const T* sY) {
+  if constexpr (sizeof(T) == 4 && BPT == 1 && GramShape<MP>::NT <= NTH)
+    g.template tile_fixed<ROWS, gram_phases<MP>(NTH)>(sX, sY);
+  else
+    g.tile(sX, sY, ROWS);
+}
 
 // Combine the phases of one CTA (fixed order) and write the CTA partial:
 // parts[e * nparts + cta] for e in [0, NE). sred needs nph * NT * 16 doubles and may
@@ -265,11 +314,6 @@ __device__ __forceinline__ void st4(double* p, const double* v) {
   reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
 
-// Phases of the Gram accumulation in a block of `threads` (1 when blocks outnumber threads).
-template <int MP>
-__host__ __device__ constexpr int gram_phases(int threads) {
-  return threads / GramShape<MP>::NT > 0 ? threads / GramShape<MP>::NT : 1;
-}
 
 // Shared bytes a Gram-fused kernel needs: two tiles of TM rows, or the phase buffer.
 template <typename T, int MP>

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(NTH) k_bop(const BSys* __restrict__ sys, const
       }
     }
     __syncthreads();
-    g.tile(sX, sY, TMD);
+    gram_tile<TMD, NTH>(g, sX, sY);
     __syncthreads();
   }
   gram_finish<T, MP>(g, reinterpret_cast<double*>(smem_raw), S.Gp, S.ncta, j);
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(TM) k_bupd_r(const BSys* __restrict__ sys, con
     }
     store_row<MP>(sX, threadIdx.x, acc);
     __syncthreads();
-    g.tile(sX, sX, TM);
+    gram_tile<TM, TM>(g, sX, sX);
     __syncthreads();
   }
   gram_finish<T, MP>(g, reinterpret_cast<double*>(smem_raw + ((MP * MP * sizeof(T) + 15) / 16) * 16), S.Sp,
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(TM) k_bgram_r(const BSys* __restrict__ sys, co
     }
     store_row<MP>(sX, threadIdx.x, v);
     __syncthreads();
-    g.tile(sX, sX, TM);
+    gram_tile<TM, TM>(g, sX, sX);
     __syncthreads();
   }
   gram_finish<T, MP>(g, reinterpret_cast<double*>(smem_raw), S.Sp, S.ncta, j);

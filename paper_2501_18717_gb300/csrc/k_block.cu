@@ -340,8 +340,9 @@ __global__ void __launch_bounds__(UpdRShape<MP>::TH)
       }
     }
     __syncthreads();
+    // columns m..MP-1 of Y are zero: the product stops at m
 #pragma unroll 4
-    for (int k = 0; k < MP; ++k) {
+    for (int k = 0; k < m; ++k) {
       T yk[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) yk[u] = sY[k * LDY + rg + 32 * u];
@@ -381,7 +382,7 @@ __global__ void __launch_bounds__(UpdRShape<MP>::TH)
       }
     }
     __syncthreads();
-    g.tile(sX, sX, TM);
+    gram_tile<TM, U::TH>(g, sX, sX);
     __syncthreads();
   }
   // the phase buffer of the Gram reduction aliases the tiles after alpha

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(TM, (csr_blocks<T, MP>()))
       }
     }
     __syncthreads();
-    g.tile(sX, sY, TM);
+    gram_tile<TM, TM>(g, sX, sY);
     __syncthreads();
   }
   gram_finish<T, MP>(g, reinterpret_cast<double*>(smem_raw), parts, nparts, blockIdx.x);

@@ -388,7 +388,7 @@ __device__ __forceinline__ void dense_tc_tile(const CUtensorMap* amap_p, const C
   if (warp == 1) tmem_dealloc(tmem, SH::kTmemCols);
   GramAcc<float, MP> g;
   g.init();
-  g.tile(sX, sY, 128);
+  gram_tile<128, kTcThreads>(g, sX, sY);
   __syncthreads();
   gram_finish<float, MP>(g, reinterpret_cast<double*>(base), parts, nparts, tile);
 }
