@@ -389,6 +389,134 @@ __global__ void __launch_bounds__(UpdRShape<MP>::TH)
   gram_finish<T, MP>(g, reinterpret_cast<double*>(smem_raw + SM::A_B), parts, nparts, blockIdx.x);
 }
 
+// FP32 residual update at widths up to 36 with the next tile in flight: the Y tile is
+// kept in shared memory in the panel layout (row r of panel q as one 16-byte slot),
+// copied there by cp.async (no registers held), and each thread's rows of R go straight
+// into its accumulators. Both are issued for tile n + 1 right after the W rows of tile
+// n are stored, so the Gram of tile n covers their latency (the accumulators are dead
+// during it). The product, its order and the Gram are those of k_update_r.
+template <int MP>
+struct UpdRPf {
+  static constexpr size_t A_B = ((size_t)MP * MP * 4 + 15) / 16 * 16;
+  static constexpr size_t Y_B = (size_t)(MP / 4) * UpdRShape<MP>::TM * 16;
+  static constexpr size_t X_B = (size_t)UpdRShape<MP>::TM * MP * 4;
+  static constexpr size_t RED_B = (size_t)gram_phases<MP>(UpdRShape<MP>::TH) * GramShape<MP>::NE * 8;
+  static constexpr size_t TOTAL = A_B + (Y_B + X_B > RED_B ? Y_B + X_B : RED_B);
+};
+
+template <int MP>
+__global__ void __launch_bounds__(UpdRShape<MP>::TH)
+    k_update_r_pf(int64_t d, int m, const float* __restrict__ Y, float* __restrict__ R, int64_t ld,
+                  const float* __restrict__ alpha_t, double* parts, int nparts, const DevState* state) {
+  if (is_done(state)) return;
+  using U = UpdRShape<MP>;
+  using SM = UpdRPf<MP>;
+  constexpr int TM = U::TM, CPT = U::CPT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sA = reinterpret_cast<float*>(smem_raw);                        // MP x MP: row k = alpha(k, :)
+  float4* sYp = reinterpret_cast<float4*>(smem_raw + SM::A_B);           // panel q, row r at q * TM + r
+  float* sX = reinterpret_cast<float*>(smem_raw + SM::A_B + SM::Y_B);    // TM x MP: new R rows
+  for (int idx = threadIdx.x; idx < MP * MP; idx += blockDim.x) sA[idx] = alpha_t[idx];
+  const int rg = threadIdx.x & 31, cg = threadIdx.x >> 5, c0 = cg * CPT;
+  GramAcc<float, MP, gram_bpt<MP, U::TH>()> g;
+  g.init();
+  const int64_t ntiles = (d + TM - 1) / TM;
+  float acc[4][CPT];
+  auto issue = [&](int64_t tile) {
+    const int64_t i0 = tile * TM;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + rg + 32 * u;
+      const bool ok = i < d;
+      const int64_t ii = ok ? i : 0;
+#pragma unroll
+      for (int pi = 0; pi < CPT / 4; ++pi) {
+        const int q = c0 / 4 + pi;
+        if (4 * q < m) {  // Y rows past d land as zeros
+          upd_cp16(sYp + q * TM + rg + 32 * u, panel_row(Y, ld, q, ii), ok ? 16 : 0);
+          if (ok)
+            ld4(panel_row(R, ld, q, i), acc[u] + 4 * pi);
+          else {
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[u][4 * pi + w] = 0.f;
+          }
+        } else {
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc[u][4 * pi + w] = 0.f;
+        }
+      }
+    }
+    upd_cp_commit();
+  };
+  if (blockIdx.x < ntiles) issue(blockIdx.x);
+  const int nq = (m + 3) >> 2;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t i0 = tile * TM;
+    upd_cp_wait0();
+    __syncthreads();  // the Y tile (and alpha) visible; every thread's previous Gram is done
+    // k over the full panels (no branch), then the live columns of the last panel:
+    // columns m..MP-1 of Y are zero, so the product stops at m
+    auto step = [&](int k, const float (&yk)[4]) {
+      float a[CPT];
+#pragma unroll
+      for (int j4 = 0; j4 < CPT / 4; ++j4) {
+        const float4 v = *reinterpret_cast<const float4*>(sA + k * MP + c0 + 4 * j4);
+        a[4 * j4] = v.x;
+        a[4 * j4 + 1] = v.y;
+        a[4 * j4 + 2] = v.z;
+        a[4 * j4 + 3] = v.w;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) acc[u][j] = fmaf(-yk[u], a[j], acc[u][j]);
+    };
+    auto panel = [&](int q, float (&y4)[4][4]) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 v = sYp[q * TM + rg + 32 * u];
+        y4[0][u] = v.x;
+        y4[1][u] = v.y;
+        y4[2][u] = v.z;
+        y4[3][u] = v.w;
+      }
+    };
+    const int qf = m >> 2;
+#pragma unroll 2
+    for (int q = 0; q < qf; ++q) {
+      float y4[4][4];
+      panel(q, y4);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) step(4 * q + w, y4[w]);
+    }
+    if (qf < nq) {
+      float y4[4][4];
+      panel(qf, y4);
+#pragma unroll
+      for (int w = 0; w < 4; ++w)
+        if (4 * qf + w < m) step(4 * qf + w, y4[w]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int row = rg + 32 * u;
+      const int64_t i = i0 + row;
+#pragma unroll
+      for (int pi = 0; pi < CPT / 4; ++pi) {
+        const int q = c0 / 4 + pi;
+        if (i < d && 4 * q < m) st4(panel_row(R, ld, q, i), acc[u] + 4 * pi);
+        float v4[4] = {acc[u][4 * pi], acc[u][4 * pi + 1], acc[u][4 * pi + 2], acc[u][4 * pi + 3]};
+        store4<MP>(sX, row, q, v4);
+      }
+    }
+    __syncthreads();  // sX complete; every thread is done reading the Y tile
+    if (tile + gridDim.x < ntiles) issue(tile + gridDim.x);
+    gram_tile<TM, U::TH>(g, sX, sX);
+  }
+  __syncthreads();
+  // the phase buffer of the Gram reduction aliases the tiles after alpha
+  gram_finish<float, MP>(g, reinterpret_cast<double*>(smem_raw + SM::A_B), parts, nparts, blockIdx.x);
+}
+
 // x += P xc; unless the solve just ended, Q = W T^{-1} (W is held in Q) and
 // P = Q + P T^T (P = Q on the first call of an inner solve, which only normalises the
 // start block); the row loop is update_pq_rows.
@@ -556,6 +684,15 @@ cudaError_t gram_impl(int64_t d, const void* X, const void* Y, int64_t ld, int m
 template <typename T, int MP>
 cudaError_t update_r_impl(int64_t d, int m, const void* Y, void* R, int64_t ld, const void* alpha_t, double* parts,
                           int nparts, const DevState* state, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4 && MP <= 36) {
+    const size_t smem = UpdRPf<MP>::TOTAL;
+    auto kern = k_update_r_pf<MP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<nparts, UpdRShape<MP>::TH, smem, st>>>(d, m, (const float*)Y, (float*)R, ld, (const float*)alpha_t,
+                                                  parts, nparts, state);
+    return cudaGetLastError();
+  }
   const size_t smem = UpdRSmem<T, MP>::TOTAL;
   auto kern = k_update_r<T, MP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

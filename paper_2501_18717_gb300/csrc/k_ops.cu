@@ -55,22 +55,30 @@ __global__ void __launch_bounds__(TM, (csr_blocks<T, MP>()))
   const int t = threadIdx.x;
   const int nq = (m + 3) >> 2;
   int64_t ntiles = (d + TM - 1) / TM;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  // The row's nonzeros for a tile. Those of the next tile are read before the Gram of
+  // the current one, so the dependent rowptr -> colidx loads leave the tile's start.
+  int k0 = 0, nz = 0;
+  T v[KMAX];
+  int off[KMAX];
+  auto load_row = [&](int64_t tile) {
     const int64_t i = tile * TM + t;
-    const bool ok = i < d;
-    int k0 = 0, nz = 0;
-    if (ok) {
+    k0 = 0;
+    nz = 0;
+    if (i < d) {
       k0 = rowptr[i];
       nz = rowptr[i + 1] - k0;
     }
-    T v[KMAX];
-    int off[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
       bool on = k < nz;
       v[k] = on ? vals[k0 + k] : (T)0;
       off[k] = on ? colidx[k0 + k] : 0;
     }
+  };
+  if (blockIdx.x < ntiles) load_row(blockIdx.x);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t i = tile * TM + t;
+    const bool ok = i < d;
 #pragma unroll 1
     for (int q0 = 0; q0 < NQ; q0 += QU) {
       T pv[QU][4], gv[QU][KMAX][4];
@@ -123,6 +131,7 @@ __global__ void __launch_bounds__(TM, (csr_blocks<T, MP>()))
       }
     }
     __syncthreads();
+    if (tile + gridDim.x < ntiles) load_row(tile + gridDim.x);
     gram_tile<TM, TM>(g, sX, sY);
     __syncthreads();
   }
