@@ -28,15 +28,16 @@ int sm_count_ops(int device) {
 // from L2. The row's nonzeros (up to KMAX, more are read in a tail loop) are held in
 // registers; the panels are walked QU at a time, and all loads of a group
 // (the row's own panel rows and nnz 16-byte gathers per panel) are issued before any
-// of them is used, so up to QU (KMAX + 1) loads per thread are in flight (FP32: 4 CTAs
-// per SM at 128 registers, measured 3 % faster than 3 at 168 despite a small spill). Each panel
+// of them is used, so up to QU (KMAX + 1) loads per thread are in flight (FP32: 3 CTAs
+// per SM at up to 168 registers, no spill; with the next tile's row data read during
+// the Gram this measured 3 % faster than 4 CTAs at 128 registers with a spill). Each panel
 // row of the result goes to Y and, as one 16-byte store, to the row-major shared tile
 // used by the fused Gram.
 template <int MP>
 __host__ __device__ constexpr int csr_group() { return (MP / 4) % 3 == 0 ? 3 : 2; }
 template <typename T, int MP>
 __host__ __device__ constexpr int csr_blocks() {
-  return MP > 36 ? (sizeof(T) == 4 ? 2 : 1) : (sizeof(T) == 4 ? 4 : 2);
+  return MP > 36 ? (sizeof(T) == 4 ? 2 : 1) : (sizeof(T) == 4 ? 3 : 2);
 }
 
 template <typename T, int MP, int TM, int KMAX>
@@ -353,7 +354,7 @@ int csr_spmm_gram_grid(int is_f64, int mp, int64_t d, int device) {
   int tm = 128;
   int64_t ntiles = (d + tm - 1) / tm;
   // resident CTAs per SM (the launch bounds of csr_blocks)
-  int cap = sm_count_ops(device) * (mp > 36 ? (is_f64 ? 1 : 2) : (is_f64 ? 2 : 4));
+  int cap = sm_count_ops(device) * (mp > 36 ? (is_f64 ? 1 : 2) : (is_f64 ? 2 : 3));
   if (ntiles < 1) ntiles = 1;
   return (int)(ntiles < cap ? ntiles : cap);
 }
