@@ -60,8 +60,11 @@ template <typename T, int MP>
 __device__ __forceinline__ void update_pq_rows(int64_t i0, int64_t stride, int64_t d, int m, T* Q, T* P, int64_t ld,
                                                const T* sTi, const T* sTT, const T* sxc, bool do_x, bool upd,
                                                double* x) {
+  double xi = (do_x && i0 < d) ? x[i0] : 0.0;  // x one row ahead (a register)
   for (int64_t i = i0; i < d; i += stride) {
     asm volatile("" ::: "memory");  // no hoisting of the shared reads across rows
+    const double xcur = xi;
+    if (do_x && i + stride < d) xi = x[i + stride];
     T p[MP], w[MP];
 #pragma unroll
     for (int q = 0; q < MP / 4; ++q) {
@@ -78,7 +81,13 @@ __device__ __forceinline__ void update_pq_rows(int64_t i0, int64_t stride, int64
         for (int u = 0; u < 4; ++u) p[4 * q + u] = w[4 * q + u] = (T)0;
       }
     }
-    update_pq_row<T, MP>(i, m, Q, P, ld, sTi, sTT, sxc, do_x, upd, x, p, w);
+    if (do_x) {
+      T xs = 0;
+#pragma unroll
+      for (int k = 0; k < MP; ++k) xs = fma(p[k], sxc[k], xs);
+      x[i] = xcur + (double)xs;
+    }
+    update_pq_row<T, MP>(i, m, Q, P, ld, sTi, sTT, sxc, false, upd, x, p, w);
   }
 }
 
@@ -118,8 +127,13 @@ __device__ __forceinline__ void update_pq_rows_async(int64_t i0, int64_t stride,
   };
   int s = 0;
   issue(i0, 0);
+  // x of the row is read one row ahead too (a register), so its read-modify-write
+  // does not wait on memory inside the row
+  double xi = (do_x && i0 < d) ? x[i0] : 0.0;
   for (int64_t i = i0; i < d; i += stride, s ^= 1) {
     issue(i + stride, s ^ 1);
+    const double xcur = xi;
+    if (do_x && i + stride < d) xi = x[i + stride];
     upd_cp_wait1();  // this row's copies have landed
     float p[MP], w[MP];
 #pragma unroll
@@ -138,7 +152,13 @@ __device__ __forceinline__ void update_pq_rows_async(int64_t i0, int64_t stride,
       w[4 * q + 2] = b.z;
       w[4 * q + 3] = b.w;
     }
-    update_pq_row<float, MP>(i, m, Q, P, ld, sTi, sTT, sxc, do_x, upd, x, p, w);
+    if (do_x) {
+      float xs = 0.f;
+#pragma unroll
+      for (int k = 0; k < MP; ++k) xs = fmaf(p[k], sxc[k], xs);
+      x[i] = xcur + (double)xs;
+    }
+    update_pq_row<float, MP>(i, m, Q, P, ld, sTi, sTT, sxc, false, upd, x, p, w);
   }
   upd_cp_wait0();
 }
