@@ -8,9 +8,9 @@
 // solved; Def. BCG, bcg^(1)). With P the search directions:
 //   Y = A_mu P ; G = P^T Y                       (k_csr_spmm_gram / k_dense_gram)
 //   Gi = G^+ ; xc = G^+ c                        (k_small_alpha)
-//   W = Q - Y Gi ; S = W^T W                     (k_update_r)
+//   W = Q - Y Gi ; S = W^T W                     (k_update_r; FP32: k_update_r_pf)
 //   S = T^T T (T upper) ; c <- T c ; test ||c||  (k_small_beta)
-//   x += P xc ; Q = W T^{-1} ; P = Q + P T^T     (k_update_p)
+//   x += P xc ; Q = W T^{-1} ; P = Q + P T^T     (k_update_p; FP32: k_update_p_async)
 // In exact arithmetic this gives the iterates of O'Leary's recurrence (the one the
 // paper cites in Sec. 3): both are the Galerkin iterates over the block Krylov space.
 // It differs in rounding: P is built from an orthonormal basis instead of residual
