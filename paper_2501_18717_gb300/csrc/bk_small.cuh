@@ -38,17 +38,24 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
   return r;
 }
 
-// 1/x for a pivot of the unit-diagonal scaled matrix (rank_tol < x, x about 1 or
-// smaller, well inside FP32 range): an FP32 reciprocal and two FP64 Newton steps,
-// rounding-level accurate. On this part a warp issues one FP64 instruction per 64
-// cycles; this chain is on the critical path of every column, so it is kept to four
-// fused multiply-adds (the square roots of the pivots are formed afterwards, off it).
+// 1/x for a positive FP64 pivot. On this part the FP64 conversions and fused
+// multiply-adds are long-latency instructions on the critical path of every column,
+// so the estimate is formed with integer operations: x's exponent and top 20 mantissa
+// bits as an FP32 value, its FP32 reciprocal, and that widened back to FP64 (exact).
+// The estimate's relative error e0 is below 2^-19. One third-order Newton step,
+// r (1 + e + e^2) with e = 1 - x r, leaves e0^3 < 2^-57 plus rounding: three dependent
+// fused multiply-adds. Pivots outside the FP32 exponent range take an FP64 division.
 __device__ __forceinline__ double recip_pivot(double x) {
-  double r = (double)__frcp_rn((float)x);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  const int hi = __double2hiint(x);
+  const int e = ((hi >> 20) & 0x7ff) - 1023;
+  if (e < -125 || e > 125) return 1.0 / x;
+  const float xf = __uint_as_float(((unsigned)(e + 127) << 23) | ((unsigned)(hi & 0xfffff) << 3));
+  const unsigned rb = __float_as_uint(__frcp_rn(xf));
+  const int re = (int)((rb >> 23) & 0xff) - 127;
+  const double r = __hiloint2double((int)((rb & 0x80000000u) | ((unsigned)(re + 1023) << 20) | ((rb & 0x7fffffu) >> 3)),
+                                    (int)((rb & 7u) << 29));
+  const double ee = fma(-x, r, 1.0);
+  return fma(r, fma(ee, ee, ee), r);
 }
 
 // Cholesky of the unit-diagonal scaled matrix in the given column order; a pivot at
@@ -96,14 +103,13 @@ __device__ int block_cholesky_skip(SmallShared& sh, int m, double rank_tol) {
   // pivot chain does not wait on a warp that also carries update work.
   constexpr int PW = NTH - 32;
   static_assert(PW % 8 == 0 && PW >= 8, "update threads form a TI x 8 grid");
-  auto pivot = [&](int k) {  // keep column k if its pivot is above rank_tol
-    const double x = W[k * kLds + k];
+  auto pivot = [&](int k, double x) {  // keep column k if its pivot x is above rank_tol
+    const double r = recip_pivot(x);      // formed beside the test, not after it
     const bool keep = x > rank_tol;
-    sh.invd[k] = keep ? recip_pivot(x) : 0.0;  // 1 / x_k during the factorisation
+    sh.invd[k] = keep ? r : 0.0;  // 1 / x_k during the factorisation
     sh.perm[k] = keep;
-    if (keep) s_rank += 1;
   };
-  if (tid == PW) pivot(0);
+  if (tid == PW) pivot(0, W[0]);
   __syncthreads();
   for (int k = 0; k < m; ++k) {
     const double rx = sh.invd[k];  // 0 drops the column: no trailing update
@@ -123,12 +129,22 @@ __device__ int block_cholesky_skip(SmallShared& sh, int m, double rank_tol) {
         }
       } else if (tid == PW) {
         const int i = k + 1;
-        if (rx != 0.0) W[i * kLds + i] = fma(-W[i * kLds + k] * rx, W[i * kLds + k], W[i * kLds + i]);
-        pivot(i);
+        double x = W[i * kLds + i];
+        if (rx != 0.0) {
+          x = fma(-W[i * kLds + k] * rx, W[i * kLds + k], x);
+          W[i * kLds + i] = x;
+        }
+        pivot(i, x);
       }
     }
     __syncthreads();
   }
+  {  // the number of kept columns (an integer sum: the order of the adds is immaterial)
+    int kept = 0;
+    for (int k = tid; k < m; k += NTH) kept += sh.perm[k];
+    if (kept) atomicAdd(&s_rank, kept);
+  }
+  __syncthreads();
   for (int k = tid; k < m; k += NTH) {  // L[k][k] = sqrt(x_k), invd[k] = 1 / L[k][k]
     const double x = W[k * kLds + k];
     const double r = sh.perm[k] ? rsqrt_newton(x) : 0.0;
